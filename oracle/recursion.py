@@ -1,0 +1,123 @@
+"""O3 driver: compiles ``recursion.c`` with gcc and calls it through ctypes.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+from .gamma import g_tensor
+from .minors import nucleus_components
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "recursion.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "liboracle_o3.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the O3 oracle library (gcc, OpenMP); returns its path."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            lib.o3_plan_build.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P,
+                                          ctypes.POINTER(ctypes.c_void_p)]
+            lib.o3_plan_build.restype = ctypes.c_int
+            lib.o3_free.argtypes = [P]
+            lib.o3_n_ops.argtypes = [P, P, P]
+            lib.o3_n_ops.restype = ctypes.c_int64
+            lib.o3_req_nl.argtypes = [P, ctypes.c_int]
+            lib.o3_req_nl.restype = ctypes.c_int64
+            lib.o3_norm.argtypes = [P]
+            lib.o3_norm.restype = ctypes.c_double
+            lib.o3_eval.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_int]
+            lib.o3_eval.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def paper_path(n_p: int, n_n: int) -> list:
+    """Recursion order of Sec. 7: all baryons of the more numerous species
+    first; on a tie, neutrons first. 0 = proton, 1 = neutron."""
+    if n_p > n_n:
+        return [0] * n_p + [1] * n_n
+    return [1] * n_n + [0] * n_p
+
+
+class Plan:
+    """Symbolic part of O3 for one nucleus and a list of (sink, source) spin
+    assignments (protons first, each species sorted ascending)."""
+
+    def __init__(self, n_p: int, n_n: int, dirac_dim: int, requests=None, path=None):
+        lib = _load()
+        self.n_p, self.n_n, self.dim = n_p, n_n, dirac_dim
+        self.A = n_p + n_n
+        if requests is None:
+            comps = nucleus_components(n_p, n_n, dirac_dim)
+            requests = [(d, a) for d in comps for a in comps]
+        self.requests = [(tuple(d), tuple(a)) for d, a in requests]
+        self.path = list(paper_path(n_p, n_n) if path is None else path)
+        G = np.ascontiguousarray(np.rint(g_tensor(dirac_dim)).astype(np.int8))
+        snk = np.ascontiguousarray(np.array([d for d, _ in self.requests], dtype=np.int8).reshape(-1))
+        src = np.ascontiguousarray(np.array([a for _, a in self.requests], dtype=np.int8).reshape(-1))
+        pa = np.ascontiguousarray(np.array(self.path, dtype=np.int8))
+        h = ctypes.c_void_p()
+        rc = lib.o3_plan_build(n_p, n_n, dirac_dim, pa.ctypes.data, G.ctypes.data, len(self.requests),
+                               snk.ctypes.data if snk.size else None, src.ctypes.data if src.size else None,
+                               ctypes.byref(h))
+        if rc != 0:
+            raise ValueError("invalid nucleus / request for O3")
+        self._h = h
+        self._lib = lib
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.o3_free(h)
+            self._h = None
+
+    def ops(self):
+        """(N_Lambda, ops per step, needed keys per stage)."""
+        per = np.zeros(16, dtype=np.int64)
+        st = np.zeros(16, dtype=np.int64)
+        t = self._lib.o3_n_ops(self._h, per.ctypes.data, st.ctypes.data)
+        return int(t), per[: self.A - 1].tolist(), st[: self.A].tolist()
+
+    def n_l(self):
+        """Nonzero L entries per request."""
+        return [int(self._lib.o3_req_nl(self._h, r)) for r in range(len(self.requests))]
+
+    @property
+    def norm(self) -> float:
+        return float(self._lib.o3_norm(self._h))
+
+    def evaluate(self, S: np.ndarray, batch: int = 16):
+        """Per-site correlators. S: (..., 12, 12) complex, u = d.
+        Returns (C, scale): C (n_sites, n_req) complex128, scale the
+        magnitude recursion "sum |terms|" (n_sites, n_req)."""
+        S = np.ascontiguousarray(np.asarray(S, dtype=np.complex128).reshape(-1, 12, 12))
+        n = S.shape[0]
+        out = np.zeros((n, len(self.requests)), dtype=np.complex128)
+        sc = np.zeros((n, len(self.requests)), dtype=np.float64)
+        rc = self._lib.o3_eval(self._h, n, S.ctypes.data, out.ctypes.data, sc.ctypes.data, int(batch))
+        if rc != 0:
+            raise RuntimeError("o3_eval failed")
+        return out, sc

@@ -1,0 +1,60 @@
+"""Seeded synthetic point-to-all quark propagators.
+
+This module holds no contraction arithmetic: it only draws random numbers.
+Both the CPU oracle and the CUDA path take their inputs from here, so the two
+sides see identical propagators without sharing any of the method's code.
+
+Recipe (the paper uses no gauge ensemble, so these stand in for real
+propagators):
+
+* one (configuration, time slice) pair is a "slab" of Lz*Ly*Lx sink sites;
+* every slab has its own generator, ``numpy.random.default_rng(
+  SeedSequence([seed, cfg, t]))``, so any slab can be regenerated alone;
+* it draws ``standard_normal((Lz, Ly, Lx, 12, 12, 2))``; entry
+  ``S[z, y, x, row, col] = (g[..., 0] + 1j * g[..., 1]) * exp(-lam * t)``;
+* ``row`` is the sink spinor-colour index, ``col`` the source index, both
+  packed as ``3 * spin + colour``;
+* u and d quarks share one field (u = d);
+* complex64 storage is the complex128 value rounded to nearest; every consumer
+  (oracle included) promotes the rounded values, so storage rounding is never
+  counted as a compute error.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["slab", "field", "site_coords"]
+
+
+def slab(seed: int, cfg: int, t: int, dims, lam: float, dtype=np.complex128) -> np.ndarray:
+    """Propagators of one (cfg, t) slab, shape (Lz, Ly, Lx, 12, 12)."""
+    lz, ly, lx = (int(d) for d in dims)
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), int(cfg), int(t)]))
+    g = rng.standard_normal((lz, ly, lx, 12, 12, 2))
+    s = (g[..., 0] + 1j * g[..., 1]) * np.exp(-float(lam) * float(t))
+    return s.astype(dtype)
+
+
+def field(seed: int, n_cfg: int, nt: int, dims, lam: float, dtype=np.complex128,
+          cfgs=None, ts=None) -> np.ndarray:
+    """Stack of slabs, shape (n_cfg', nt', Lz, Ly, Lx, 12, 12).
+
+    ``cfgs`` / ``ts`` select a subset of configurations / time slices (default:
+    all); each slab is generated from its own (seed, cfg, t) stream.
+    """
+    cfgs = list(range(n_cfg)) if cfgs is None else list(cfgs)
+    ts = list(range(nt)) if ts is None else list(ts)
+    lz, ly, lx = (int(d) for d in dims)
+    out = np.empty((len(cfgs), len(ts), lz, ly, lx, 12, 12), dtype=dtype)
+    for i, c in enumerate(cfgs):
+        for j, t in enumerate(ts):
+            out[i, j] = slab(seed, c, t, dims, lam, dtype)
+    return out
+
+
+def site_coords(dims) -> np.ndarray:
+    """(x, y, z) integer coordinates of the sites of a slab in storage order
+    (z slowest, x fastest), shape (Lz*Ly*Lx, 3)."""
+    lz, ly, lx = (int(d) for d in dims)
+    z, y, x = np.meshgrid(np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)

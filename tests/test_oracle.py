@@ -1,0 +1,302 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (O1 Wick, O2 minors, O3 recursion) against
+something other than itself: the paper's printed counts (Tables 1, 2, 4, 5
+and Sec. 3), closed forms (single nucleon, 4He nonrelativistic, 8Be),
+symmetries (colour SU(3), homogeneity, Pauli zeros, mirror nuclei) and
+brute force on tiny inputs.
+"""
+import itertools
+from math import factorial
+
+import numpy as np
+import pytest
+
+from conftest import read_golden, spins_of
+from oracle import counts, gamma, minors, recursion, site_sum, wick
+
+
+def rand_prop(rng, n=None):
+    shape = (12, 12) if n is None else (n, 12, 12)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def baryons(n_p, n_n):
+    return "P" * n_p + "N" * n_n
+
+
+# ---- conventions -------------------------------------------------------------
+
+def test_gamma_conventions():
+    g = gamma.gammas()
+    for a in range(4):
+        for b in range(4):
+            ac = g[a] @ g[b] + g[b] @ g[a]
+            assert np.allclose(ac, 2 * np.eye(4) * (a == b))  # Euclidean Clifford algebra
+    cg5 = gamma.charge_conjugation() @ gamma.gamma5()
+    expect = np.zeros((4, 4))
+    expect[0, 1], expect[1, 0], expect[2, 3], expect[3, 2] = -1, 1, -1, 1
+    assert np.allclose(cg5, expect)
+    assert np.allclose(gamma.p_nr(), np.diag([1, 1, 0, 0]))
+    for D, g_expect in ((4, 24), (2, 12)):
+        nz = gamma.g_nonzeros(D)
+        assert [len(nz[a]) for a in range(D)] == [g_expect] * D
+        assert all(abs(v) == 1 for a in range(D) for _, v in nz[a])
+
+
+# ---- printed counts ------------------------------------------------------------
+
+def test_naive_counts_match_tables():
+    for name, D in (("table1_rel_all.txt", 4), ("table2_nonrel_all.txt", 2)):
+        for row in read_golden(name):
+            n_p, n_n = int(row[0]), int(row[1])
+            naive = counts.naive_ops(n_p, n_n, D)
+            printed = float(row[3])
+            if "e" in row[3]:
+                assert abs(naive / printed - 1) < 0.06, row  # two printed digits
+            else:
+                assert naive == int(row[3]), row
+
+
+def test_max_components_sec3():
+    for row in read_golden("sec3_max_components.txt"):
+        assert counts.p_bound(int(row[0]), int(row[1]), 4) == int(row[2])
+
+
+def test_uca_columns_consistent_with_n_l():
+    """N_list = n_u! n_d! N_L and N_contr = N_list / 2^A (Sec. 8)."""
+    for name in ("table4_nonrel_spin.txt", "table5_rel_spin.txt"):
+        for row in read_golden(name):
+            n_p, n_n = int(row[0]), int(row[1])
+            n_l, n_list, n_contr = int(row[4]), int(row[5]), int(row[6])
+            assert factorial(2 * n_p + n_n) * factorial(n_p + 2 * n_n) * n_l == n_list
+            assert n_list // 2 ** (n_p + n_n) == n_contr
+
+
+def test_n_l_from_l_tensor_matches_tables():
+    """O2's brute-force L (eq. tensor_L) has N_L nonzero components (Tables 4, 5)."""
+    for name, D in (("table4_nonrel_spin.txt", 2), ("table5_rel_spin.txt", 4)):
+        for row in read_golden(name):
+            n_p, n_n = int(row[0]), int(row[1])
+            if n_p + n_n > 4 or (D == 4 and n_p + n_n == 4 and n_p != 2):
+                continue
+            L = minors.l_tensor(baryons(n_p, n_n), spins_of(row[2]), D)
+            assert len(L) == int(row[4]), row
+
+
+def test_o3_op_counts_match_tables():
+    """O3's pruned recursion performs N_Lambda operations (Tables 1, 2, 4, 5)."""
+    for name, D, single in (("table2_nonrel_all.txt", 2, False), ("table4_nonrel_spin.txt", 2, True),
+                            ("table1_rel_all.txt", 4, False), ("table5_rel_spin.txt", 4, True)):
+        for row in read_golden(name):
+            n_p, n_n = int(row[0]), int(row[1])
+            n_ops = int(row[2 if not single else 3])
+            if D == 4 and n_ops > 2e7:
+                continue  # the large rows are pinned through the product builder
+            if single:
+                sp = spins_of(row[2])
+                plan = recursion.Plan(n_p, n_n, D, requests=[(sp, sp)])
+                assert plan.n_l() == [int(row[4])], row
+            else:
+                plan = recursion.Plan(n_p, n_n, D)
+            tot, per, stages = plan.ops()
+            assert tot == n_ops, row
+            # stage sizes never exceed the bound P (Sec. 7)
+            path = "".join("P" if b == 0 else "N" for b in plan.path)
+            np_, nn_ = 0, 0
+            for m, b in enumerate(path):
+                np_ += b == "P"
+                nn_ += b == "N"
+                assert stages[m] <= counts.p_bound(np_, nn_, D)
+
+
+def test_dense_cases_reach_q_bound():
+    """4He nonrel and the unpruned (0,2) nonrel stage need every operation of
+    the Q bounds (Sec. 7): the pruned count equals the bound sum."""
+    plan = recursion.Plan(2, 2, 2)
+    assert plan.ops()[0] == counts.q_sum_along("NNPP", 2) == 10980
+    assert counts.q_sum_along("NNNNPPPP", 4) == 448496928  # Table 1 / Table 5, 8Be
+
+
+# ---- brute force and identities --------------------------------------------------
+
+@pytest.mark.parametrize("bs,D,pairs", [
+    ("P", 4, [((0,), (0,)), ((1,), (0,)), ((3,), (3,))]),
+    ("N", 4, [((2,), (2,)), ((0,), (1,))]),
+    ("P", 2, [((0,), (0,)), ((1,), (0,))]),
+    ("PN", 2, [((0, 0), (0, 0)), ((0, 1), (1, 0)), ((1, 1), (0, 1))]),
+    ("NN", 4, [((0, 1), (0, 1)), ((0, 2), (1, 3))]),
+    ("PN", 4, [((1, 0), (0, 1))]),
+])
+def test_wick_equals_minors(rng, bs, D, pairs):
+    Su, Sd = rand_prop(rng), rand_prop(rng)
+    for d, a in pairs:
+        c1 = wick.correlator(bs, d, a, D, Su, Sd)
+        c2 = minors.correlator(bs, d, a, D, Su, Sd)
+        assert abs(c1 - c2) <= 1e-12 * max(abs(c2), 1.0)
+
+
+@pytest.mark.slow
+def test_wick_equals_minors_three_baryons(rng):
+    S = rand_prop(rng)
+    c1 = wick.correlator("PPN", (0, 1, 0), (0, 1, 1), 2, S, S)
+    c2 = minors.correlator("PPN", (0, 1, 0), (0, 1, 1), 2, S, S)
+    assert abs(c1 - c2) <= 1e-12 * abs(c2)
+
+
+@pytest.mark.parametrize("n_p,n_n,D", [(1, 0, 4), (0, 1, 4), (1, 0, 2), (1, 1, 2), (0, 2, 2), (2, 1, 2),
+                                       (1, 2, 2), (2, 2, 2), (1, 1, 4), (0, 2, 4)])
+def test_recursion_equals_minors(rng, n_p, n_n, D):
+    """O3 (the method) equals O2 (the grouped Wick sum) for every independent
+    component; this fixes the normalisation 1/(n_P! n_N!)^2."""
+    S = rand_prop(rng)
+    plan = recursion.Plan(n_p, n_n, D)
+    C, sc = plan.evaluate(S[None])
+    bs = baryons(n_p, n_n)
+    idx = range(len(plan.requests)) if len(plan.requests) <= 40 else rng.choice(len(plan.requests), 40, False)
+    for r in idx:
+        d, a = plan.requests[r]
+        c2 = minors.correlator(bs, d, a, D, S, S)
+        assert abs(C[0, r] - c2) <= 1e-13 * sc[0, r]
+    assert plan.norm == (factorial(n_p) * factorial(n_n)) ** 2
+
+
+def test_recursion_equals_minors_he4_rel_component(rng):
+    S = rand_prop(rng)
+    sp = (0, 1, 0, 1)
+    plan = recursion.Plan(2, 2, 4, requests=[(sp, sp)])
+    C, sc = plan.evaluate(S[None])
+    c2 = minors.correlator("PPNN", sp, sp, 4, S, S)
+    assert abs(C[0, 0] - c2) <= 1e-13 * sc[0, 0]
+
+
+@pytest.mark.parametrize("D", [4, 2])
+def test_single_nucleon_closed_form(rng, D):
+    """S_q = diag_spin(d^q) x 1_colour: C_P = delta 6 d^u_d [sum_b d^u_b d^d_p(b)
+    + d^u_d d^d_p(d)], C_N the same with the slot-1 flavour d, p = (0 1)(2 3)."""
+    du = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    dd = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    Su = np.kron(np.diag(du), np.eye(3))
+    Sd = np.kron(np.diag(dd), np.eye(3))
+    p = [1, 0, 3, 2]
+    inner = sum(du[b] * dd[p[b]] for b in range(D))
+    for d, a in itertools.product(range(D), repeat=2):
+        cp = wick.correlator("P", (d,), (a,), D, Su, Sd)
+        cn = wick.correlator("N", (d,), (a,), D, Su, Sd)
+        ep = 6 * du[d] * (inner + du[d] * dd[p[d]]) if d == a else 0.0
+        en = 6 * dd[d] * (inner + dd[d] * du[p[d]]) if d == a else 0.0
+        assert abs(cp - ep) <= 1e-12 * max(1, abs(ep))
+        assert abs(cn - en) <= 1e-12 * max(1, abs(en))
+    # O3 (u = d) on the same kind of propagator
+    for n_p, n_n in ((1, 0), (0, 1)):
+        plan = recursion.Plan(n_p, n_n, D)
+        C, _ = plan.evaluate(Su[None])
+        for r, (d, a) in enumerate(plan.requests):
+            inner_u = sum(du[b] * du[p[b]] for b in range(D))
+            e = 6 * du[d[0]] * (inner_u + du[d[0]] * du[p[d[0]]]) if d == a else 0.0
+            assert abs(C[0, r] - e) <= 1e-12 * max(1, abs(e))
+
+
+def test_he4_nonrel_is_determinant_product(rng):
+    """Six u and six d quarks saturate the upper spinor components: N_L = 1 and
+    C / (det S_u[up; up] det S_d[up; up]) is the same for every propagator."""
+    S = rand_prop(rng, 5)
+    plan = recursion.Plan(2, 2, 2)
+    C, _ = plan.evaluate(S)
+    ratio = C[:, 0] / np.linalg.det(S[:, :6, :6]) ** 2
+    assert np.allclose(ratio, ratio[0], rtol=1e-12, atol=0)
+    Su, Sd = rand_prop(rng), rand_prop(rng)
+    c2 = minors.correlator("PPNN", (0, 1, 0, 1), (0, 1, 0, 1), 2, Su, Sd)
+    assert abs(c2 / (np.linalg.det(Su[:6, :6]) * np.linalg.det(Sd[:6, :6])) - ratio[0]) <= 1e-10 * abs(ratio[0])
+    L = minors.l_tensor("PPNN", (0, 1, 0, 1), 2)
+    assert len(L) == 1 and abs(ratio[0] - list(L.values())[0] ** 2) <= 1e-9 * abs(ratio[0])
+
+
+def test_su3_colour_invariance(rng):
+    """S(x) -> (1 x V) S (1 x U)^dagger with V, U in SU(3) leaves C unchanged:
+    every G carries epsilon and det V = det U = 1."""
+    def su3():
+        z = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        q, r = np.linalg.qr(z)
+        q = q @ np.diag(np.diag(r) / abs(np.diag(r)))
+        return q / np.linalg.det(q) ** (1 / 3)
+    S = rand_prop(rng)
+    V, U = su3(), su3()
+    S2 = np.kron(np.eye(4), V) @ S @ np.kron(np.eye(4), U).conj().T
+    for n_p, n_n, D in ((1, 1, 2), (2, 1, 2), (1, 1, 4)):
+        plan = recursion.Plan(n_p, n_n, D)
+        C, sc = plan.evaluate(np.stack([S, S2]))
+        assert np.all(abs(C[0] - C[1]) <= 1e-12 * sc[0])
+
+
+def test_homogeneity(rng):
+    S = rand_prop(rng)
+    lam = 0.37 - 1.2j
+    for n_p, n_n, D in ((1, 1, 2), (2, 2, 2), (0, 2, 4)):
+        plan = recursion.Plan(n_p, n_n, D)
+        C, sc = plan.evaluate(np.stack([S, lam * S]))
+        A = n_p + n_n
+        assert np.all(abs(C[1] - lam ** (3 * A) * C[0]) <= 1e-12 * abs(lam) ** (3 * A) * sc[0])
+
+
+def test_pauli_forbidden_vanish(rng):
+    S = rand_prop(rng)
+    # three neutrons need three distinct upper spins: impossible with D = 2
+    assert minors.nucleus_components(0, 3, 2) == []
+    assert minors.l_tensor("NNN", (0, 1, 0), 2) == {}
+    scale = abs(wick.correlator("NN", (0, 1), (0, 1), 2, S, S))
+    assert abs(wick.correlator("NN", (0, 0), (0, 0), 2, S, S)) <= 1e-13 * scale  # repeated neutron spin
+    assert minors.l_tensor("PP", (1, 1), 4) == {}
+
+
+def test_mirror_nuclei(rng):
+    """With u = d, 3He (2,1) and 3H (1,2) are mirror images: every component
+    agrees once the species are swapped (Sec. 7 lists (1,2) only)."""
+    S = rand_prop(rng)
+    he3 = recursion.Plan(2, 1, 2)
+    h3 = recursion.Plan(1, 2, 2)
+    C1, sc = he3.evaluate(S[None])
+    C2, _ = h3.evaluate(S[None])
+    look = {r: i for i, r in enumerate(h3.requests)}
+    for i, (d, a) in enumerate(he3.requests):
+        j = look[((d[2],) + d[:2], (a[2],) + a[:2])]
+        assert abs(C1[0, i] - C2[0, j]) <= 1e-12 * sc[0, i]
+
+
+def test_site_sum_phases(rng):
+    dims = (4, 3, 5)
+    lx, ly, lz = dims
+    coords = np.array([(x, y, z) for z in range(lz) for y in range(ly) for x in range(lx)])
+    C = rng.standard_normal((len(coords), 2)) + 1j * rng.standard_normal((len(coords), 2))
+    moms = [(0, 0, 0), (1, 0, 0), (2, 1, 3), (-1, 2, 0)]
+    out = site_sum.site_sum(C, coords, dims, moms)
+    assert np.allclose(out[0], C.sum(axis=0), rtol=1e-14)
+    grid = C.reshape(lz, ly, lx, 2)
+    fft = np.fft.fftn(grid, axes=(0, 1, 2))
+    for q, (nx, ny, nz) in enumerate(moms):
+        assert np.allclose(out[q], fft[nz % lz, ny % ly, nx % lx], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.slow
+def test_be8_saturated_ratio(rng):
+    """8Be fills all 12 u and 12 d spinor-colour states at sink and source, so
+    C = K det S_u det S_d with one constant K for every propagator (the
+    saturation that also trivialises the determinant method, Sec. 8); the
+    recursion needs every one of the 448,496,928 operations (Tables 1, 5)."""
+    sp = (0, 1, 2, 3, 0, 1, 2, 3)
+    plan = recursion.Plan(4, 4, 4, requests=[(sp, sp)])
+    assert plan.ops()[0] == 448496928
+    assert plan.n_l() == [1]
+    S = rand_prop(rng, 3)
+    C, sc = plan.evaluate(S, batch=3)
+    ratio = C[:, 0] / np.linalg.det(S) ** 2
+    tol = 1e-13 * sc[:, 0] / abs(np.linalg.det(S) ** 2)
+    assert np.all(abs(ratio - ratio[0]) <= tol + tol[0])
+
+
+@pytest.mark.slow
+def test_he4_rel_all_components_count():
+    plan = recursion.Plan(2, 2, 4)
+    tot, per, stages = plan.ops()
+    assert tot == 531321120  # Table 1
+    assert len(plan.requests) == 36 * 36
