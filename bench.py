@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of the recursive multibaryon contraction on GB300.
+
+Default workload: 3He and 4He with nonrelativistic local operators on a
+16^3 x 32 lattice of synthetic u = d propagators (complex128, Gaussian
+entries times exp(-0.4 t), seed 1). One step = one mbc_contract call over
+the whole lattice for both nuclei (blocks, F_- recursion, contraction with L,
+zero-momentum site sum). The headline value is FP64; the mixed FP32-product
+/ compensated form is reported beside it with its speedup.
+
+Unit: sink-site correlators per second - one unit is the full requested C
+tensor of one nucleus at one (configuration, time slice, sink site).
+
+Multi-GPU (torchrun, one rank per GPU): configurations are sharded, rank r
+contracts configuration r of the same recipe; no collective touches the data
+path (weak scaling). --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (description, nuclei [(n_p, n_n, D, spins)], dims (Lz, Ly, Lx), nt, seed, lam, dtype)
+    "nonrel": ("3He + 4He nonrelativistic, 16^3x32, complex128, seed 1, exp(-0.4 t)",
+               [(2, 1, 2, None), (2, 2, 2, None)], (16, 16, 16), 32, 1, 0.4, "c128"),
+    "deuteron": ("deuteron (pn) nonrelativistic, all 16 components, 4^3x8, complex128, seed 0, exp(-0.5 t)",
+                 [(1, 1, 2, None)], (4, 4, 4), 8, 0, 0.5, "c128"),
+    "he4rel1": ("4He relativistic, spin component (0,1,0,1), 16^3x32, complex128, seed 2, exp(-0.4 t)",
+                [(2, 2, 4, [((0, 1, 0, 1), (0, 1, 0, 1))])], (16, 16, 16), 32, 2, 0.4, "c128"),
+    "he4rel": ("4He relativistic, all 1296 spin components, 16^3 x t-subset, complex128, seed 2",
+               [(2, 2, 4, None)], (16, 16, 16), 32, 2, 0.4, "c128"),
+    "be8": ("8Be relativistic (0,1,2,3,0,1,2,3), 16^3 x t-subset, complex64 storage, seed 4",
+            [(4, 4, 4, [((0, 1, 2, 3, 0, 1, 2, 3), (0, 1, 2, 3, 0, 1, 2, 3))])], (16, 16, 16), 32, 4, 0.4, "c64"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nonrel", choices=sorted(WORKLOADS))
+    ap.add_argument("--nt", type=int, default=0, help="time slices (0: workload default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def site_flops(st, dirac_dim):
+    nxi = 3 * dirac_dim
+    n_g2 = 4 if dirac_dim == 4 else 2
+    n_blocks = len(set(st["path"]))
+    diquark = 3 * nxi * nxi * (2 * n_g2) * 8
+    blocks = n_blocks * st["block_size"] * 6 * 8
+    recursion = 8 * st["n_ops_total"]
+    contraction = 4 * st["n_l_total"]
+    return {"recursion": recursion, "blocks": diquark + blocks, "contraction": contraction,
+            "total": recursion + diquark + blocks + contraction}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def make_field(wl, cfg, nt):
+    import synth
+    _, _, dims, _, seed, lam, dt = wl
+    return synth.field(seed, cfg + 1, nt, dims, lam, dtype=np.complex64 if dt == "c64" else np.complex128,
+                       cfgs=[cfg])
+
+
+def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0):
+    """The oracle (O3, plain C with OpenMP) on a bounded sample: whole slabs
+    of the same workload until the budget is spent."""
+    from oracle import recursion
+    _, nuclei, dims, nt, seed, lam, dt = wl
+    import synth
+    plans = [recursion.Plan(n_p, n_n, D, requests=comps) for (n_p, n_n, D, _), comps in lists_spec]
+    v3 = dims[0] * dims[1] * dims[2]
+    done = 0
+    t_tot = 0.0
+    slabs = 0
+    for t in range(nt_used):
+        slab = synth.slab(seed, 0, t, dims, lam, np.complex64 if dt == "c64" else np.complex128)
+        S = slab.reshape(-1, 12, 12).astype(np.complex128)
+        n_sites = v3
+        if t_tot > 0 and t_tot > budget_s:
+            break
+        t0 = time.perf_counter()
+        for pl in plans:
+            if v3 > 4096 or pl.A > 4 or pl.dim == 4:
+                n_sites = min(v3, 256 if pl.A <= 4 else 8)
+            pl.evaluate(S[:n_sites], batch=16)
+            done += n_sites
+        t_tot += time.perf_counter() - t0
+        slabs += 1
+        if t_tot > budget_s:
+            break
+    cores = os.cpu_count()
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        pass
+    omp = os.environ.get("OMP_NUM_THREADS")
+    return {"value": done / t_tot, "unit": "sink-site correlators/s", "cores": int(omp) if omp else cores,
+            "kind": "oracle",
+            "sample": f"{slabs} slab(s) of the workload, {done} site-correlators over all nuclei, O3 plain "
+                      f"recursion in C with OpenMP, {t_tot:.1f} s"}
+
+
+def run_reference(args, wl):
+    """--impl reference: the CPU oracle as it stands, on the machine's host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import recursion
+    import synth
+    _, nuclei, dims, nt, seed, lam, dt = wl
+    plans = []
+    for (n_p, n_n, D, spins) in nuclei:
+        plans.append(recursion.Plan(n_p, n_n, D, requests=spins))
+    v3 = dims[0] * dims[1] * dims[2]
+    per_step_sites = 1024 if all(p.dim == 2 for p in plans) else 4
+    slab = synth.slab(seed, 0, 0, dims, lam, np.complex64 if dt == "c64" else np.complex128)
+    S = slab.reshape(-1, 12, 12).astype(np.complex128)[: min(v3, per_step_sites)]
+    def step():
+        for pl in plans:
+            pl.evaluate(S, batch=16)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt_s = time.perf_counter() - t0
+    units = S.shape[0] * len(plans) * args.steps
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    val = units / dt_s
+    line = {"impl": "reference", "metric": "sink-site correlators/s", "value": val,
+            "unit": "sink-site correlators/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl[0], "sample_sites_per_step": int(S.shape[0])},
+            "cpu_baseline": {"value": val, "unit": "sink-site correlators/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{S.shape[0]} sites of slab t=0 per step, every nucleus of the workload"},
+            "e2e": {"value": val, "unit": "sink-site correlators/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    import torch
+    import paper_1301_4895_gb300 as mbc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    desc, nuclei, dims, nt_full, seed, lam, dt = wl
+    nt = args.nt or nt_full
+    if args.workload in ("he4rel", "be8") and not args.nt:
+        nt = 1  # one time slice: 4096 sinks
+    lists = [mbc.build_term_list(n_p, n_n, D, spins=spins) for (n_p, n_n, D, spins) in nuclei]
+    stats = [tl.stats() for tl in lists]
+    field_np = make_field(wl, rank, nt)
+    v3 = dims[0] * dims[1] * dims[2]
+    field = torch.from_numpy(field_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    units_per_step = v3 * nt * len(lists)
+
+    def step(precision):
+        return mbc.contract(field, lists, precision=precision, stream=stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(precision, steps, warmup):
+        for _ in range(warmup):
+            step(precision)
+        torch.cuda.synchronize(dev)
+        mbc.timing_enable(True)
+        mbc.timing_read()
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            out = step(precision)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        kms, launches = mbc.timing_read()
+        mbc.timing_enable(False)
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), kms, launches, out
+
+    with ClockSampler(local) as clk:
+        ms64, k64, n64, _ = timed(0, args.steps, args.warmup)
+        msmx, kmx, nmx, _ = timed(1, args.steps, args.warmup)
+    clocks = clk.summary()
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(field_np.shape, dtype=field.dtype, pin_memory=True)
+        pinned.copy_(torch.from_numpy(field_np))
+        host = pinned.numpy()
+        for _ in range(max(1, args.warmup)):
+            mbc.contract(host, lists, precision=0)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            res = mbc.contract(host, lists, precision=0)
+            _ = complex(res.reshape(-1)[0])  # the step's result read on the host
+        dt_s = time.perf_counter() - t0
+        tt = torch.tensor([dt_s], dtype=torch.float64, device=dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt_s = float(tt.item())
+        e2e = {"value": units_per_step * world * args.steps / dt_s, "unit": "sink-site correlators/s",
+               "h2d_bytes_per_step": int(field_np.nbytes), "d2h_bytes_per_step": int(res.nbytes)}
+
+    if rank != 0:
+        return 0
+
+    value = units_per_step * world * args.steps / (ms64 * 1e-3)
+    value_mx = units_per_step * world * args.steps / (msmx * 1e-3)
+    # roofline of the dominant kernel (the contraction kernel; FP64 pipe)
+    fl = [site_flops(st, n[2]) for st, n in zip(stats, nuclei)]
+    flops_step = sum(f["total"] for f in fl) * v3 * nt
+    peaks = measured_peaks()
+    probe64 = mbc.fma_probe(0)
+    probe32 = mbc.fma_probe(1)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nominal64 = 152 * 2 * 2 * sm_max * 1e6  # 2 DFMA / clk / SM (1.25 TFLOP/s class), 2 flop each
+    nominal32 = 152 * 128 * 2 * sm_max * 1e6
+    ach64 = flops_step * args.steps / (k64 * 1e-3) if k64 > 0 else None
+    ach32 = flops_step * args.steps / (kmx * 1e-3) if kmx > 0 else None
+    roof = {"bound": "alu", "achieved": ach64 / 1e12 if ach64 else None, "peak": nominal64 / 1e12,
+            "unit": "TFLOP/s", "frac": (ach64 / nominal64) if ach64 else None, "traffic": None,
+            "peak_kind": "FP64 vector, derived: 152 SMs x 2 DFMA/clk x max SM clock",
+            "measured_fma_peak": probe64 / 1e12, "frac_of_measured_fma": (ach64 / probe64) if ach64 else None,
+            "kernel": "k_small<FP64>", "kernel_ms_per_step": k64 / args.steps, "launches_timed": n64,
+            "flops_per_step": flops_step}
+    roof_mx = {"bound": "alu", "achieved": ach32 / 1e12 if ach32 else None, "peak": nominal32 / 1e12,
+               "unit": "TFLOP/s", "frac": (ach32 / nominal32) if ach32 else None,
+               "peak_kind": "FP32 vector, derived: 152 SMs x 128 FFMA/clk x max SM clock",
+               "measured_fma_peak": probe32 / 1e12, "kernel": "k_small<MIXED>",
+               "kernel_ms_per_step": kmx / args.steps}
+    line = {
+        "metric": "sink-site correlators/s", "value": value, "unit": "sink-site correlators/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "nuclei": [f"({n[0]},{n[1]}) D={n[2]}" for n in nuclei],
+                   "sites_per_step": v3 * nt, "units_per_step": units_per_step,
+                   "l2": "inputs larger than L2 (field %.0f MB)" % (field_np.nbytes / 2 ** 20),
+                   "parallelism": f"configurations sharded over {world} GPU(s)"},
+        "roofline": roof,
+        "mixed": {"value": value_mx, "ms_per_step": msmx / args.steps, "speedup_vs_fp64": value_mx / value,
+                  "dtype": "f32 products, float-float accumulation, f64 contraction", "roofline": roof_mx},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": int(2 * len(lists) * args.steps),
+        "n_ops": [st["n_ops_total"] for st in stats],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, [(n, tl.components()) for n, tl in zip(nuclei, lists)], nt)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

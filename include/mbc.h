@@ -1,0 +1,257 @@
+/*
+ * mbc.h - C ABI of libmbc: recursive multibaryon correlation functions on
+ * one GB300 (sm_103a).
+ *
+ * Method: Guenther, Toth, Varnhorst, "A recursive approach to determine
+ * correlation functions in multibaryon systems" (arXiv:1301.4895).
+ *
+ * Two calls make up the path:
+ *
+ *   mbc_build_term_list  - host only, once per nucleus: the G tensors
+ *                          (Sec. 2 eq. def_g), the symbolic tensor L by the
+ *                          bullet recursion (Sec. 4 eq. recr_L, Sec. 7
+ *                          eqs. rec_L_P / rec_L_N), the components of
+ *                          interest (Sec. 4-5), backward pruning into the
+ *                          operation lists Lambda^(m) (Sec. 3, Fig. 1).
+ *   mbc_contract         - on the GPU, per (configuration, time slice, sink
+ *                          site): the baryon blocks (Sec. 2, blocks
+ *                          equation, with the sink function a delta at the
+ *                          site), the F_- recursion over the lists (Sec. 4
+ *                          eq. recr_F), the contraction with L (eq.
+ *                          C_final) and the sum over sink sites with a
+ *                          momentum phase.
+ *
+ * Conventions (the paper leaves them open; every choice below changes at
+ * most a global sign, identically for every component):
+ *   - spinor-colour index xi = 3 * spin + colour, 0..11;
+ *   - Euclidean Dirac representation, C = gamma_2 gamma_4, so that
+ *     C gamma_5 has entries (0,1) = -1, (1,0) = +1, (2,3) = -1, (3,2) = +1;
+ *   - relativistic operators Gamma_1 = 1, Gamma_2 = C gamma_5; nonrelativistic
+ *     Gamma_1 = P_nr, Gamma_2 = C gamma_5 P_nr, P_nr = (1 + gamma_4) / 2
+ *     (Sec. 7), which keeps spins 0 and 1 only;
+ *   - proton (u, u, d), neutron (d, u, d) (Sec. 7); the same G at sink and
+ *     source;
+ *   - spin components are written protons first, then neutrons, each
+ *     species as an ascending set (the antisymmetric tuples of Sec. 3);
+ *   - C = (1 / (n_P! n_N!)^2) sum F_-^(A) L^(A) for the antisymmetric
+ *     components produced by the bullet recursion (eq. C_final; the paper's
+ *     normalisation also carries n_u! n_d!, which belongs to a different
+ *     block convention - the Wick definition decides);
+ *   - momentum phase exp(-2 pi i (n_x x / L_x + n_y y / L_y + n_z z / L_z)).
+ *
+ * Errors: every call returns an mbc_status; nothing throws across the ABI.
+ * Thread safety: term lists are immutable after construction and may be
+ * shared between threads; one mbc_contract call at a time per stream.
+ */
+#ifndef MBC_H
+#define MBC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MBC_OK = 0,
+    MBC_ERR_INVALID_ARG = 1,     /* malformed spec, pointer or size          */
+    MBC_ERR_PAULI_FORBIDDEN = 2, /* nucleus/component vanishes identically  */
+    MBC_ERR_OOM = 3,             /* host or device allocation failed         */
+    MBC_ERR_CUDA = 4,            /* a CUDA runtime call failed               */
+    MBC_ERR_TIMEOUT = 5,         /* a bounded device wait gave up            */
+    MBC_ERR_UNSUPPORTED = 6      /* valid request outside what is built      */
+} mbc_status;
+
+/* Human-readable name of a status; static storage, never NULL. */
+const char *mbc_status_string(mbc_status s);
+
+/* ------------------------------------------------------------------------
+ * Term lists (host, once per nucleus)
+ * ---------------------------------------------------------------------- */
+
+enum { MBC_SPIN_ALL = 0, MBC_SPIN_LISTED = 1 };
+enum { MBC_PROTON = 0, MBC_NEUTRON = 1 };
+
+/*
+ * Operator specification (Sec. 7).
+ *   n_p, n_n     number of protons and neutrons, A = n_p + n_n, 1 <= A <= 16.
+ *   dirac_dim    4 = relativistic (Gamma_1 = 1, Gamma_2 = C gamma_5),
+ *                2 = nonrelativistic (Gamma_1 = P_nr, Gamma_2 = C gamma_5 P_nr).
+ *   n_sources    number of quark sources; only 1 is built.
+ *   spin_mode    MBC_SPIN_ALL: every independent component, i.e. every pair
+ *                (sink spin set, source spin set) (Sec. 4); the output
+ *                component index is snk_index * n_sets + src_index with the
+ *                sets ordered as by mbc_term_list_components.
+ *                MBC_SPIN_LISTED: the n_spin_sel pairs given by snk_spins and
+ *                src_spins (each n_spin_sel * A int8 values, protons first,
+ *                each species ascending) (Sec. 5, Sec. 8 delta projection).
+ *   path         NULL, or path_len == A entries MBC_PROTON / MBC_NEUTRON: the
+ *                order in which baryons are added (Sec. 7). NULL selects the
+ *                paper's rule: the more numerous species first, neutrons
+ *                first on a tie.
+ * The spec is read during the call only; the caller keeps ownership.
+ */
+typedef struct {
+    int32_t n_p, n_n;
+    int32_t dirac_dim;
+    int32_t n_sources;
+    int32_t spin_mode;
+    int32_t n_spin_sel;
+    const int8_t *snk_spins;
+    const int8_t *src_spins;
+    int32_t path_len;
+    const int8_t *path;
+} mbc_op_spec;
+
+typedef struct mbc_term_list mbc_term_list; /* opaque, library-owned */
+
+#define MBC_MAX_A 16
+
+/* Statistics of a term list (Sec. 3 eqs. gen_P / gen_Q, Sec. 7 P, Q_P, Q_N;
+ * N_Lambda as in Tables 1-6). */
+typedef struct {
+    int32_t A;
+    int32_t n_steps;                     /* A - 1                            */
+    int8_t path[MBC_MAX_A];              /* baryon added at each stage       */
+    int64_t n_ops_total;                 /* N_Lambda                         */
+    int64_t n_ops[MBC_MAX_A];            /* ops of step m -> m+1, index m-1  */
+    int64_t ops_per_z[MBC_MAX_A];        /* splits per output component      */
+    int64_t stage_size[MBC_MAX_A];       /* needed components of stage m     */
+    int64_t stage_bound[MBC_MAX_A];      /* P(n_P, n_N) upper bound          */
+    int64_t q_bound[MBC_MAX_A];          /* Q_P / Q_N upper bound of step m  */
+    int64_t block_size;                  /* antisymmetric block components   */
+    int32_t n_comp;                      /* output components per site       */
+    int64_t n_l_total;                   /* nonzero L entries, all components */
+    double norm;                         /* (n_P! n_N!)^2                    */
+} mbc_list_stats;
+
+/*
+ * Build the term list for one nucleus (host only; no device involvement).
+ * On MBC_OK or MBC_ERR_PAULI_FORBIDDEN, *out receives a list the caller
+ * frees with mbc_free_term_list; a Pauli-forbidden list holds no
+ * operations and every component it yields is exactly zero (e.g. more
+ * than dirac_dim baryons of one species, Sec. 6 on the 12-quark limit).
+ * On any other status *out is set to NULL.
+ */
+mbc_status mbc_build_term_list(const mbc_op_spec *spec, mbc_term_list **out);
+
+/* Fill *st (caller-owned). */
+mbc_status mbc_term_list_stats(const mbc_term_list *list, mbc_list_stats *st);
+
+/* Spin labels of the output components: snk and src each receive
+ * n_comp * A int8 values (caller-owned), protons first. */
+mbc_status mbc_term_list_components(const mbc_term_list *list, int8_t *snk, int8_t *src);
+
+/* Number of nonzero L entries of output component c (N_L, Tables 4-6). */
+int64_t mbc_term_list_n_l(const mbc_term_list *list, int32_t c);
+
+/* Release a list and its cached device copies (NULL is a no-op). Must not
+ * race with an mbc_contract call still using the list. */
+void mbc_free_term_list(mbc_term_list *list);
+
+/* ------------------------------------------------------------------------
+ * Contraction (GPU)
+ * ---------------------------------------------------------------------- */
+
+enum { MBC_C128 = 0, MBC_C64 = 1 };              /* propagator storage */
+enum { MBC_FP64 = 0, MBC_MIXED = 1 };            /* arithmetic          */
+enum { MBC_MEM_DEVICE = 0, MBC_MEM_HOST = 1 };   /* where s_u/s_d/out live */
+
+/*
+ * Propagator fields, layout [cfg][t][z][y][x][row 12][col 12] complex,
+ * row = sink spinor-colour index, col = source index, re/im interleaved.
+ *   s_u, s_d     u and d fields (may be the same pointer: u = d).
+ *   dtype        MBC_C128 (complex double) or MBC_C64 (complex float).
+ *   memory       MBC_MEM_DEVICE: s_u, s_d and out are device pointers.
+ *                MBC_MEM_HOST: they are host pointers (pinned memory gives
+ *                overlap); the library copies slabs in and results out on
+ *                the given stream and returns after the results are in out.
+ *   stride_cfg, stride_t  element strides (in complex numbers) between
+ *                configurations and time slices; 0 selects the dense values.
+ */
+typedef struct {
+    const void *s_u;
+    const void *s_d;
+    int32_t dtype;
+    int32_t memory;
+    int32_t n_cfg, nt, lx, ly, lz;
+    int64_t stride_cfg, stride_t;
+} mbc_props;
+
+/* Launch tuning; zero fields select the library's choice. */
+typedef struct {
+    int32_t sites_per_cta;      /* small-stage kernel: sites per CTA           */
+    int32_t threads_per_cta;    /* small-stage kernel: threads per CTA         */
+    int32_t wave_sites;         /* large-stage kernels: sites in flight        */
+    int32_t regime;             /* 0 auto, 1 force small-stage, 2 force large  */
+} mbc_tune;
+
+/*
+ * Options.
+ *   precision    MBC_FP64: FP64 products and sums throughout.
+ *                MBC_MIXED: per-site power-of-two input scaling, FP32 complex
+ *                products with compensated (two-sum) float-float
+ *                accumulation of every component, FP64 for the contraction
+ *                with L and for the site/momentum sum.
+ *   n_mom, mom   n_mom >= 1 momenta, mom[3 * i + {0, 1, 2}] = (n_x, n_y, n_z)
+ *                integers (host pointer, read during the call).
+ *   t0, t1       time slices [t0, t1) are evaluated; t1 == 0 means nt.
+ *   tune         NULL or launch tuning.
+ */
+typedef struct {
+    int32_t precision;
+    int32_t n_mom;
+    const int32_t *mom;
+    int32_t t0, t1;
+    const mbc_tune *tune;
+} mbc_contract_opts;
+
+/*
+ * Evaluate the correlators of n_lists nuclei.
+ * out: complex128 [n_cfg][n_lists][t1 - t0][n_mom][n_comp_max], where
+ * n_comp_max is the largest n_comp of the lists; unused tail entries are
+ * zero. With memory == MBC_MEM_DEVICE the call is asynchronous on stream
+ * (a cudaStream_t; NULL = legacy default stream) and out is written in a
+ * fixed reduction order (bitwise reproducible). Device scratch is owned by
+ * the library, grown on demand and reused across calls; the first call per
+ * list uploads it to the current device and caches it there.
+ * Returns MBC_ERR_INVALID_ARG for bad sizes/pointers, MBC_ERR_OOM when
+ * device memory cannot be had, MBC_ERR_CUDA for a failed CUDA call.
+ */
+mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *const *lists, int32_t n_lists,
+                        const mbc_contract_opts *opts, void *out, void *stream);
+
+/* Wait for the stream and report any deferred device-side status. */
+mbc_status mbc_sync_status(void *stream);
+
+/* Release the library's device scratch on the current device. */
+void mbc_release_scratch(void);
+
+/*
+ * Kernel timing for benchmarks. While enabled, every launch of the
+ * contraction kernels (the shared-memory kernel, or the per-step wave
+ * kernels) is bracketed by CUDA events recorded on its launch stream.
+ * mbc_timing_read waits for those events and returns the summed device time
+ * in milliseconds and the number of bracketed launches since the previous
+ * read (or since enabling), then forgets them. Off by default; the flag is
+ * process-wide.
+ */
+void mbc_timing_enable(int32_t on);
+mbc_status mbc_timing_read(double *ms, int64_t *launches);
+
+/*
+ * Arithmetic peak probe: runs independent FMA chains on every SM of the
+ * current device (precision MBC_FP64: DFMA, MBC_MIXED: FFMA) and writes the
+ * achieved flop/s (2 flops per FMA) to *flops. Synchronous; used as the
+ * measured denominator of the ALU roofline.
+ */
+mbc_status mbc_fma_probe(int32_t precision, double *flops);
+
+/* Library version string, static storage. */
+const char *mbc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBC_H */

@@ -1,0 +1,295 @@
+"""Python binding of libmbc (recursive multibaryon correlation functions).
+
+Argument marshalling only: every step of the contraction runs in the CUDA
+library (``csrc/``), the term lists are built by its host C++ builder. The
+names follow the C ABI in ``include/mbc.h`` without the ``mbc_`` prefix.
+Loading fails loudly when the compiled library is missing: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "MbcError", "load", "build_term_list", "TermList", "contract", "sync_status", "release_scratch",
+    "FP64", "MIXED", "C128", "C64", "PROTON", "NEUTRON", "timing_enable", "timing_read", "fma_probe",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmbc.so")
+
+FP64, MIXED = 0, 1
+C128, C64 = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+PROTON, NEUTRON = 0, 1
+SPIN_ALL, SPIN_LISTED = 0, 1
+MAX_A = 16
+MAX_MOM = 32
+
+STATUS = {0: "MBC_OK", 1: "MBC_ERR_INVALID_ARG", 2: "MBC_ERR_PAULI_FORBIDDEN", 3: "MBC_ERR_OOM",
+          4: "MBC_ERR_CUDA", 5: "MBC_ERR_TIMEOUT", 6: "MBC_ERR_UNSUPPORTED"}
+
+
+class MbcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+class OpSpec(ctypes.Structure):
+    _fields_ = [("n_p", ctypes.c_int32), ("n_n", ctypes.c_int32), ("dirac_dim", ctypes.c_int32),
+                ("n_sources", ctypes.c_int32), ("spin_mode", ctypes.c_int32), ("n_spin_sel", ctypes.c_int32),
+                ("snk_spins", ctypes.c_void_p), ("src_spins", ctypes.c_void_p), ("path_len", ctypes.c_int32),
+                ("path", ctypes.c_void_p)]
+
+
+class ListStats(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("path", ctypes.c_int8 * MAX_A),
+                ("n_ops_total", ctypes.c_int64), ("n_ops", ctypes.c_int64 * MAX_A),
+                ("ops_per_z", ctypes.c_int64 * MAX_A), ("stage_size", ctypes.c_int64 * MAX_A),
+                ("stage_bound", ctypes.c_int64 * MAX_A), ("q_bound", ctypes.c_int64 * MAX_A),
+                ("block_size", ctypes.c_int64), ("n_comp", ctypes.c_int32), ("n_l_total", ctypes.c_int64),
+                ("norm", ctypes.c_double)]
+
+
+class Props(ctypes.Structure):
+    _fields_ = [("s_u", ctypes.c_void_p), ("s_d", ctypes.c_void_p), ("dtype", ctypes.c_int32),
+                ("memory", ctypes.c_int32), ("n_cfg", ctypes.c_int32), ("nt", ctypes.c_int32),
+                ("lx", ctypes.c_int32), ("ly", ctypes.c_int32), ("lz", ctypes.c_int32),
+                ("stride_cfg", ctypes.c_int64), ("stride_t", ctypes.c_int64)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("sites_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("wave_sites", ctypes.c_int32), ("regime", ctypes.c_int32)]
+
+
+class ContractOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("n_mom", ctypes.c_int32), ("mom", ctypes.c_void_p),
+                ("t0", ctypes.c_int32), ("t1", ctypes.c_int32), ("tune", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libmbc.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or os.environ.get("MBC_LIB") or LIB_PATH
+        if not os.path.exists(p):
+            raise OSError(f"libmbc.so not found at {p}: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(p)
+        V = ctypes.c_void_p
+        lib.mbc_status_string.argtypes = [ctypes.c_int]
+        lib.mbc_status_string.restype = ctypes.c_char_p
+        lib.mbc_build_term_list.argtypes = [ctypes.POINTER(OpSpec), ctypes.POINTER(V)]
+        lib.mbc_build_term_list.restype = ctypes.c_int
+        lib.mbc_term_list_stats.argtypes = [V, ctypes.POINTER(ListStats)]
+        lib.mbc_term_list_stats.restype = ctypes.c_int
+        lib.mbc_term_list_components.argtypes = [V, V, V]
+        lib.mbc_term_list_components.restype = ctypes.c_int
+        lib.mbc_term_list_n_l.argtypes = [V, ctypes.c_int32]
+        lib.mbc_term_list_n_l.restype = ctypes.c_int64
+        lib.mbc_free_term_list.argtypes = [V]
+        lib.mbc_free_term_list.restype = None
+        lib.mbc_contract.argtypes = [ctypes.POINTER(Props), ctypes.POINTER(V), ctypes.c_int32,
+                                     ctypes.POINTER(ContractOpts), V, V]
+        lib.mbc_contract.restype = ctypes.c_int
+        lib.mbc_sync_status.argtypes = [V]
+        lib.mbc_sync_status.restype = ctypes.c_int
+        lib.mbc_release_scratch.argtypes = []
+        lib.mbc_release_scratch.restype = None
+        lib.mbc_timing_enable.argtypes = [ctypes.c_int32]
+        lib.mbc_timing_enable.restype = None
+        lib.mbc_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        lib.mbc_timing_read.restype = ctypes.c_int
+        lib.mbc_fma_probe.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+        lib.mbc_fma_probe.restype = ctypes.c_int
+        lib.mbc_version.argtypes = []
+        lib.mbc_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, what: str, ok=(0,)):
+    if rc not in ok:
+        raise MbcError(rc, what)
+    return rc
+
+
+class TermList:
+    """Owning handle of an ``mbc_term_list``."""
+
+    def __init__(self, handle, status: int, spec: dict):
+        self._h = handle
+        self.status = status
+        self.spec = spec
+        self._lib = load()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def pauli_forbidden(self) -> bool:
+        return self.status == 2
+
+    def stats(self) -> dict:
+        st = ListStats()
+        _check(self._lib.mbc_term_list_stats(self._h, ctypes.byref(st)), "mbc_term_list_stats")
+        A = st.A
+        return {
+            "A": A, "n_steps": st.n_steps, "path": list(st.path[:A]), "n_ops_total": st.n_ops_total,
+            "n_ops": list(st.n_ops[: st.n_steps]), "ops_per_z": list(st.ops_per_z[: st.n_steps]),
+            "stage_size": list(st.stage_size[:A]), "stage_bound": list(st.stage_bound[:A]),
+            "q_bound": list(st.q_bound[: st.n_steps]), "block_size": st.block_size, "n_comp": st.n_comp,
+            "n_l_total": st.n_l_total, "norm": st.norm,
+        }
+
+    def components(self):
+        st = self.stats()
+        n, A = st["n_comp"], st["A"]
+        snk = np.zeros(max(n * A, 1), dtype=np.int8)
+        src = np.zeros(max(n * A, 1), dtype=np.int8)
+        if n:
+            _check(self._lib.mbc_term_list_components(self._h, snk.ctypes.data, src.ctypes.data),
+                   "mbc_term_list_components")
+        return [(tuple(snk[i * A:(i + 1) * A].tolist()), tuple(src[i * A:(i + 1) * A].tolist())) for i in range(n)]
+
+    def n_l(self, c: int) -> int:
+        return int(self._lib.mbc_term_list_n_l(self._h, c))
+
+    def free(self):
+        if self._h:
+            self._lib.mbc_free_term_list(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_term_list(n_p: int, n_n: int, dirac_dim: int = 4, spins=None, path=None, n_sources: int = 1) -> TermList:
+    """``mbc_build_term_list``. spins: None for every independent component,
+    or a list of (sink spins, source spins) pairs, protons first."""
+    lib = load()
+    A = n_p + n_n
+    spec = OpSpec()
+    spec.n_p, spec.n_n, spec.dirac_dim, spec.n_sources = n_p, n_n, dirac_dim, n_sources
+    keep = []
+    if spins is None:
+        spec.spin_mode = SPIN_ALL
+    else:
+        spec.spin_mode = SPIN_LISTED
+        snk = np.ascontiguousarray(np.array([s for s, _ in spins], dtype=np.int8).reshape(-1))
+        src = np.ascontiguousarray(np.array([a for _, a in spins], dtype=np.int8).reshape(-1))
+        if snk.size != len(spins) * A or src.size != len(spins) * A:
+            raise ValueError("each spin assignment needs A entries")
+        spec.n_spin_sel = len(spins)
+        spec.snk_spins, spec.src_spins = snk.ctypes.data, src.ctypes.data
+        keep += [snk, src]
+    if path is not None:
+        pa = np.ascontiguousarray(np.array(path, dtype=np.int8))
+        spec.path_len, spec.path = len(path), pa.ctypes.data
+        keep.append(pa)
+    h = ctypes.c_void_p()
+    rc = lib.mbc_build_term_list(ctypes.byref(spec), ctypes.byref(h))
+    _check(rc, "mbc_build_term_list", ok=(0, 2))
+    return TermList(h, rc, {"n_p": n_p, "n_n": n_n, "dirac_dim": dirac_dim, "spins": spins, "path": path})
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0, t1: int = 0, tune=None,
+             out=None, stream=None, dims=None):
+    """``mbc_contract`` on a u = d propagator field.
+
+    field: torch tensor (device memory) or numpy array (host memory) of shape
+    (n_cfg, nt, Lz, Ly, Lx, 12, 12), complex128 or complex64, contiguous.
+    Returns out: complex128 (n_cfg, n_lists, t1 - t0, n_mom, n_comp_max) on the
+    same side as the field.
+    """
+    lib = load()
+    lists = list(lists)
+    is_np = isinstance(field, np.ndarray)
+    if is_np:
+        if field.dtype not in (np.complex128, np.complex64) or not field.flags.c_contiguous:
+            raise ValueError("field must be a C-contiguous complex128/complex64 array")
+        dtype = C128 if field.dtype == np.complex128 else C64
+        ptr = field.ctypes.data
+        shape = field.shape
+    else:
+        import torch
+        if field.dtype not in (torch.complex128, torch.complex64) or not field.is_contiguous():
+            raise ValueError("field must be a contiguous complex128/complex64 tensor")
+        dtype = C128 if field.dtype == torch.complex128 else C64
+        ptr = field.data_ptr()
+        shape = tuple(field.shape)
+    if len(shape) != 7 or shape[-2:] != (12, 12):
+        raise ValueError("field shape must be (n_cfg, nt, Lz, Ly, Lx, 12, 12)")
+    n_cfg, nt, lz, ly, lx = shape[:5]
+    t1e = nt if t1 == 0 else t1
+    moms = np.ascontiguousarray(np.array(moms, dtype=np.int32).reshape(-1, 3))
+    comp_max = max(1, max(tl.stats()["n_comp"] for tl in lists))
+    oshape = (n_cfg, len(lists), t1e - t0, moms.shape[0], comp_max)
+    if out is None:
+        if is_np:
+            out = np.zeros(oshape, dtype=np.complex128)
+        else:
+            import torch
+            out = torch.zeros(oshape, dtype=torch.complex128, device=field.device)
+    optr = out.ctypes.data if is_np else out.data_ptr()
+    pr = Props(ptr, ptr, dtype, MEM_HOST if is_np else MEM_DEVICE, n_cfg, nt, lx, ly, lz, 0, 0)
+    tn = None
+    if tune is not None:
+        tn = Tune(tune.get("sites_per_cta", 0), tune.get("threads_per_cta", 0), tune.get("wave_sites", 0),
+                  tune.get("regime", 0))
+    op = ContractOpts(precision, moms.shape[0], moms.ctypes.data, t0, t1, ctypes.addressof(tn) if tn else None)
+    handles = (ctypes.c_void_p * len(lists))(*[tl.handle for tl in lists])
+    rc = lib.mbc_contract(ctypes.byref(pr), handles, len(lists), ctypes.byref(op), optr, _stream_ptr(stream))
+    _check(rc, "mbc_contract")
+    return out
+
+
+def sync_status(stream=None):
+    _check(load().mbc_sync_status(_stream_ptr(stream)), "mbc_sync_status")
+
+
+def release_scratch():
+    load().mbc_release_scratch()
+
+
+def timing_enable(on: bool = True):
+    """``mbc_timing_enable``: bracket the contraction kernels with CUDA events."""
+    load().mbc_timing_enable(1 if on else 0)
+
+
+def timing_read():
+    """``mbc_timing_read``: (summed kernel milliseconds, launches) since the last read."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().mbc_timing_read(ctypes.byref(ms), ctypes.byref(n)), "mbc_timing_read")
+    return ms.value, n.value
+
+
+def fma_probe(precision: int = FP64) -> float:
+    """``mbc_fma_probe``: measured FMA throughput (flop/s) of the current device."""
+    f = ctypes.c_double()
+    _check(load().mbc_fma_probe(precision, ctypes.byref(f)), "mbc_fma_probe")
+    return f.value

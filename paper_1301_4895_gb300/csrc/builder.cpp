@@ -1,0 +1,614 @@
+// Host term-list builder (runs once per nucleus; no device involvement).
+//
+// Steps (arXiv:1301.4895):
+//   * G^B tensors, eq. def_g, for the nucleon operators of Sec. 7;
+//   * their antisymmetric components (Sec. 3 tuples, Sec. 4);
+//   * L^(A) by the bullet recursion, eq. recr_L / rec_L_P / rec_L_N, with
+//     the product of eq. antis_product_2 and sgn(x|y) of Sec. 3;
+//   * the components of interest (all independent spin components, Sec. 4,
+//     or listed (sink set, source set) pairs, Sec. 5 / Sec. 8);
+//   * backward pruning into the operation lists Lambda^(m) (Sec. 3, Fig. 1,
+//     Sec. 4 end): every split of a needed component is one operation;
+//   * compaction of every stage to dense indices and z-major op arrays.
+//
+// Index spaces. A component is a tuple of four sets (Sec. 3): proton spins,
+// neutron spins (values < dim), u and d spinor-colour indices (values
+// < nxi = 3 * dim: with the nonrelativistic projector only spins 0, 1 occur).
+// A stage with set sizes (kp, kn, ku, kd) is enumerated densely by the
+// colex ranks of its four sets, proton set slowest and d set fastest; its
+// size is the bound P(n_P, n_N) of Sec. 7.
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <stdexcept>
+#include <vector>
+
+#include "mbc_internal.h"
+
+namespace {
+
+using u32 = uint32_t;
+using i64 = int64_t;
+
+i64 binom(int n, int k) {
+    if (k < 0 || n < 0 || k > n) return 0;
+    i64 r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// multinomial (a+b+c)! / (a! b! c!), zero if any part is negative
+i64 multinom3(int a, int b, int c) {
+    if (a < 0 || b < 0 || c < 0) return 0;
+    return binom(a + b + c, a) * binom(b + c, b);
+}
+
+struct Binom {
+    i64 c[25][25];
+    Binom() {
+        for (int n = 0; n < 25; ++n)
+            for (int k = 0; k < 25; ++k) c[n][k] = binom(n, k);
+    }
+};
+const Binom &B() {
+    static Binom b;
+    return b;
+}
+
+// colex rank of a set given as a bitmask: sum over its t-th element p of C(p, t+1)
+inline i64 colex_rank(u32 m) {
+    i64 r = 0;
+    int t = 1;
+    while (m) {
+        int p = __builtin_ctz(m);
+        r += B().c[p][t++];
+        m &= m - 1;
+    }
+    return r;
+}
+
+inline u32 colex_unrank(i64 r, int k, int n) {
+    u32 m = 0;
+    for (int t = k; t >= 1; --t) {
+        int p = t - 1;
+        while (p + 1 < n && B().c[p + 1][t] <= r) ++p;
+        r -= B().c[p][t];
+        m |= 1u << p;
+    }
+    return m;
+}
+
+// A component key: four sets.
+struct Key {
+    u32 dp, dn, u, d;
+};
+inline bool disjoint(const Key &a, const Key &b) {
+    return !(a.dp & b.dp) && !(a.dn & b.dn) && !(a.u & b.u) && !(a.d & b.d);
+}
+inline Key unite(const Key &a, const Key &b) { return {a.dp | b.dp, a.dn | b.dn, a.u | b.u, a.d | b.d}; }
+inline Key minus(const Key &a, const Key &b) { return {a.dp & ~b.dp, a.dn & ~b.dn, a.u & ~b.u, a.d & ~b.d}; }
+
+// sgn(x|y) of one index group: (-1)^{#(i in x, j in y, i > j)}  (Sec. 3)
+inline int group_parity(u32 x, u32 y) {
+    int n = 0;
+    while (y) {
+        int j = __builtin_ctz(y);
+        n += __builtin_popcount(x >> (j + 1));
+        y &= y - 1;
+    }
+    return n & 1;
+}
+inline int key_sign(const Key &x, const Key &y) {
+    int p = group_parity(x.dp, y.dp) ^ group_parity(x.dn, y.dn) ^ group_parity(x.u, y.u) ^ group_parity(x.d, y.d);
+    return p ? -1 : 1;
+}
+
+// Dense enumeration of a stage with fixed set sizes.
+struct Space {
+    int dim = 4, nxi = 12;
+    int kp = 0, kn = 0, ku = 0, kd = 0;
+    i64 np_ = 1, nn_ = 1, nu_ = 1, nd_ = 1;
+    void init(int dim_, int nxi_, int kp_, int kn_, int ku_, int kd_) {
+        dim = dim_; nxi = nxi_; kp = kp_; kn = kn_; ku = ku_; kd = kd_;
+        np_ = binom(dim, kp); nn_ = binom(dim, kn); nu_ = binom(nxi, ku); nd_ = binom(nxi, kd);
+    }
+    i64 size() const { return np_ * nn_ * nu_ * nd_; }
+    i64 index(const Key &k) const {
+        return ((colex_rank(k.dp) * nn_ + colex_rank(k.dn)) * nu_ + colex_rank(k.u)) * nd_ + colex_rank(k.d);
+    }
+    Key key(i64 i) const {
+        Key k;
+        i64 rd = i % nd_; i /= nd_;
+        i64 ru = i % nu_; i /= nu_;
+        i64 rn = i % nn_; i /= nn_;
+        k.d = colex_unrank(rd, kd, nxi);
+        k.u = colex_unrank(ru, ku, nxi);
+        k.dn = colex_unrank(rn, kn, dim);
+        k.dp = colex_unrank(i, kp, dim);
+        return k;
+    }
+};
+
+// Quark content of the baryons (Sec. 7): proton (u,u,d), neutron (d,u,d).
+inline int n_u_of(int b) { return b == MBC_PROTON ? 2 : 1; }
+inline int n_d_of(int b) { return b == MBC_PROTON ? 1 : 2; }
+
+// Block component index of y (one baryon): [spin][pair rank][single], where
+// for the proton the pair is the u pair and the single the d index, for the
+// neutron the pair is the d pair and the single the u index.
+inline i64 block_index(const Key &y, int b, int nxi) {
+    i64 npair = binom(nxi, 2);
+    if (b == MBC_PROTON) {
+        int s = __builtin_ctz(y.dp);
+        return (s * npair + colex_rank(y.u)) * nxi + __builtin_ctz(y.d);
+    }
+    int s = __builtin_ctz(y.dn);
+    return (s * npair + colex_rank(y.d)) * nxi + __builtin_ctz(y.u);
+}
+
+// Enumerate every split z = x + y where y is a component of one baryon of
+// type b (Sec. 3): y takes one spin of its species, n_u_of(b) u indices and
+// n_d_of(b) d indices out of z. The order is fixed (spin, u choice, d choice).
+template <class F>
+inline void for_splits(const Key &z, int b, F &&f) {
+    u32 ds = b == MBC_PROTON ? z.dp : z.dn;
+    int up[24], dq[24];
+    int nu = 0, nd = 0;
+    for (u32 m = z.u; m; m &= m - 1) up[nu++] = __builtin_ctz(m);
+    for (u32 m = z.d; m; m &= m - 1) dq[nd++] = __builtin_ctz(m);
+    for (u32 m = ds; m; m &= m - 1) {
+        u32 sbit = m & (~m + 1);
+        if (b == MBC_PROTON) {
+            for (int i = 0; i < nu; ++i)
+                for (int j = i + 1; j < nu; ++j)
+                    for (int k = 0; k < nd; ++k) {
+                        Key y{sbit, 0, (1u << up[i]) | (1u << up[j]), 1u << dq[k]};
+                        f(y);
+                    }
+        } else {
+            for (int j = 0; j < nu; ++j)
+                for (int i = 0; i < nd; ++i)
+                    for (int k = i + 1; k < nd; ++k) {
+                        Key y{0, sbit, 1u << up[j], (1u << dq[i]) | (1u << dq[k])};
+                        f(y);
+                    }
+        }
+    }
+}
+
+// ---- Gamma matrices and G (eq. def_g) -------------------------------------
+
+struct SpinEntry {
+    int r, c, v;
+};
+
+// Gamma_1 (Sec. 1 / Sec. 7): identity (rel) or P_nr = diag(1,1,0,0) (nonrel).
+std::vector<SpinEntry> gamma1(int dim) {
+    std::vector<SpinEntry> g;
+    for (int s = 0; s < dim; ++s) g.push_back({s, s, 1});
+    return g;
+}
+// Gamma_2 = C gamma_5 (Euclidean Dirac representation, C = gamma_2 gamma_4):
+// entries (0,1) = -1, (1,0) = +1, (2,3) = -1, (3,2) = +1; the nonrelativistic
+// C gamma_5 P_nr keeps the upper-left block only.
+std::vector<SpinEntry> gamma2(int dim) {
+    std::vector<SpinEntry> g = {{0, 1, -1}, {1, 0, 1}};
+    if (dim == 4) {
+        g.push_back({2, 3, -1});
+        g.push_back({3, 2, 1});
+    }
+    return g;
+}
+int levi(int a, int b, int c) {
+    if (a == b || b == c || a == c) return 0;
+    int inv = (a > b) + (a > c) + (b > c);
+    return (inv & 1) ? -1 : 1;
+}
+
+// G(alpha; xi1, xi2, xi3) nonzeros for one alpha
+struct GEntry {
+    int x1, x2, x3, v;
+};
+std::vector<GEntry> g_entries(int dim, int alpha) {
+    std::vector<GEntry> out;
+    for (auto &a : gamma1(dim)) {
+        if (a.r != alpha) continue;
+        for (auto &b : gamma2(dim))
+            for (int c1 = 0; c1 < 3; ++c1)
+                for (int c2 = 0; c2 < 3; ++c2)
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        int e = levi(c1, c2, c3);
+                        if (!e) continue;
+                        out.push_back({3 * a.c + c1, 3 * b.r + c2, 3 * b.c + c3, a.v * b.v * e});
+                    }
+    }
+    return out;
+}
+
+// Antisymmetric components of G_B (Sec. 3-4): sum over the orderings of the
+// baryon's same-flavour slots with the sign of the ordering.
+struct SparseEntry {
+    Key k;
+    i64 v;
+};
+std::vector<SparseEntry> g_minus(int dim, int b) {
+    std::vector<SparseEntry> out;
+    for (int a = 0; a < dim; ++a) {
+        auto ge = g_entries(dim, a);
+        std::vector<SparseEntry> acc;
+        for (auto &e : ge) {
+            Key k;
+            int sign = 1;
+            if (b == MBC_PROTON) {  // u at slots 1, 2; d at slot 3
+                if (e.x1 == e.x2) continue;
+                k = {1u << a, 0, (1u << e.x1) | (1u << e.x2), 1u << e.x3};
+                if (e.x1 > e.x2) sign = -1;
+            } else {  // d at slots 1, 3; u at slot 2
+                if (e.x1 == e.x3) continue;
+                k = {0, 1u << a, 1u << e.x2, (1u << e.x1) | (1u << e.x3)};
+                if (e.x1 > e.x3) sign = -1;
+            }
+            bool found = false;
+            for (auto &c : acc)
+                if (c.k.dp == k.dp && c.k.dn == k.dn && c.k.u == k.u && c.k.d == k.d) {
+                    c.v += sign * e.v;
+                    found = true;
+                    break;
+                }
+            if (!found) acc.push_back({k, (i64)(sign * e.v)});
+        }
+        for (auto &c : acc)
+            if (c.v) out.push_back(c);
+    }
+    return out;
+}
+
+struct StageCounts {
+    int kp, kn, ku, kd;
+};
+StageCounts counts_after(const int8_t *path, int m) {  // stage m (1-based)
+    StageCounts c{0, 0, 0, 0};
+    for (int i = 0; i < m; ++i) {
+        if (path[i] == MBC_PROTON) ++c.kp; else ++c.kn;
+        c.ku += n_u_of(path[i]);
+        c.kd += n_d_of(path[i]);
+    }
+    return c;
+}
+
+// Sec. 7 bounds: P(n_P, n_N) and Q_P / Q_N for adding baryon b.
+i64 p_bound(int dim, int np, int nn) {
+    int n3 = 3 * dim;
+    return binom(dim, np) * binom(dim, nn) * binom(n3, 2 * np + nn) * binom(n3, np + 2 * nn);
+}
+i64 q_bound(int dim, int np, int nn, int b) {
+    int n3 = 3 * dim;
+    int nu = 2 * np + nn, nd = np + 2 * nn;
+    if (b == MBC_PROTON)
+        return multinom3(np, 1, dim - 1 - np) * multinom3(nn, 0, dim - nn) * multinom3(nu, 2, n3 - 2 - nu) *
+               multinom3(nd, 1, n3 - 1 - nd);
+    return multinom3(np, 0, dim - np) * multinom3(nn, 1, dim - 1 - nn) * multinom3(nu, 1, n3 - 1 - nu) *
+           multinom3(nd, 2, n3 - 2 - nd);
+}
+
+double factorial(int n) {
+    double f = 1;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
+    const int np = spec->n_p, nn = spec->n_n, A = np + nn, dim = spec->dirac_dim;
+    const int nxi = 3 * dim;
+    L->A = A; L->n_p = np; L->n_n = nn; L->dim = dim; L->n_sources = 1; L->nxi = nxi;
+    L->block_size = (i64)dim * binom(nxi, 2) * nxi;
+    L->norm = factorial(np) * factorial(nn);
+    L->norm *= L->norm;
+    if (spec->path) {
+        for (int i = 0; i < A; ++i) L->path[i] = spec->path[i];
+    } else {
+        int first = np > nn ? MBC_PROTON : MBC_NEUTRON;  // Sec. 7 rule, ties: neutrons first
+        int nf = first == MBC_PROTON ? np : nn;
+        for (int i = 0; i < A; ++i) L->path[i] = (int8_t)(i < nf ? first : 1 - first);
+    }
+    for (int i = 0; i < A; ++i) L->need_block[L->path[i]] = true;
+
+    // requested components
+    auto sets = [&](int k) {
+        std::vector<std::vector<int8_t>> out;
+        for (i64 r = 0; r < binom(dim, k); ++r) {
+            u32 m = colex_unrank(r, k, dim);
+            std::vector<int8_t> v;
+            for (int s = 0; s < dim; ++s)
+                if (m & (1u << s)) v.push_back((int8_t)s);
+            out.push_back(v);
+        }
+        return out;
+    };
+    bool forbidden = np > dim || nn > dim || 2 * np + nn > nxi || np + 2 * nn > nxi;
+    std::vector<std::vector<int8_t>> comps;
+    if (spec->spin_mode == MBC_SPIN_ALL) {
+        if (!forbidden)
+            for (auto &p : sets(np))
+                for (auto &n : sets(nn)) {
+                    std::vector<int8_t> v = p;
+                    v.insert(v.end(), n.begin(), n.end());
+                    comps.push_back(v);
+                }
+        for (auto &a : comps)
+            for (auto &b : comps) {
+                L->comp_snk.insert(L->comp_snk.end(), a.begin(), a.end());
+                L->comp_src.insert(L->comp_src.end(), b.begin(), b.end());
+            }
+        L->n_comp = (int32_t)(comps.size() * comps.size());
+    } else {
+        L->n_comp = spec->n_spin_sel;
+        L->comp_snk.assign(spec->snk_spins, spec->snk_spins + (size_t)A * spec->n_spin_sel);
+        L->comp_src.assign(spec->src_spins, spec->src_spins + (size_t)A * spec->n_spin_sel);
+    }
+    L->fin_off.assign((size_t)L->n_comp + 1, 0);
+    auto spin_mask = [&](const int8_t *s, int off, int n) {
+        u32 m = 0;
+        for (int i = 0; i < n; ++i) {
+            if (s[off + i] < 0 || s[off + i] >= dim || (m & (1u << s[off + i]))) return (u32)0xFFFFFFFFu;
+            m |= 1u << s[off + i];
+        }
+        return m;
+    };
+
+    mbc_list_stats &st = L->stats;
+    std::memset(&st, 0, sizeof(st));
+    st.A = A; st.n_steps = A - 1;
+    for (int i = 0; i < A; ++i) st.path[i] = L->path[i];
+    st.block_size = L->block_size;
+    st.n_comp = L->n_comp;
+    st.norm = L->norm;
+    for (int m = 1; m <= A; ++m) {
+        auto c = counts_after(L->path, m);
+        st.stage_bound[m - 1] = p_bound(dim, c.kp, c.kn);
+        if (m < A) st.q_bound[m - 1] = q_bound(dim, c.kp, c.kn, L->path[m]);
+    }
+    if (forbidden) {
+        L->pauli_forbidden = true;
+        return MBC_ERR_PAULI_FORBIDDEN;
+    }
+
+    // ---- L^(A) by the bullet recursion (eq. recr_L) -------------------------
+    std::vector<SparseEntry> gm[2] = {g_minus(dim, MBC_PROTON), g_minus(dim, MBC_NEUTRON)};
+    std::vector<SparseEntry> cur = gm[L->path[0]];
+    for (int m = 1; m < A; ++m) {
+        int b = L->path[m];
+        auto c = counts_after(L->path, m + 1);
+        Space sp;
+        sp.init(dim, nxi, c.kp, c.kn, c.ku, c.kd);
+        std::vector<std::atomic<i64>> dense((size_t)sp.size());
+        for (auto &d : dense) d.store(0, std::memory_order_relaxed);
+        const auto &g = gm[b];
+#pragma omp parallel for schedule(dynamic, 256)
+        for (i64 i = 0; i < (i64)cur.size(); ++i)
+            for (auto &y : g)
+                if (disjoint(cur[i].k, y.k)) {
+                    Key z = unite(cur[i].k, y.k);
+                    dense[(size_t)sp.index(z)].fetch_add(cur[i].v * y.v * key_sign(cur[i].k, y.k),
+                                                         std::memory_order_relaxed);
+                }
+        std::vector<SparseEntry> nxt;
+        for (i64 i = 0; i < sp.size(); ++i) {
+            i64 v = dense[(size_t)i].load(std::memory_order_relaxed);
+            if (v) nxt.push_back({sp.key(i), v});
+        }
+        cur.swap(nxt);
+    }
+    // cur: nonzero L^(A) entries, in dense-index order of the final space
+
+    // ---- components of interest and the final needed set --------------------
+    auto cA = counts_after(L->path, A);
+    Space spA;
+    spA.init(dim, nxi, cA.kp, cA.kn, cA.ku, cA.kd);
+    std::vector<uint8_t> need_hi((size_t)spA.size(), 0);  // needed at stage A
+    struct FinEntry {
+        i64 zfull;
+        i64 l;
+    };
+    std::vector<std::vector<FinEntry>> fin((size_t)L->n_comp);
+    for (int c = 0; c < L->n_comp; ++c) {
+        u32 sp_ = spin_mask(L->comp_snk.data(), c * A, np), sn_ = spin_mask(L->comp_snk.data(), c * A + np, nn);
+        u32 ap_ = spin_mask(L->comp_src.data(), c * A, np), an_ = spin_mask(L->comp_src.data(), c * A + np, nn);
+        if (sp_ == 0xFFFFFFFFu || sn_ == 0xFFFFFFFFu || ap_ == 0xFFFFFFFFu || an_ == 0xFFFFFFFFu)
+            continue;  // a repeated or out-of-range spin: Pauli zero component
+        for (auto &e : cur) {
+            if (e.k.dp != ap_ || e.k.dn != an_) continue;
+            Key z{sp_, sn_, e.k.u, e.k.d};
+            i64 zi = spA.index(z);
+            need_hi[(size_t)zi] = 1;
+            fin[(size_t)c].push_back({zi, e.v});
+        }
+    }
+
+    // ---- backward pruning (Sec. 3): stage m needs every x of every split ----
+    std::vector<Space> spaces((size_t)A + 1);
+    for (int m = 1; m <= A; ++m) {
+        auto c = counts_after(L->path, m);
+        spaces[(size_t)m].init(dim, nxi, c.kp, c.kn, c.ku, c.kd);
+    }
+    std::vector<std::vector<uint8_t>> need((size_t)A + 1);
+    need[(size_t)A].swap(need_hi);
+    std::vector<std::vector<i64>> members((size_t)A + 1);  // needed full indices, ascending
+    std::vector<std::vector<int32_t>> compact((size_t)A + 1);
+    for (int m = A; m >= 1; --m) {
+        auto &nd = need[(size_t)m];
+        auto &mem = members[(size_t)m];
+        for (i64 i = 0; i < (i64)nd.size(); ++i)
+            if (nd[(size_t)i]) mem.push_back(i);
+        if (m == 1) break;
+        const Space &sz = spaces[(size_t)m], &sx = spaces[(size_t)m - 1];
+        std::vector<uint8_t> nx((size_t)sx.size(), 0);
+        int b = L->path[m - 1];
+#pragma omp parallel for schedule(dynamic, 256)
+        for (i64 i = 0; i < (i64)mem.size(); ++i) {
+            Key z = sz.key(mem[(size_t)i]);
+            for_splits(z, b, [&](const Key &y) {
+                __atomic_store_n(&nx[(size_t)sx.index(minus(z, y))], (uint8_t)1, __ATOMIC_RELAXED);
+            });
+        }
+        need[(size_t)m - 1].swap(nx);
+    }
+    for (int m = 1; m <= A; ++m) st.stage_size[m - 1] = (i64)members[(size_t)m].size();
+
+    // compact index of every needed component; stage 1 uses block indices
+    for (int m = 2; m <= A; ++m) {
+        auto &cm = compact[(size_t)m];
+        cm.assign((size_t)spaces[(size_t)m].size(), -1);
+        auto &mem = members[(size_t)m];
+        for (i64 i = 0; i < (i64)mem.size(); ++i) cm[(size_t)mem[(size_t)i]] = (int32_t)i;
+    }
+
+    // ---- operation lists (z-major) -----------------------------------------
+    L->steps.resize((size_t)A - 1);
+    for (int m = 1; m < A; ++m) {
+        mbc::Step &s = L->steps[(size_t)m - 1];
+        int b = L->path[m];
+        s.baryon = b;
+        const Space &sz = spaces[(size_t)m + 1], &sx = spaces[(size_t)m];
+        auto &mem = members[(size_t)m + 1];
+        s.n_z = (i64)mem.size();
+        s.n_x = m == 1 ? L->block_size : (i64)members[(size_t)m].size();
+        i64 k = 0;
+        if (s.n_z) for_splits(sz.key(mem[0]), b, [&](const Key &) { ++k; });
+        s.k = k;
+        st.ops_per_z[m - 1] = k;
+        st.n_ops[m - 1] = k * s.n_z;
+        st.n_ops_total += k * s.n_z;
+        s.x.resize((size_t)(k * s.n_z));
+        s.ys.resize((size_t)(k * s.n_z));
+        const auto &cmx = compact[(size_t)m];
+        int bprev = L->path[0];
+        std::atomic<bool> bad{false};
+#pragma omp parallel for schedule(dynamic, 256)
+        for (i64 i = 0; i < s.n_z; ++i) {
+            Key z = sz.key(mem[(size_t)i]);
+            i64 j = 0;
+            for_splits(z, b, [&](const Key &y) {
+                Key x = minus(z, y);
+                i64 xi = m == 1 ? block_index(x, bprev, nxi) : (i64)cmx[(size_t)sx.index(x)];
+                if (xi < 0 || j >= k) {
+                    bad = true;
+                    return;
+                }
+                size_t o = (size_t)(i * k + j);
+                s.x[o] = (uint32_t)xi;
+                s.ys[o] = (uint16_t)(block_index(y, b, nxi) | (key_sign(x, y) < 0 ? 0x8000u : 0u));
+                ++j;
+            });
+            if (j != k) bad = true;
+        }
+        if (bad) return MBC_ERR_INVALID_ARG;
+    }
+
+    // ---- contraction list (eq. C_final) ------------------------------------
+    if (A == 1) {
+        L->final_size = L->block_size;
+    } else {
+        L->final_size = (i64)members[(size_t)A].size();
+    }
+    const auto &cmA = compact[(size_t)A];
+    for (int c = 0; c < L->n_comp; ++c) {
+        auto &v = fin[(size_t)c];
+        std::sort(v.begin(), v.end(), [](const FinEntry &a, const FinEntry &b) { return a.zfull < b.zfull; });
+        for (auto &e : v) {
+            i64 zi = A == 1 ? block_index(spA.key(e.zfull), L->path[0], nxi) : (i64)cmA[(size_t)e.zfull];
+            L->fin_z.push_back((uint32_t)zi);
+            L->fin_l.push_back(e.l);
+        }
+        L->fin_off[(size_t)c + 1] = (i64)L->fin_z.size();
+    }
+    st.n_l_total = (i64)L->fin_z.size();
+    return MBC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mbc_status_string(mbc_status s) {
+    switch (s) {
+        case MBC_OK: return "MBC_OK";
+        case MBC_ERR_INVALID_ARG: return "MBC_ERR_INVALID_ARG";
+        case MBC_ERR_PAULI_FORBIDDEN: return "MBC_ERR_PAULI_FORBIDDEN";
+        case MBC_ERR_OOM: return "MBC_ERR_OOM";
+        case MBC_ERR_CUDA: return "MBC_ERR_CUDA";
+        case MBC_ERR_TIMEOUT: return "MBC_ERR_TIMEOUT";
+        case MBC_ERR_UNSUPPORTED: return "MBC_ERR_UNSUPPORTED";
+    }
+    return "MBC_ERR_UNKNOWN";
+}
+
+mbc_status mbc_build_term_list(const mbc_op_spec *spec, mbc_term_list **out) {
+    if (!out) return MBC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!spec) return MBC_ERR_INVALID_ARG;
+    const int A = spec->n_p + spec->n_n;
+    if (spec->n_p < 0 || spec->n_n < 0 || A < 1 || A > MBC_MAX_A) return MBC_ERR_INVALID_ARG;
+    if (spec->dirac_dim != 2 && spec->dirac_dim != 4) return MBC_ERR_INVALID_ARG;
+    if (spec->n_sources != 1) return MBC_ERR_UNSUPPORTED;
+    if (spec->spin_mode != MBC_SPIN_ALL && spec->spin_mode != MBC_SPIN_LISTED) return MBC_ERR_INVALID_ARG;
+    if (spec->spin_mode == MBC_SPIN_LISTED &&
+        (spec->n_spin_sel < 1 || !spec->snk_spins || !spec->src_spins))
+        return MBC_ERR_INVALID_ARG;
+    if (spec->path) {
+        if (spec->path_len != A) return MBC_ERR_INVALID_ARG;
+        int cp = 0;
+        for (int i = 0; i < A; ++i) {
+            if (spec->path[i] != MBC_PROTON && spec->path[i] != MBC_NEUTRON) return MBC_ERR_INVALID_ARG;
+            cp += spec->path[i] == MBC_PROTON;
+        }
+        if (cp != spec->n_p) return MBC_ERR_INVALID_ARG;
+    }
+    mbc_term_list *L = new (std::nothrow) mbc_term_list();
+    if (!L) return MBC_ERR_OOM;
+    mbc_status s;
+    try {
+        s = build(spec, L);
+    } catch (const std::bad_alloc &) {
+        s = MBC_ERR_OOM;
+    } catch (...) {
+        s = MBC_ERR_INVALID_ARG;
+    }
+    if (s == MBC_OK || s == MBC_ERR_PAULI_FORBIDDEN) {
+        *out = L;
+    } else {
+        delete L;
+    }
+    return s;
+}
+
+mbc_status mbc_term_list_stats(const mbc_term_list *list, mbc_list_stats *st) {
+    if (!list || !st) return MBC_ERR_INVALID_ARG;
+    *st = list->stats;
+    return MBC_OK;
+}
+
+mbc_status mbc_term_list_components(const mbc_term_list *list, int8_t *snk, int8_t *src) {
+    if (!list || (!snk && !src)) return MBC_ERR_INVALID_ARG;
+    if (snk) std::copy(list->comp_snk.begin(), list->comp_snk.end(), snk);
+    if (src) std::copy(list->comp_src.begin(), list->comp_src.end(), src);
+    return MBC_OK;
+}
+
+int64_t mbc_term_list_n_l(const mbc_term_list *list, int32_t c) {
+    if (!list || c < 0 || c >= list->n_comp || list->fin_off.empty()) return 0;
+    return list->fin_off[(size_t)c + 1] - list->fin_off[(size_t)c];
+}
+
+void mbc_free_term_list(mbc_term_list *list) {
+    if (!list) return;
+    mbc::free_device_cache(list);
+    delete list;
+}
+
+const char *mbc_version(void) { return "mbc 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,679 @@
+// mbc_contract: device side of the recursive multibaryon contraction.
+//
+// Host responsibilities here: validate arguments, upload each term list once
+// per device (cached on the list), pick the kernel regime and launch shape,
+// own the device scratch (grown on demand, kept per device and stream), and
+// enqueue everything on the caller's stream. All arithmetic of the path runs
+// in the kernels of small_kernel.cuh / large_kernel.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "large_kernel.cuh"
+#include "mbc_internal.h"
+#include "probe.cuh"
+#include "small_kernel.cuh"
+
+namespace mbc {
+
+#define MBC_CUDA_TRY(expr)                         \
+    do {                                           \
+        cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) {                   \
+            (void)cudaGetLastError();              \
+            return _e == cudaErrorMemoryAllocation ? MBC_ERR_OOM : MBC_ERR_CUDA; \
+        }                                          \
+    } while (0)
+
+namespace {
+
+constexpr int kSmemLimit = 227 * 1024;
+
+int64_t binom64(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// lanes per output component for a rectangular step (n_z outputs, k terms)
+int pick_group(int64_t n_z, int64_t k) {
+    int best = 1;
+    double best_eff = -1.0;
+    for (int g = 1; g <= 32; g <<= 1) {
+        int64_t per = 32 / g;
+        int64_t rounds = (n_z + per - 1) / per;
+        int64_t kk = (k + g - 1) / g;
+        double eff = (double)(n_z * k) / (double)(32 * rounds * std::max<int64_t>(kk, 1));
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = g;
+        }
+    }
+    return best;
+}
+
+struct Interval {
+    int start, end;
+    int64_t size, off;
+};
+
+// first-fit placement of buffers with lifetimes [start, end] (inclusive)
+void place(std::vector<Interval *> &bufs) {
+    std::vector<Interval *> placed;
+    for (Interval *b : bufs) {
+        std::vector<std::pair<int64_t, int64_t>> busy;
+        for (Interval *p : placed)
+            if (p->start <= b->end && b->start <= p->end) busy.push_back({p->off, p->off + p->size});
+        std::sort(busy.begin(), busy.end());
+        int64_t off = 0;
+        for (auto &r : busy) {
+            if (off + b->size <= r.first) break;
+            off = std::max(off, r.second);
+        }
+        b->off = off;
+        placed.push_back(b);
+    }
+}
+
+}  // namespace
+
+struct DeviceCache {
+    int device = -1;
+    bool small_ok = false;
+    SmallPlan sp{};          // device pointers filled in
+    int64_t site_entries = 0;
+    uint32_t *d_small_ops = nullptr;
+    // large path
+    std::vector<uint32_t *> d_opx;
+    std::vector<uint16_t *> d_opy;
+    int64_t *d_fin_off = nullptr;
+    uint32_t *d_fin_z = nullptr;
+    double *d_fin_l = nullptr;
+    int64_t max_stage = 0;
+};
+
+namespace {
+
+void free_cache(DeviceCache *c) {
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (c->device >= 0) cudaSetDevice(c->device);
+    cudaFree(c->d_small_ops);
+    for (auto p : c->d_opx) cudaFree(p);
+    for (auto p : c->d_opy) cudaFree(p);
+    cudaFree(c->d_fin_off);
+    cudaFree(c->d_fin_z);
+    cudaFree(c->d_fin_l);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete c;
+}
+
+template <class T>
+mbc_status upload(T **dst, const T *src, size_t n) {
+    *dst = nullptr;
+    if (n == 0) return MBC_OK;
+    MBC_CUDA_TRY(cudaMalloc((void **)dst, n * sizeof(T)));
+    MBC_CUDA_TRY(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return MBC_OK;
+}
+
+// Build the small-kernel plan (shared-memory layout of one site) on the host.
+bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries) {
+    std::memset(&P, 0, sizeof(P));
+    const int A = L->A;
+    if (A > 16 || L->n_comp > kSmallMaxComp || L->n_comp < 1) return false;
+    P.A = A;
+    P.dim = L->dim;
+    P.nxi = L->nxi;
+    P.n_g2 = L->dim == 4 ? 4 : 2;
+    P.n_comp = L->n_comp;
+    P.n_steps = A - 1;
+    P.path0 = L->path[0];
+    P.block_size = (int)L->block_size;
+    P.npair = (int)binom64(L->nxi, 2);
+    P.inv_norm = 1.0 / L->norm;
+    if (L->block_size >= 32768) return false;
+    for (auto &s : L->steps)
+        if (s.n_x >= 65536) return false;
+    const int n_ph = 3 + A;  // phases: 0 load, 1 Q, 2 blocks, 3.. steps, 2 + A contraction
+    Interval Sb{0, 2, (int64_t)L->nxi * L->nxi, 0}, Qb{1, 2, 3LL * L->nxi * L->nxi, 0};
+    Interval blk[2];
+    std::vector<Interval> stage((size_t)A + 1);
+    std::vector<Interval *> order = {&Sb, &Qb};
+    for (int b = 0; b < 2; ++b) {
+        P.need_blk[b] = L->need_block[b] ? 1 : 0;
+        if (!P.need_blk[b]) continue;
+        int last = 2;
+        for (int m = 1; m < A; ++m)
+            if (L->path[m] == b) last = std::max(last, 3 + m - 1);
+        if (L->path[0] == b) last = std::max(last, A == 1 ? 2 + A : 3);
+        blk[b] = {2, last, L->block_size, 0};
+        order.push_back(&blk[b]);
+    }
+    for (int m = 1; m < A; ++m) {
+        stage[(size_t)m + 1] = {3 + m - 1, 3 + m, L->steps[(size_t)m - 1].n_z, 0};
+        order.push_back(&stage[(size_t)m + 1]);
+    }
+    (void)n_ph;
+    place(order);
+    int64_t top = 0;
+    for (auto *b : order) top = std::max(top, b->off + b->size);
+    site_entries = (top + 1) & ~int64_t(1);
+    P.site_entries = (int)site_entries;
+    P.s_off = (int)Sb.off;
+    P.q_off = (int)Qb.off;
+    for (int b = 0; b < 2; ++b) P.blk_off[b] = P.need_blk[b] ? (int)blk[b].off : 0;
+    int64_t op_off = 0;
+    for (int m = 1; m < A; ++m) {
+        const Step &s = L->steps[(size_t)m - 1];
+        SmallStepDesc &d = P.step[m - 1];
+        d.n_z = (int)s.n_z;
+        d.k = (int)s.k;
+        d.g = pick_group(s.n_z, s.k);
+        d.x_off = m == 1 ? P.blk_off[L->path[0]] : (int)stage[(size_t)m].off;
+        d.y_off = P.blk_off[s.baryon];
+        d.z_off = (int)stage[(size_t)m + 1].off;
+        d.op_off = op_off;
+        op_off += s.n_z * s.k;
+    }
+    P.fin_off_buf = A == 1 ? P.blk_off[L->path[0]] : (int)stage[(size_t)A].off;
+    int64_t kmax = 1;
+    for (int c = 0; c < L->n_comp; ++c) kmax = std::max(kmax, L->fin_off[(size_t)c + 1] - L->fin_off[(size_t)c]);
+    P.fin_g = pick_group(L->n_comp, kmax);
+    return true;
+}
+
+DeviceCache *get_cache(const mbc_term_list *Lc, int device, mbc_status &st) {
+    mbc_term_list *L = const_cast<mbc_term_list *>(Lc);
+    std::lock_guard<std::mutex> g(L->dev_mu);
+    if ((int)L->dev.size() <= device) L->dev.resize((size_t)device + 1, nullptr);
+    if (L->dev[(size_t)device]) {
+        st = MBC_OK;
+        return L->dev[(size_t)device];
+    }
+    DeviceCache *c = new (std::nothrow) DeviceCache();
+    if (!c) {
+        st = MBC_ERR_OOM;
+        return nullptr;
+    }
+    c->device = device;
+    st = MBC_OK;
+    // contraction list
+    std::vector<double> lval(L->fin_l.begin(), L->fin_l.end());
+    if ((st = upload(&c->d_fin_off, L->fin_off.data(), L->fin_off.size())) != MBC_OK ||
+        (st = upload(&c->d_fin_z, L->fin_z.data(), L->fin_z.size())) != MBC_OK ||
+        (st = upload(&c->d_fin_l, lval.data(), lval.size())) != MBC_OK) {
+        free_cache(c);
+        return nullptr;
+    }
+    // small-kernel plan and packed ops
+    c->small_ok = !L->pauli_forbidden && plan_small(L, c->sp, c->site_entries);
+    if (c->small_ok) {
+        std::vector<uint32_t> packed;
+        for (auto &s : L->steps)
+            for (size_t i = 0; i < s.x.size(); ++i)
+                packed.push_back(s.x[i] | ((uint32_t)(s.ys[i] & 0x7fffu) << 16) | ((uint32_t)(s.ys[i] >> 15) << 31));
+        if ((st = upload(&c->d_small_ops, packed.data(), packed.size())) != MBC_OK) {
+            free_cache(c);
+            return nullptr;
+        }
+        c->sp.ops = c->d_small_ops;
+        c->sp.fin_off = c->d_fin_off;
+        c->sp.fin_z = c->d_fin_z;
+        c->sp.fin_l = c->d_fin_l;
+    }
+    // large-path op arrays
+    c->d_opx.assign(L->steps.size(), nullptr);
+    c->d_opy.assign(L->steps.size(), nullptr);
+    for (size_t m = 0; m < L->steps.size(); ++m) {
+        const Step &s = L->steps[m];
+        c->max_stage = std::max(c->max_stage, s.n_z);
+        if ((st = upload(&c->d_opx[m], s.x.data(), s.x.size())) != MBC_OK ||
+            (st = upload(&c->d_opy[m], s.ys.data(), s.ys.size())) != MBC_OK) {
+            free_cache(c);
+            return nullptr;
+        }
+    }
+    L->dev[(size_t)device] = c;
+    return c;
+}
+
+// ---- scratch ---------------------------------------------------------------
+struct Scratch {
+    void *p = nullptr;
+    size_t n = 0;
+};
+std::mutex g_scratch_mu;
+std::map<std::pair<int, cudaStream_t>, Scratch> g_scratch;
+
+mbc_status scratch_get(int device, cudaStream_t s, size_t bytes, void **out) {
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    Scratch &sc = g_scratch[{device, s}];
+    if (sc.n < bytes) {
+        if (sc.p) {
+            cudaStreamSynchronize(s);
+            cudaFree(sc.p);
+            sc.p = nullptr;
+            sc.n = 0;
+        }
+        size_t want = std::max(bytes, (size_t)(1 << 20));
+        MBC_CUDA_TRY(cudaMalloc(&sc.p, want));
+        sc.n = want;
+    }
+    *out = sc.p;
+    return MBC_OK;
+}
+
+int g_const_dev_mask = 0;
+std::mutex g_const_mu;
+
+mbc_status ensure_constants(int device) {
+    std::lock_guard<std::mutex> g(g_const_mu);
+    if (device < 31 && (g_const_dev_mask >> device) & 1) return MBC_OK;
+    uint8_t pi[66], pj[66];
+    int r = 0;
+    for (int j = 1; j < 12; ++j)
+        for (int i = 0; i < j; ++i) {  // colex order: rank = i + j(j-1)/2
+            pi[r] = (uint8_t)i;
+            pj[r] = (uint8_t)j;
+            ++r;
+        }
+    MBC_CUDA_TRY(cudaMemcpyToSymbol(c_pair_i, pi, sizeof(pi)));
+    MBC_CUDA_TRY(cudaMemcpyToSymbol(c_pair_j, pj, sizeof(pj)));
+    if (device < 31) g_const_dev_mask |= 1 << device;
+    return MBC_OK;
+}
+
+int sm_count(int device) {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(device);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+    if (n <= 0) n = 1;
+    cache[device] = n;
+    return n;
+}
+
+// ---- launchers -------------------------------------------------------------
+
+template <class Tr>
+mbc_status run_small(const DeviceCache *c, const FieldDesc &F, const MomDesc &M, const mbc_tune *tune, int device,
+                     cudaStream_t stream, double2 *partial_out, int64_t &n_tiles, int &tiles_per_slab, int &T) {
+    using V = typename Tr::V;
+    const SmallPlan &P = c->sp;
+    const int64_t per_site = c->site_entries * (int64_t)sizeof(V) + 16LL * (P.n_comp + M.n_mom);
+    T = (int)std::min<int64_t>(32, kSmemLimit / per_site);
+    if (tune && tune->sites_per_cta > 0) T = std::min(T, tune->sites_per_cta);
+    if (T < 1) return MBC_ERR_UNSUPPORTED;
+    const size_t smem = (size_t)T * per_site;
+    const int v3 = F.lx * F.ly * F.lz;
+    tiles_per_slab = (v3 + T - 1) / T;
+    n_tiles = (int64_t)F.n_cfg * F.n_t * tiles_per_slab;
+    if (!partial_out) return MBC_OK;  // sizing query
+    MBC_CUDA_TRY(cudaFuncSetAttribute(k_small<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small<Tr>, 32 * T, smem));
+    if (per_sm < 1) return MBC_ERR_UNSUPPORTED;
+    int64_t grid = std::min<int64_t>(n_tiles, (int64_t)per_sm * sm_count(device));
+    if (grid < 1) return MBC_OK;
+    {
+        TimedLaunch tl(stream);
+        k_small<Tr><<<(unsigned)grid, 32 * T, smem, stream>>>(P, F, M, partial_out, n_tiles, tiles_per_slab);
+    }
+    MBC_CUDA_TRY(cudaGetLastError());
+    return MBC_OK;
+}
+
+struct LargeSizes {
+    int W;
+    size_t blk_bytes, stage_bytes, c_bytes, sexp_bytes;
+};
+
+template <class Tr>
+LargeSizes large_sizes(const mbc_term_list *L, const DeviceCache *c, const mbc_tune *tune, int64_t n_items) {
+    using V = typename Tr::V;
+    LargeSizes s{};
+    int64_t per_site = (int64_t)sizeof(V) * (2 * L->block_size + 2 * std::max<int64_t>(c->max_stage, 1)) +
+                       16LL * L->n_comp + 4;
+    const int64_t budget = 8LL << 30;
+    int64_t W = budget / per_site;
+    if (tune && tune->wave_sites > 0) W = tune->wave_sites;
+    W = std::max<int64_t>(32, std::min<int64_t>(W, 4096));
+    W = std::min<int64_t>(W, (n_items + 31) / 32 * 32);
+    W = std::max<int64_t>(32, W / 32 * 32);
+    s.W = (int)W;
+    s.blk_bytes = (size_t)(L->block_size * W) * sizeof(V);
+    s.stage_bytes = (size_t)(std::max<int64_t>(c->max_stage, 1) * W) * sizeof(V);
+    s.c_bytes = (size_t)L->n_comp * W * sizeof(double2);
+    s.sexp_bytes = (size_t)W * sizeof(int32_t);
+    return s;
+}
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+template <class Tr>
+mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDesc &F, const MomDesc &M,
+                     const mbc_tune *tune, int device, cudaStream_t stream, char *scratch, double2 *partial,
+                     const LargeSizes &ls, int64_t n_items, int v3p) {
+    using V = typename Tr::V;
+    const int W = ls.W;
+    char *p = scratch;
+    V *fP = reinterpret_cast<V *>(p);
+    p += align256(ls.blk_bytes);
+    V *fN = reinterpret_cast<V *>(p);
+    p += align256(ls.blk_bytes);
+    V *buf[2];
+    buf[0] = reinterpret_cast<V *>(p);
+    p += align256(ls.stage_bytes);
+    buf[1] = reinterpret_cast<V *>(p);
+    p += align256(ls.stage_bytes);
+    double2 *Cb = reinterpret_cast<double2 *>(p);
+    p += align256(ls.c_bytes);
+    int32_t *sexp = reinterpret_cast<int32_t *>(p);
+    const int nsm = sm_count(device);
+    const int nxi = L->nxi;
+    const size_t blk_smem = (size_t)16 * 4 * nxi * nxi * sizeof(V);
+    MBC_CUDA_TRY(cudaFuncSetAttribute(k_large_blocks<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk_smem));
+    for (int64_t item0 = 0; item0 < n_items; item0 += W) {
+        WaveDesc wv;
+        wv.item0 = item0;
+        wv.W = W;
+        wv.v3 = F.lx * F.ly * F.lz;
+        wv.v3p = v3p;
+        wv.n_items = n_items;
+        k_large_blocks<Tr><<<W / 16, 512, blk_smem, stream>>>(F, wv, nxi, L->dim == 4 ? 4 : 2, (int)L->block_size,
+                                                              (int)binom64(nxi, 2), L->need_block[0],
+                                                              L->need_block[1], fP, fN, sexp);
+        MBC_CUDA_TRY(cudaGetLastError());
+        const V *X = L->path[0] == MBC_PROTON ? fP : fN;
+        for (size_t m = 0; m < L->steps.size(); ++m) {
+            const Step &s = L->steps[m];
+            V *Z = buf[(m + 1) & 1];
+            const V *Y = s.baryon == MBC_PROTON ? fP : fN;
+            const int threads = 256;
+            const int64_t total_warps = (int64_t)nsm * 8 * (threads / 32);
+            int64_t ngroups = W / 32;
+            int64_t zchunk = (s.n_z * ngroups + 8 * total_warps - 1) / (8 * total_warps);
+            zchunk = std::max<int64_t>(1, std::min<int64_t>(zchunk, 256));
+            if (tune && tune->regime == 2 && tune->threads_per_cta > 0) zchunk = tune->threads_per_cta;
+            int64_t items = ((s.n_z + zchunk - 1) / zchunk) * ngroups;
+            int64_t grid = std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8);
+            grid = std::max<int64_t>(grid, 1);
+            {
+                TimedLaunch tl(stream);
+                k_large_step<Tr><<<(unsigned)grid, threads, 0, stream>>>(c->d_opx[m], c->d_opy[m], s.n_z, s.k,
+                                                                         zchunk, W, X, Y, Z);
+            }
+            MBC_CUDA_TRY(cudaGetLastError());
+            X = Z;
+        }
+        {
+            int64_t items = (int64_t)L->n_comp * (W / 32);
+            int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
+            k_large_contract<Tr><<<(unsigned)grid, 256, 0, stream>>>(c->d_fin_off, c->d_fin_z, c->d_fin_l, L->n_comp,
+                                                                     W, X, sexp, L->A, 1.0 / L->norm, Cb);
+            MBC_CUDA_TRY(cudaGetLastError());
+        }
+        {
+            int64_t groups = std::min<int64_t>(W, n_items - item0) / 32;
+            k_large_sitesum<<<(unsigned)groups, 256, 0, stream>>>(F, wv, M, L->n_comp, Cb, partial);
+            MBC_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    return MBC_OK;
+}
+
+}  // namespace
+
+void free_device_cache(mbc_term_list *list) {
+    std::lock_guard<std::mutex> g(list->dev_mu);
+    for (auto *c : list->dev) free_cache(c);
+    list->dev.clear();
+}
+
+}  // namespace mbc
+
+using namespace mbc;
+
+extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *const *lists, int32_t n_lists,
+                                   const mbc_contract_opts *opts, void *out, void *stream_v) {
+    if (!props || !lists || n_lists < 1 || !opts || !out) return MBC_ERR_INVALID_ARG;
+    if (!props->s_u || !props->s_d) return MBC_ERR_INVALID_ARG;
+    if (props->s_u != props->s_d) return MBC_ERR_UNSUPPORTED;  // u = d fields only
+    if (props->dtype != MBC_C128 && props->dtype != MBC_C64) return MBC_ERR_INVALID_ARG;
+    if (props->memory != MBC_MEM_DEVICE && props->memory != MBC_MEM_HOST) return MBC_ERR_INVALID_ARG;
+    if (props->n_cfg < 1 || props->nt < 1 || props->lx < 1 || props->ly < 1 || props->lz < 1) return MBC_ERR_INVALID_ARG;
+    if (opts->precision != MBC_FP64 && opts->precision != MBC_MIXED) return MBC_ERR_INVALID_ARG;
+    if (opts->n_mom < 1 || opts->n_mom > kMaxMom || !opts->mom) return MBC_ERR_INVALID_ARG;
+    const int t0 = opts->t0, t1 = opts->t1 == 0 ? props->nt : opts->t1;
+    if (t0 < 0 || t1 > props->nt || t1 <= t0) return MBC_ERR_INVALID_ARG;
+    for (int i = 0; i < n_lists; ++i)
+        if (!lists[i]) return MBC_ERR_INVALID_ARG;
+    const int64_t v3 = (int64_t)props->lx * props->ly * props->lz;
+    if (v3 > (1LL << 30)) return MBC_ERR_INVALID_ARG;
+    const int64_t site_elems = 144;
+    const int64_t stride_t = props->stride_t ? props->stride_t : v3 * site_elems;
+    const int64_t stride_cfg = props->stride_cfg ? props->stride_cfg : stride_t * props->nt;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_v);
+    int device = 0;
+    MBC_CUDA_TRY(cudaGetDevice(&device));
+    mbc_status st = ensure_constants(device);
+    if (st != MBC_OK) return st;
+
+    int comp_max = 1;
+    for (int i = 0; i < n_lists; ++i) comp_max = std::max(comp_max, (int)lists[i]->n_comp);
+    const int n_t = t1 - t0;
+    const size_t out_bytes = (size_t)props->n_cfg * n_lists * n_t * opts->n_mom * comp_max * sizeof(double2);
+
+    // host-memory mode: stage the evaluated slices on the device
+    const void *field = props->s_u;
+    void *dev_out = out;
+    const size_t elem = props->dtype == MBC_C128 ? 16 : 8;
+    void *staging = nullptr;
+    int64_t f_stride_cfg = stride_cfg, f_stride_t = stride_t, f_t_shift = 0;
+    if (props->memory == MBC_MEM_HOST) {
+        const size_t slab_bytes = (size_t)v3 * site_elems * elem;
+        const size_t in_bytes = (size_t)props->n_cfg * n_t * slab_bytes;
+        MBC_CUDA_TRY(cudaMallocAsync(&staging, in_bytes + out_bytes, stream));
+        for (int cfg = 0; cfg < props->n_cfg; ++cfg) {
+            const char *src = reinterpret_cast<const char *>(props->s_u) + ((size_t)cfg * stride_cfg + (size_t)t0 * stride_t) * elem;
+            char *dst = reinterpret_cast<char *>(staging) + (size_t)cfg * n_t * slab_bytes;
+            if (stride_t * (int64_t)elem == (int64_t)slab_bytes) {
+                MBC_CUDA_TRY(cudaMemcpyAsync(dst, src, n_t * slab_bytes, cudaMemcpyHostToDevice, stream));
+            } else {
+                for (int t = 0; t < n_t; ++t)
+                    MBC_CUDA_TRY(cudaMemcpyAsync(dst + t * slab_bytes, src + (size_t)t * stride_t * elem, slab_bytes,
+                                                 cudaMemcpyHostToDevice, stream));
+            }
+        }
+        field = staging;
+        f_stride_t = v3 * site_elems;
+        f_stride_cfg = f_stride_t * n_t;
+        f_t_shift = t0;
+        dev_out = reinterpret_cast<char *>(staging) + in_bytes;
+    }
+
+    FieldDesc F;
+    F.s = field;
+    F.dtype = props->dtype == MBC_C128 ? 0 : 1;
+    F.n_cfg = props->n_cfg;
+    F.nt = props->nt;
+    F.lx = props->lx;
+    F.ly = props->ly;
+    F.lz = props->lz;
+    F.stride_cfg = f_stride_cfg;
+    F.stride_t = f_stride_t;
+    F.t0 = (int)(t0 - f_t_shift);
+    F.n_t = n_t;
+    // with staging, slice t0 sits at index 0: shift the base instead
+    MomDesc M;
+    std::memset(&M, 0, sizeof(M));
+    M.n_mom = opts->n_mom;
+    for (int q = 0; q < opts->n_mom; ++q)
+        for (int d = 0; d < 3; ++d) M.mom[q][d] = opts->mom[3 * q + d];
+
+    cudaError_t ce = cudaMemsetAsync(dev_out, 0, out_bytes, stream);
+    if (ce != cudaSuccess) return MBC_ERR_CUDA;
+    const int64_t n_slabs = (int64_t)props->n_cfg * n_t;
+    const bool mixed = opts->precision == MBC_MIXED;
+
+    for (int li = 0; li < n_lists; ++li) {
+        const mbc_term_list *L = lists[li];
+        if (L->pauli_forbidden || L->n_comp == 0) continue;  // identically zero
+        DeviceCache *c = get_cache(L, device, st);
+        if (!c) return st;
+        const int regime = opts->tune ? opts->tune->regime : 0;
+        bool small = c->small_ok && regime != 2;
+        if (regime == 1 && !c->small_ok) return MBC_ERR_UNSUPPORTED;
+        if (small) {
+            int64_t n_tiles = 0;
+            int tps = 0, T = 0;
+            st = mixed ? run_small<MixedTraits>(c, F, M, opts->tune, device, stream, nullptr, n_tiles, tps, T)
+                       : run_small<FP64Traits>(c, F, M, opts->tune, device, stream, nullptr, n_tiles, tps, T);
+            if (st != MBC_OK) small = false;
+            else {
+                void *scr = nullptr;
+                size_t pbytes = (size_t)n_tiles * M.n_mom * L->n_comp * sizeof(double2);
+                if ((st = scratch_get(device, stream, pbytes, &scr)) != MBC_OK) return st;
+                double2 *partial = reinterpret_cast<double2 *>(scr);
+                st = mixed ? run_small<MixedTraits>(c, F, M, opts->tune, device, stream, partial, n_tiles, tps, T)
+                           : run_small<FP64Traits>(c, F, M, opts->tune, device, stream, partial, n_tiles, tps, T);
+                if (st != MBC_OK) return st;
+                int64_t outs = n_slabs * M.n_mom * L->n_comp;
+                unsigned grid = (unsigned)std::min<int64_t>((outs + 255) / 256, 65535);
+                k_reduce_tiles<<<std::max(grid, 1u), 256, 0, stream>>>(partial, n_slabs, tps, M.n_mom, L->n_comp,
+                                                                      n_t, li, n_lists, comp_max,
+                                                                      reinterpret_cast<double2 *>(dev_out));
+                MBC_CUDA_TRY(cudaGetLastError());
+                continue;
+            }
+        }
+        // large-stage path
+        const int v3p = (int)((v3 + 31) / 32 * 32);
+        const int64_t n_items = n_slabs * v3p;
+        LargeSizes ls = mixed ? large_sizes<MixedTraits>(L, c, opts->tune, n_items)
+                              : large_sizes<FP64Traits>(L, c, opts->tune, n_items);
+        const size_t pbytes = (size_t)(n_items / 32) * M.n_mom * L->n_comp * sizeof(double2);
+        const size_t need = align256(pbytes) + 2 * align256(ls.blk_bytes) + 2 * align256(ls.stage_bytes) +
+                            align256(ls.c_bytes) + align256(ls.sexp_bytes);
+        void *scr = nullptr;
+        if ((st = scratch_get(device, stream, need, &scr)) != MBC_OK) return st;
+        double2 *partial = reinterpret_cast<double2 *>(scr);
+        char *rest = reinterpret_cast<char *>(scr) + align256(pbytes);
+        st = mixed ? run_large<MixedTraits>(L, c, F, M, opts->tune, device, stream, rest, partial, ls, n_items, v3p)
+                   : run_large<FP64Traits>(L, c, F, M, opts->tune, device, stream, rest, partial, ls, n_items, v3p);
+        if (st != MBC_OK) return st;
+        int64_t outs = n_slabs * M.n_mom * L->n_comp;
+        unsigned grid = (unsigned)std::min<int64_t>((outs + 255) / 256, 65535);
+        k_reduce_tiles<<<std::max(grid, 1u), 256, 0, stream>>>(partial, n_slabs, v3p / 32, M.n_mom, L->n_comp, n_t,
+                                                              li, n_lists, comp_max,
+                                                              reinterpret_cast<double2 *>(dev_out));
+        MBC_CUDA_TRY(cudaGetLastError());
+    }
+
+    if (props->memory == MBC_MEM_HOST) {
+        MBC_CUDA_TRY(cudaMemcpyAsync(out, dev_out, out_bytes, cudaMemcpyDeviceToHost, stream));
+        MBC_CUDA_TRY(cudaFreeAsync(staging, stream));
+        MBC_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    return MBC_OK;
+}
+
+extern "C" mbc_status mbc_sync_status(void *stream_v) {
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream_v));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return MBC_ERR_CUDA;
+    }
+    return MBC_OK;
+}
+
+extern "C" void mbc_release_scratch(void) {
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return;
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    for (auto it = g_scratch.begin(); it != g_scratch.end();) {
+        if (it->first.first == device) {
+            cudaStreamSynchronize(it->first.second);
+            cudaFree(it->second.p);
+            it = g_scratch.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+extern "C" void mbc_timing_enable(int32_t on) {
+    TimingState &t = timing();
+    std::lock_guard<std::mutex> g(t.mu);
+    t.on = on != 0;
+}
+
+extern "C" mbc_status mbc_timing_read(double *ms, int64_t *launches) {
+    if (!ms || !launches) return MBC_ERR_INVALID_ARG;
+    TimingState &t = timing();
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    {
+        std::lock_guard<std::mutex> g(t.mu);
+        ev.swap(t.ev);
+    }
+    double tot = 0.0;
+    mbc_status st = MBC_OK;
+    for (auto &e : ev) {
+        float f = 0.f;
+        if (cudaEventSynchronize(e.second) != cudaSuccess || cudaEventElapsedTime(&f, e.first, e.second) != cudaSuccess) {
+            (void)cudaGetLastError();
+            st = MBC_ERR_CUDA;
+        }
+        tot += f;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    *ms = tot;
+    *launches = (int64_t)ev.size();
+    return st;
+}
+
+extern "C" mbc_status mbc_fma_probe(int32_t precision, double *flops) {
+    if (!flops || (precision != MBC_FP64 && precision != MBC_MIXED)) return MBC_ERR_INVALID_ARG;
+    int device = 0;
+    MBC_CUDA_TRY(cudaGetDevice(&device));
+    const int nsm = sm_count(device);
+    const int threads = 256, blocks = nsm * 8;
+    const int iters = precision == MBC_FP64 ? 4096 : 65536;
+    void *buf = nullptr;
+    MBC_CUDA_TRY(cudaMalloc(&buf, (size_t)threads * blocks * sizeof(double)));
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a);
+        if (precision == MBC_FP64)
+            k_fma_probe<double><<<blocks, threads>>>((double *)buf, iters, 1.0);
+        else
+            k_fma_probe<float><<<blocks, threads>>>((float *)buf, iters, 1.0f);
+        cudaEventRecord(b);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(buf);
+    if (e != cudaSuccess) return MBC_ERR_CUDA;
+    *flops = 2.0 * 8.0 * iters * (double)threads * blocks / (best * 1e-3);
+    return MBC_OK;
+}

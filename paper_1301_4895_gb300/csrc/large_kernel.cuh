@@ -1,0 +1,237 @@
+// Large-stage contraction kernels (relativistic nuclei: blocks of 3168
+// components, stages up to millions of components per site, Sec. 7 P bound
+// with D = 4). Stage buffers live in device scratch with the layout
+// [component][wave site], so 32 consecutive sites of one component are one
+// coalesced row; a "wave" of W sites (a multiple of 32) is processed by the
+// whole GPU one step at a time, and each step streams its term list once per
+// wave. Lanes are sites; a warp walks the z-major list of its chunk with
+// warp-uniform (x, y, sign) operands that the lanes load cooperatively and
+// broadcast by shuffles.
+#pragma once
+
+#include "device_common.cuh"
+#include "small_kernel.cuh"
+
+namespace mbc {
+
+struct WaveDesc {
+    int64_t item0;         // first padded site item of the wave
+    int32_t W;             // sites in the wave (multiple of 32)
+    int32_t v3;            // sites per slab
+    int32_t v3p;           // padded sites per slab (multiple of 32)
+    int64_t n_items;       // total padded items
+};
+
+__device__ __forceinline__ bool item_site(const FieldDesc &F, const WaveDesc &wv, int64_t item, int &cfg, int &t,
+                                          int &site) {
+    if (item >= wv.n_items) return false;
+    int64_t slab = item / wv.v3p;
+    site = (int)(item % wv.v3p);
+    cfg = (int)(slab / F.n_t);
+    t = F.t0 + (int)(slab % F.n_t);
+    return site < wv.v3;
+}
+
+// Blocks for 16 sites per CTA (512 threads): thread = (site lane, entry slice).
+template <class Tr>
+__global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, int nxi, int n_g2, int block_size,
+                                                      int npair, int need_p, int need_n, typename Tr::V *fP,
+                                                      typename Tr::V *fN, int32_t *sexp_out) {
+    using V = typename Tr::V;
+    constexpr int NS = 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *S = reinterpret_cast<V *>(smem_raw);  // [NS][nxi*nxi]
+    V *Q = S + NS * nxi * nxi;               // [NS][3*nxi*nxi]
+    const int sl = threadIdx.x % NS, slice = threadIdx.x / NS, nslice = blockDim.x / NS;
+    const int w0 = blockIdx.x * NS;  // first site of this CTA within the wave
+    const int nent = nxi * nxi;
+    // load + scale: one warp per site
+    for (int s = threadIdx.x >> 5; s < NS; s += blockDim.x >> 5) {
+        int lane = threadIdx.x & 31;
+        int cfg, t, site;
+        bool live = item_site(F, wv, wv.item0 + w0 + s, cfg, t, site);
+        int64_t base = live ? cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * 144 : 0;
+        double2 sv[5];
+        double amax = 0.0;
+        for (int q = 0; q < 5; ++q) {
+            int e = lane + 32 * q;
+            sv[q] = make_double2(0, 0);
+            if (live && e < nent) {
+                sv[q] = load_prop(F, base, (e / nxi) * 12 + (e % nxi));
+                amax = fmax(amax, fmax(fabs(sv[q].x), fabs(sv[q].y)));
+            }
+        }
+        int se = 0;
+        if (sizeof(V) == sizeof(float2)) {
+            for (int off = 16; off > 0; off >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+            se = amax > 0.0 ? -ilogb(amax) : 0;
+        }
+        for (int q = 0; q < 5; ++q) {
+            int e = lane + 32 * q;
+            if (e < nent) S[s * nent + e] = Tr::from_d(make_double2(scalbn(sv[q].x, se), scalbn(sv[q].y, se)));
+        }
+        if (lane == 0) sexp_out[w0 + s] = se;
+    }
+    __syncthreads();
+    for (int e = slice; e < 3 * nent; e += nslice) {
+        int c = e / nent, r = e % nent;
+        Q[sl * 3 * nent + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
+    }
+    __syncthreads();
+    const V *Ss = S + sl * nent;
+    const V *Qs = Q + sl * 3 * nent;
+    const int per_spin = npair * nxi;
+    for (int b = 0; b < 2; ++b) {
+        if (b == 0 ? !need_p : !need_n) continue;
+        V *out = b == 0 ? fP : fN;
+        for (int e = slice; e < block_size; e += nslice) {
+            int dl = e / per_spin, r = e % per_spin;
+            int pr = r / nxi, single = r % nxi;
+            int i = c_pair_i[pr], j = c_pair_j[pr];
+            V acc{0, 0};
+            for (int c = 0; c < 3; ++c) {
+                const V *Sr = Ss + (3 * dl + c) * nxi;
+                if (b == 0) {
+                    acc = cfma(Sr[i], Qs[(c * nxi + j) * nxi + single], acc);
+                    acc = csub(acc, cmul(Sr[j], Qs[(c * nxi + i) * nxi + single]));
+                } else {
+                    acc = cfma(Sr[i], Qs[(c * nxi + single) * nxi + j], acc);
+                    acc = csub(acc, cmul(Sr[j], Qs[(c * nxi + single) * nxi + i]));
+                }
+            }
+            out[(int64_t)e * wv.W + w0 + sl] = acc;
+        }
+    }
+}
+
+// One recursion step (eq. recr_F) for a whole wave. Work item = (z chunk,
+// 32-site group), site group fastest so that concurrent warps share list
+// entries and nearby rows of X.
+template <class Tr>
+__global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__ opx, const uint16_t *__restrict__ opy,
+                                                    int64_t n_z, int64_t k, int64_t zchunk, int W,
+                                                    const typename Tr::V *__restrict__ X,
+                                                    const typename Tr::V *__restrict__ Y, typename Tr::V *__restrict__ Z) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int ngroups = W >> 5;
+    const int64_t nchunks = (n_z + zchunk - 1) / zchunk;
+    for (int64_t item = warp_global; item < nchunks * ngroups; item += nwarps) {
+        const int64_t chunk = item / ngroups;
+        const int col = (int)(item % ngroups) * 32 + lane;
+        const int64_t z_begin = chunk * zchunk;
+        const int64_t z_end = min(n_z, z_begin + zchunk);
+        const int64_t o_begin = z_begin * k, o_end = z_end * k;
+        typename Tr::Acc acc;
+        acc.zero();
+        int64_t z = z_begin;
+        int64_t next_flush = o_begin + k;
+        for (int64_t ob = o_begin; ob < o_end; ob += 32) {
+            uint32_t mx = 0;
+            uint32_t my = 0;
+            if (ob + lane < o_end) {
+                mx = __ldg(opx + ob + lane);
+                my = __ldg(opy + ob + lane);
+            }
+            const int nb = (int)min((int64_t)32, o_end - ob);
+            for (int t = 0; t < nb; ++t) {
+                uint32_t x = __shfl_sync(0xffffffffu, mx, t);
+                uint32_t y = __shfl_sync(0xffffffffu, my, t);
+                acc.fma(X[(int64_t)x * W + col], Y[(int64_t)(y & 0x7fffu) * W + col], (y & 0x8000u) << 16);
+                if (ob + t + 1 == next_flush) {
+                    Z[z * W + col] = acc.store();
+                    acc.zero();
+                    ++z;
+                    next_flush += k;
+                }
+            }
+        }
+    }
+}
+
+// Contraction with L (eq. C_final) in FP64: lanes = sites, warps = components.
+template <class Tr>
+__global__ void __launch_bounds__(256) k_large_contract(const int64_t *__restrict__ fin_off,
+                                                        const uint32_t *__restrict__ fin_z,
+                                                        const double *__restrict__ fin_l, int n_comp, int W,
+                                                        const typename Tr::V *__restrict__ FA,
+                                                        const int32_t *__restrict__ sexp, int A, double inv_norm,
+                                                        double2 *__restrict__ Cout) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int ngroups = W >> 5;
+    for (int64_t item = warp_global; item < (int64_t)n_comp * ngroups; item += nwarps) {
+        const int c = (int)(item / ngroups);
+        const int col = (int)(item % ngroups) * 32 + lane;
+        double re = 0.0, im = 0.0;
+        for (int64_t e = fin_off[c]; e < fin_off[c + 1]; ++e) {
+            double2 f = Tr::to_d(FA[(int64_t)__ldg(fin_z + e) * W + col]);
+            double l = __ldg(fin_l + e);
+            re = __fma_rn(l, f.x, re);
+            im = __fma_rn(l, f.y, im);
+        }
+        int ue = -3 * A * sexp[col];
+        Cout[(int64_t)c * W + col] = make_double2(scalbn(re * inv_norm, ue), scalbn(im * inv_norm, ue));
+    }
+}
+
+// Momentum phases and the fixed-order sum over each 32-site group: one CTA
+// per group, partial[tile][mom][comp].
+__global__ void __launch_bounds__(256) k_large_sitesum(FieldDesc F, WaveDesc wv, MomDesc M, int n_comp,
+                                                       const double2 *__restrict__ C, double2 *__restrict__ partial) {
+    __shared__ double2 ph[32 * kMaxMom];
+    const int g = blockIdx.x;
+    for (int i = threadIdx.x; i < 32 * M.n_mom; i += blockDim.x) {
+        int s = i / M.n_mom, q = i % M.n_mom;
+        int cfg, t, site;
+        bool live = item_site(F, wv, wv.item0 + g * 32 + s, cfg, t, site);
+        double2 p = make_double2(0, 0);
+        if (live) {
+            int x = site % F.lx, y = (site / F.lx) % F.ly, z = site / (F.lx * F.ly);
+            p = mom_phase(M.mom[q], x, y, z, F.lx, F.ly, F.lz);
+        }
+        ph[i] = p;
+    }
+    __syncthreads();
+    const int64_t tile = (wv.item0 >> 5) + g;
+    for (int o = threadIdx.x; o < M.n_mom * n_comp; o += blockDim.x) {
+        int q = o / n_comp, c = o % n_comp;
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < 32; ++s) {
+            double2 p = ph[s * M.n_mom + q], cv = C[(int64_t)c * wv.W + g * 32 + s];
+            re += p.x * cv.x - p.y * cv.y;
+            im += p.x * cv.y + p.y * cv.x;
+        }
+        partial[tile * (int64_t)(M.n_mom * n_comp) + o] = make_double2(re, im);
+    }
+}
+
+// Final reduction over the tiles of each slab (Neumaier-compensated, fixed
+// order): out[cfg][list][t - t0][mom][comp_stride].
+__global__ void k_reduce_tiles(const double2 *__restrict__ partial, int64_t n_slabs, int tiles_per_slab, int n_mom,
+                               int n_comp, int n_t, int list_idx, int n_lists, int comp_stride, double2 *out) {
+    const int64_t per_slab = (int64_t)n_mom * n_comp;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_slabs * per_slab;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slab = o / per_slab;
+        const int r = (int)(o % per_slab);
+        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+        for (int tl = 0; tl < tiles_per_slab; ++tl) {
+            double2 v = partial[(slab * tiles_per_slab + tl) * per_slab + r];
+            double t = sr + v.x;
+            cr += fabs(sr) >= fabs(v.x) ? (sr - t) + v.x : (v.x - t) + sr;
+            sr = t;
+            t = si + v.y;
+            ci += fabs(si) >= fabs(v.y) ? (si - t) + v.y : (v.y - t) + si;
+            si = t;
+        }
+        const int cfg = (int)(slab / n_t), tt = (int)(slab % n_t);
+        const int q = r / n_comp, c = r % n_comp;
+        int64_t oi = ((((int64_t)cfg * n_lists + list_idx) * n_t + tt) * n_mom + q) * comp_stride + c;
+        out[oi] = make_double2(sr + cr, si + ci);
+    }
+}
+
+}  // namespace mbc

@@ -1,0 +1,58 @@
+// Internal layout of a term list, shared by the host builder and the CUDA
+// contraction. Not part of the public ABI (include/mbc.h).
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/mbc.h"
+
+namespace mbc {
+
+// One step F^(m) -> F^(m+1) of the F_- recursion (Sec. 4 eq. recr_F).
+// Output components z (compact index at stage m+1) each have exactly
+// k operations (all splits of a needed key, Sec. 3/7), stored z-major:
+// op j of z at z * k + j. x indexes stage m (for m = 1 it is the block
+// index of the first baryon), y the block of the added baryon, and the sign
+// sgn(x|y) of eq. antis_product_2 sits in bit 15 of ys.
+struct Step {
+    int baryon = 0;          // MBC_PROTON or MBC_NEUTRON
+    int64_t n_x = 0;         // size of the input stage (block size for m = 1)
+    int64_t n_z = 0;         // size of the output stage
+    int64_t k = 0;           // operations per output component
+    std::vector<uint32_t> x; // n_z * k
+    std::vector<uint16_t> ys;
+};
+
+struct DeviceCache;  // defined by the CUDA side
+
+}  // namespace mbc
+
+struct mbc_term_list {
+    int A = 0, n_p = 0, n_n = 0, dim = 4, n_sources = 1;
+    int8_t path[MBC_MAX_A] = {0};
+    bool pauli_forbidden = false;
+    int nxi = 12;             // source spinor-colour values used (3 * dim)
+    int64_t block_size = 0;   // dim * C(nxi, 2) * nxi
+    bool need_block[2] = {false, false};
+    std::vector<mbc::Step> steps;        // A - 1 steps
+    int64_t final_size = 0;              // components of F^(A) kept
+    int32_t n_comp = 0;
+    std::vector<int8_t> comp_snk, comp_src;     // n_comp * A
+    // contraction with L (eq. C_final): entries of component c at
+    // [fin_off[c], fin_off[c+1]): F^(A) index and integer L value
+    std::vector<int64_t> fin_off;
+    std::vector<uint32_t> fin_z;
+    std::vector<int64_t> fin_l;
+    double norm = 1.0;
+    mbc_list_stats stats{};
+    // device copies, one per device ordinal, created on first use
+    std::mutex dev_mu;
+    std::vector<mbc::DeviceCache *> dev;
+};
+
+namespace mbc {
+// Implemented by the CUDA side; releases the device copies of a list.
+void free_device_cache(mbc_term_list *list);
+}  // namespace mbc

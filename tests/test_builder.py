@@ -1,0 +1,132 @@
+"""Host-side tests of libmbc (no GPU needed): the term-list builder against the
+paper's counts and the oracle's independent pruning, the ABI surface and its
+argument checks."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT, read_golden, spins_of
+from oracle import counts, recursion
+
+mbc = pytest.importorskip("paper_1301_4895_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1301_4895_gb300 import _build
+    _build.build()
+    mbc.load()
+
+
+def test_library_exports_every_declared_symbol():
+    with open(os.path.join(ROOT, "include", "mbc.h")) as f:
+        header = f.read()
+    names = set(re.findall(r"\b(mbc_[a-z_0-9]+)\s*\(", header))
+    assert {"mbc_build_term_list", "mbc_contract", "mbc_term_list_stats", "mbc_free_term_list"} <= names
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_1301_4895_gb300", "libmbc.so"))
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("name,D", [("table1_rel_all.txt", 4), ("table2_nonrel_all.txt", 2)])
+def test_all_component_counts(name, D):
+    for row in read_golden(name):
+        n_p, n_n, ops = int(row[0]), int(row[1]), int(row[2])
+        if ops > 6e8:
+            continue  # (2,3) and (3,3) need several GB of list
+        tl = mbc.build_term_list(n_p, n_n, D)
+        st = tl.stats()
+        assert st["n_ops_total"] == ops, row
+        assert st["n_comp"] == counts.multinomial(n_p, D - n_p) ** 2 * counts.multinomial(n_n, D - n_n) ** 2
+        tl.free()
+
+
+@pytest.mark.parametrize("name,D", [("table4_nonrel_spin.txt", 2), ("table5_rel_spin.txt", 4)])
+def test_single_component_counts(name, D):
+    for row in read_golden(name):
+        n_p, n_n, ops = int(row[0]), int(row[1]), int(row[3])
+        if ops > 3e8:
+            continue
+        sp = spins_of(row[2])
+        tl = mbc.build_term_list(n_p, n_n, D, spins=[(sp, sp)])
+        st = tl.stats()
+        assert st["n_ops_total"] == ops, row
+        assert tl.n_l(0) == int(row[4]), row
+        tl.free()
+
+
+def test_bounds_and_dense_cases():
+    for n_p, n_n, D in ((1, 1, 2), (2, 1, 2), (2, 2, 2), (1, 2, 4), (0, 3, 4)):
+        st = mbc.build_term_list(n_p, n_n, D).stats()
+        path = "".join("P" if b == 0 else "N" for b in st["path"])
+        np_ = nn_ = 0
+        for m, b in enumerate(path):
+            np_ += b == "P"
+            nn_ += b == "N"
+            assert st["stage_bound"][m] == counts.p_bound(np_, nn_, D)
+            assert st["stage_size"][m] <= st["stage_bound"][m]
+            if m + 1 < len(path):
+                nxt = path[m + 1]
+                assert st["q_bound"][m] == counts.q_bound(np_, nn_, D, nxt)
+                assert st["n_ops"][m] <= st["q_bound"][m]
+    st = mbc.build_term_list(2, 2, 2).stats()
+    assert st["n_ops"] == st["q_bound"]  # nothing to prune for nonrelativistic 4He
+
+
+def test_stage_sizes_agree_with_oracle_pruning():
+    """Two independent implementations of the backward pruning (Sec. 3)."""
+    for n_p, n_n, D, sp in ((1, 1, 2, None), (2, 1, 2, None), (2, 2, 2, None), (1, 1, 4, None),
+                            (2, 2, 4, (0, 1, 0, 1)), (1, 2, 4, (0, 0, 1))):
+        spins = None if sp is None else [(sp, sp)]
+        tl = mbc.build_term_list(n_p, n_n, D, spins=spins)
+        st = tl.stats()
+        plan = recursion.Plan(n_p, n_n, D, requests=None if sp is None else [(sp, sp)])
+        tot, per, stages = plan.ops()
+        assert st["n_ops_total"] == tot
+        assert st["n_ops"] == per
+        assert st["stage_size"] == stages
+        assert sorted(tl.components()) == sorted(plan.requests)
+
+
+@pytest.mark.slow
+def test_headline_lists():
+    st = mbc.build_term_list(2, 2, 4).stats()
+    assert st["n_ops_total"] == 531321120 and st["n_comp"] == 1296
+    sp = (0, 1, 2, 3, 0, 1, 2, 3)
+    st = mbc.build_term_list(4, 4, 4, spins=[(sp, sp)]).stats()
+    assert st["n_ops_total"] == 448496928
+    assert st["stage_size"] == [3168, 196020, 813120, 245025, 813120, 196020, 3168, 1]
+
+
+def test_paper_path_rule():
+    assert mbc.build_term_list(2, 1, 2).stats()["path"] == [0, 0, 1]
+    assert mbc.build_term_list(1, 2, 2).stats()["path"] == [1, 1, 0]
+    assert mbc.build_term_list(1, 1, 2).stats()["path"] == [1, 0]
+    st = mbc.build_term_list(1, 1, 2, path=[0, 1]).stats()
+    assert st["path"] == [0, 1] and st["n_ops_total"] == 2664
+
+
+def test_pauli_forbidden_and_invalid_specs():
+    tl = mbc.build_term_list(0, 3, 2)
+    assert tl.pauli_forbidden and tl.stats()["n_comp"] == 0 and tl.stats()["n_ops_total"] == 0
+    tl = mbc.build_term_list(0, 2, 2, spins=[((0, 0), (0, 1))])  # repeated sink spin
+    assert tl.stats()["n_comp"] == 1 and tl.n_l(0) == 0
+    with pytest.raises(mbc.MbcError):
+        mbc.build_term_list(1, 1, 3)
+    with pytest.raises(mbc.MbcError):
+        mbc.build_term_list(0, 0, 4)
+    with pytest.raises(mbc.MbcError):
+        mbc.build_term_list(1, 1, 2, path=[0, 0])
+    with pytest.raises(mbc.MbcError):
+        mbc.build_term_list(1, 1, 2, n_sources=2)
+
+
+def test_contract_rejects_bad_arguments_before_any_device_work():
+    import numpy as np
+    tl = mbc.build_term_list(1, 1, 2)
+    with pytest.raises(ValueError):
+        mbc.contract(np.zeros((1, 1, 1, 1, 1, 12, 11), dtype=np.complex128), [tl])
+    lib = mbc.load()
+    assert lib.mbc_contract(None, None, 0, None, None, None) == 1
