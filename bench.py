@@ -331,7 +331,7 @@ def main():
     roof_mx = {"bound": "alu", "achieved": ach32 / 1e12 if ach32 else None, "peak": nominal32 / 1e12,
                "unit": "TFLOP/s", "frac": (ach32 / nominal32) if ach32 else None,
                "peak_kind": "FP32 vector, derived: 152 SMs x 128 FFMA/clk x max SM clock",
-               "measured_fma_peak": probe32 / 1e12, "kernel": "k_small<MIXED>",
+               "measured_fma_peak": probe32 / 1e12, "kernel": "k_small_ls<Mixed>",
                "kernel_ms_per_step": kmx / args.steps}
     line = {
         "metric": "sink-site correlators/s", "value": value, "unit": "sink-site correlators/s", "n_gpus": world,
@@ -346,7 +346,7 @@ def main():
                   "dtype": "f32 products, float-float accumulation, f64 contraction", "roofline": roof_mx},
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": int(2 * len(lists) * args.steps),
+        "gpu_launches": int((1 + 2 * len(lists)) * args.steps),
         "n_ops": [st["n_ops_total"] for st in stats],
     }
     if not args.no_cpu_baseline:

@@ -41,17 +41,20 @@ int64_t binom64(int n, int k) {
     return r;
 }
 
-// lanes per output component for a rectangular step (n_z outputs, k terms)
-int pick_group(int64_t n_z, int64_t k) {
+// Lanes per output component for a rectangular step (n_z outputs, k terms)
+// in the warp-per-site kernel: minimise warp-instructions on the FP64 pipe,
+// rounds * (ceil(k/g) * 4 DFMA + log2(g) * 2 DADD for the shuffle tree).
+int pick_group(int64_t n_z, int64_t k, double c_op = 4.0, double c_level = 2.0) {
     int best = 1;
-    double best_eff = -1.0;
-    for (int g = 1; g <= 32; g <<= 1) {
+    double best_cost = 1e300;
+    int lg = 0;
+    for (int g = 1; g <= 32; g <<= 1, ++lg) {
         int64_t per = 32 / g;
         int64_t rounds = (n_z + per - 1) / per;
         int64_t kk = (k + g - 1) / g;
-        double eff = (double)(n_z * k) / (double)(32 * rounds * std::max<int64_t>(kk, 1));
-        if (eff > best_eff + 1e-9) {
-            best_eff = eff;
+        double cost = (double)rounds * ((double)kk * c_op + lg * c_level);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
             best = g;
         }
     }
@@ -89,6 +92,7 @@ struct DeviceCache {
     SmallPlan sp{};          // device pointers filled in
     int64_t site_entries = 0;
     uint32_t *d_small_ops = nullptr;
+    uint32_t *d_small_zops = nullptr;
     // large path
     std::vector<uint32_t *> d_opx;
     std::vector<uint16_t *> d_opy;
@@ -106,6 +110,7 @@ void free_cache(DeviceCache *c) {
     cudaGetDevice(&prev);
     if (c->device >= 0) cudaSetDevice(c->device);
     cudaFree(c->d_small_ops);
+    cudaFree(c->d_small_zops);
     for (auto p : c->d_opx) cudaFree(p);
     for (auto p : c->d_opy) cudaFree(p);
     cudaFree(c->d_fin_off);
@@ -167,6 +172,7 @@ bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries) {
     for (auto *b : order) top = std::max(top, b->off + b->size);
     site_entries = (top + 1) & ~int64_t(1);
     P.site_entries = (int)site_entries;
+    P.part_off = (int)site_entries;  // lanes-are-sites kernel: 64 partial rows after the site region
     P.s_off = (int)Sb.off;
     P.q_off = (int)Qb.off;
     for (int b = 0; b < 2; ++b) P.blk_off[b] = P.need_blk[b] ? (int)blk[b].off : 0;
@@ -216,14 +222,39 @@ DeviceCache *get_cache(const mbc_term_list *Lc, int device, mbc_status &st) {
     // small-kernel plan and packed ops
     c->small_ok = !L->pauli_forbidden && plan_small(L, c->sp, c->site_entries);
     if (c->small_ok) {
+        // per step: [round j][z][sub], padded to a whole number of rounds
         std::vector<uint32_t> packed;
-        for (auto &s : L->steps)
-            for (size_t i = 0; i < s.x.size(); ++i)
-                packed.push_back(s.x[i] | ((uint32_t)(s.ys[i] & 0x7fffu) << 16) | ((uint32_t)(s.ys[i] >> 15) << 31));
+        for (size_t m = 0; m < L->steps.size(); ++m) {
+            const Step &s = L->steps[m];
+            SmallStepDesc &d = c->sp.step[m];
+            d.op_off = (int64_t)packed.size();
+            const int64_t g = d.g, kk = (s.k + g - 1) / g;
+            packed.resize(packed.size() + (size_t)(kk * s.n_z * g), 0u);
+            uint32_t *dst = packed.data() + d.op_off;
+            for (int64_t z = 0; z < s.n_z; ++z)
+                for (int64_t j = 0; j < s.k; ++j) {
+                    size_t i = (size_t)(z * s.k + j);
+                    uint32_t op = s.x[i] | ((uint32_t)(s.ys[i] & 0x7fffu) << 16) | ((uint32_t)(s.ys[i] >> 15) << 31);
+                    dst[((j / g) * s.n_z + z) * g + (j % g)] = op;
+                }
+        }
         if ((st = upload(&c->d_small_ops, packed.data(), packed.size())) != MBC_OK) {
             free_cache(c);
             return nullptr;
         }
+        // lanes-are-sites layout: z-major
+        std::vector<uint32_t> zpk;
+        for (size_t m = 0; m < L->steps.size(); ++m) {
+            const Step &s = L->steps[m];
+            c->sp.step[m].zop_off = (int64_t)zpk.size();
+            for (size_t i = 0; i < s.x.size(); ++i)
+                zpk.push_back(s.x[i] | ((uint32_t)(s.ys[i] & 0x7fffu) << 16) | ((uint32_t)(s.ys[i] >> 15) << 31));
+        }
+        if ((st = upload(&c->d_small_zops, zpk.data(), zpk.size())) != MBC_OK) {
+            free_cache(c);
+            return nullptr;
+        }
+        c->sp.zops = c->d_small_zops;
         c->sp.ops = c->d_small_ops;
         c->sp.fin_off = c->d_fin_off;
         c->sp.fin_z = c->d_fin_z;
@@ -306,29 +337,56 @@ int sm_count(int device) {
 
 // ---- launchers -------------------------------------------------------------
 
-template <class Tr>
-mbc_status run_small(const DeviceCache *c, const FieldDesc &F, const MomDesc &M, const mbc_tune *tune, int device,
-                     cudaStream_t stream, double2 *partial_out, int64_t &n_tiles, int &tiles_per_slab, int &T) {
-    using V = typename Tr::V;
+// Small-stage kernels. FP64: one warp per site (k_small). MIXED: 32 sites
+// per CTA, lanes are sites (k_small_ls). A call with partial_out == nullptr
+// only sizes the launch (tiles and scratch).
+struct SmallLaunch {
+    bool ok = false;
+    int T = 0;            // sites per tile
+    int threads = 0;
+    size_t smem = 0;
+    int tiles_per_slab = 0;
+    int64_t n_tiles = 0;
+};
+
+SmallLaunch size_small(const DeviceCache *c, const FieldDesc &F, const MomDesc &M, const mbc_tune *tune,
+                       bool mixed) {
+    SmallLaunch l;
     const SmallPlan &P = c->sp;
-    const int64_t per_site = c->site_entries * (int64_t)sizeof(V) + 16LL * (P.n_comp + M.n_mom);
-    T = (int)std::min<int64_t>(32, kSmemLimit / per_site);
-    if (tune && tune->sites_per_cta > 0) T = std::min(T, tune->sites_per_cta);
-    if (T < 1) return MBC_ERR_UNSUPPORTED;
-    const size_t smem = (size_t)T * per_site;
+    if (!mixed) {
+        const int64_t per_site = c->site_entries * 16LL + 16LL * P.n_comp;
+        l.T = (int)std::min<int64_t>(32, kSmemLimit / per_site);
+        if (tune && tune->sites_per_cta > 0) l.T = std::min(l.T, tune->sites_per_cta);
+        l.threads = 32 * l.T;
+        l.smem = (size_t)l.T * per_site;
+    } else {
+        l.T = 32;
+        l.smem = (size_t)(c->site_entries + 64) * 32 * sizeof(float2);
+        l.threads = (tune && tune->threads_per_cta > 0) ? tune->threads_per_cta : 1024;
+        l.threads = std::max(64, std::min(1024, l.threads / 32 * 32));
+        if (l.smem > (size_t)kSmemLimit - 1024) return l;
+    }
+    if (l.T < 1) return l;
     const int v3 = F.lx * F.ly * F.lz;
-    tiles_per_slab = (v3 + T - 1) / T;
-    n_tiles = (int64_t)F.n_cfg * F.n_t * tiles_per_slab;
-    if (!partial_out) return MBC_OK;  // sizing query
-    MBC_CUDA_TRY(cudaFuncSetAttribute(k_small<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    l.tiles_per_slab = (v3 + l.T - 1) / l.T;
+    l.n_tiles = (int64_t)F.n_cfg * F.n_t * l.tiles_per_slab;
+    l.ok = true;
+    return l;
+}
+
+mbc_status run_small(const DeviceCache *c, const FieldDesc &F, const MomDesc &M, const SmallLaunch &l, bool mixed,
+                     int device, cudaStream_t stream, const double2 *phase, double2 *partial_out) {
+    const SmallPlan &P = c->sp;
+    auto kern = mixed ? k_small_ls<MixedTraits> : k_small<FP64Traits>;
+    MBC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem));
     int per_sm = 0;
-    MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small<Tr>, 32 * T, smem));
+    MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, l.threads, l.smem));
     if (per_sm < 1) return MBC_ERR_UNSUPPORTED;
-    int64_t grid = std::min<int64_t>(n_tiles, (int64_t)per_sm * sm_count(device));
+    int64_t grid = std::min<int64_t>(l.n_tiles, (int64_t)per_sm * sm_count(device));
     if (grid < 1) return MBC_OK;
     {
         TimedLaunch tl(stream);
-        k_small<Tr><<<(unsigned)grid, 32 * T, smem, stream>>>(P, F, M, partial_out, n_tiles, tiles_per_slab);
+        kern<<<(unsigned)grid, l.threads, l.smem, stream>>>(P, F, M, phase, partial_out, l.n_tiles, l.tiles_per_slab);
     }
     MBC_CUDA_TRY(cudaGetLastError());
     return MBC_OK;
@@ -364,7 +422,7 @@ size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 template <class Tr>
 mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDesc &F, const MomDesc &M,
                      const mbc_tune *tune, int device, cudaStream_t stream, char *scratch, double2 *partial,
-                     const LargeSizes &ls, int64_t n_items, int v3p) {
+                     const LargeSizes &ls, int64_t n_items, int v3p, const double2 *phase) {
     using V = typename Tr::V;
     const int W = ls.W;
     char *p = scratch;
@@ -426,7 +484,7 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
         }
         {
             int64_t groups = std::min<int64_t>(W, n_items - item0) / 32;
-            k_large_sitesum<<<(unsigned)groups, 256, 0, stream>>>(F, wv, M, L->n_comp, Cb, partial);
+            k_large_sitesum<<<(unsigned)groups, 256, 0, stream>>>(F, wv, M, L->n_comp, phase, Cb, partial);
             MBC_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -527,56 +585,76 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     const int64_t n_slabs = (int64_t)props->n_cfg * n_t;
     const bool mixed = opts->precision == MBC_MIXED;
 
+    // plan every list: regime, launch shape, scratch bytes
+    struct ListRun {
+        DeviceCache *c = nullptr;
+        bool skip = true, small = false;
+        SmallLaunch sl;
+        LargeSizes ls{};
+        size_t need = 0, pbytes = 0;
+    };
+    const int v3p = (int)((v3 + 31) / 32 * 32);
+    const int64_t n_items = n_slabs * v3p;
+    const int regime = opts->tune ? opts->tune->regime : 0;
+    std::vector<ListRun> runs((size_t)n_lists);
+    size_t max_need = 0;
     for (int li = 0; li < n_lists; ++li) {
         const mbc_term_list *L = lists[li];
+        ListRun &r = runs[(size_t)li];
         if (L->pauli_forbidden || L->n_comp == 0) continue;  // identically zero
-        DeviceCache *c = get_cache(L, device, st);
-        if (!c) return st;
-        const int regime = opts->tune ? opts->tune->regime : 0;
-        bool small = c->small_ok && regime != 2;
-        if (regime == 1 && !c->small_ok) return MBC_ERR_UNSUPPORTED;
-        if (small) {
-            int64_t n_tiles = 0;
-            int tps = 0, T = 0;
-            st = mixed ? run_small<MixedTraits>(c, F, M, opts->tune, device, stream, nullptr, n_tiles, tps, T)
-                       : run_small<FP64Traits>(c, F, M, opts->tune, device, stream, nullptr, n_tiles, tps, T);
-            if (st != MBC_OK) small = false;
-            else {
-                void *scr = nullptr;
-                size_t pbytes = (size_t)n_tiles * M.n_mom * L->n_comp * sizeof(double2);
-                if ((st = scratch_get(device, stream, pbytes, &scr)) != MBC_OK) return st;
-                double2 *partial = reinterpret_cast<double2 *>(scr);
-                st = mixed ? run_small<MixedTraits>(c, F, M, opts->tune, device, stream, partial, n_tiles, tps, T)
-                           : run_small<FP64Traits>(c, F, M, opts->tune, device, stream, partial, n_tiles, tps, T);
-                if (st != MBC_OK) return st;
-                int64_t outs = n_slabs * M.n_mom * L->n_comp;
-                unsigned grid = (unsigned)std::min<int64_t>((outs + 255) / 256, 65535);
-                k_reduce_tiles<<<std::max(grid, 1u), 256, 0, stream>>>(partial, n_slabs, tps, M.n_mom, L->n_comp,
-                                                                      n_t, li, n_lists, comp_max,
-                                                                      reinterpret_cast<double2 *>(dev_out));
-                MBC_CUDA_TRY(cudaGetLastError());
-                continue;
-            }
+        r.skip = false;
+        r.c = get_cache(L, device, st);
+        if (!r.c) return st;
+        if (regime == 1 && !r.c->small_ok) return MBC_ERR_UNSUPPORTED;
+        if (r.c->small_ok && regime != 2) {
+            r.sl = size_small(r.c, F, M, opts->tune, mixed);
+            r.small = r.sl.ok;
         }
-        // large-stage path
-        const int v3p = (int)((v3 + 31) / 32 * 32);
-        const int64_t n_items = n_slabs * v3p;
-        LargeSizes ls = mixed ? large_sizes<MixedTraits>(L, c, opts->tune, n_items)
-                              : large_sizes<FP64Traits>(L, c, opts->tune, n_items);
-        const size_t pbytes = (size_t)(n_items / 32) * M.n_mom * L->n_comp * sizeof(double2);
-        const size_t need = align256(pbytes) + 2 * align256(ls.blk_bytes) + 2 * align256(ls.stage_bytes) +
-                            align256(ls.c_bytes) + align256(ls.sexp_bytes);
-        void *scr = nullptr;
-        if ((st = scratch_get(device, stream, need, &scr)) != MBC_OK) return st;
-        double2 *partial = reinterpret_cast<double2 *>(scr);
-        char *rest = reinterpret_cast<char *>(scr) + align256(pbytes);
-        st = mixed ? run_large<MixedTraits>(L, c, F, M, opts->tune, device, stream, rest, partial, ls, n_items, v3p)
-                   : run_large<FP64Traits>(L, c, F, M, opts->tune, device, stream, rest, partial, ls, n_items, v3p);
-        if (st != MBC_OK) return st;
+        if (regime == 1 && !r.small) return MBC_ERR_UNSUPPORTED;
+        if (r.small) {
+            r.pbytes = (size_t)r.sl.n_tiles * M.n_mom * L->n_comp * sizeof(double2);
+            r.need = align256(r.pbytes);
+        } else {
+            r.ls = mixed ? large_sizes<MixedTraits>(L, r.c, opts->tune, n_items)
+                         : large_sizes<FP64Traits>(L, r.c, opts->tune, n_items);
+            r.pbytes = (size_t)(n_items / 32) * M.n_mom * L->n_comp * sizeof(double2);
+            r.need = align256(r.pbytes) + 2 * align256(r.ls.blk_bytes) + 2 * align256(r.ls.stage_bytes) +
+                     align256(r.ls.c_bytes) + align256(r.ls.sexp_bytes);
+        }
+        max_need = std::max(max_need, r.need);
+    }
+    const size_t phase_bytes = align256((size_t)v3 * M.n_mom * sizeof(double2));
+    void *scr = nullptr;
+    if ((st = scratch_get(device, stream, phase_bytes + max_need, &scr)) != MBC_OK) return st;
+    double2 *phase = reinterpret_cast<double2 *>(scr);
+    {
+        unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((v3 * M.n_mom + 255) / 256, 4096));
+        k_phase_table<<<grid, 256, 0, stream>>>(F, M, phase);
+        MBC_CUDA_TRY(cudaGetLastError());
+    }
+    char *rest = reinterpret_cast<char *>(scr) + phase_bytes;
+    for (int li = 0; li < n_lists; ++li) {
+        const mbc_term_list *L = lists[li];
+        ListRun &r = runs[(size_t)li];
+        if (r.skip) continue;
+        double2 *partial = reinterpret_cast<double2 *>(rest);
+        int tiles_per_slab;
+        if (r.small) {
+            if ((st = run_small(r.c, F, M, r.sl, mixed, device, stream, phase, partial)) != MBC_OK) return st;
+            tiles_per_slab = r.sl.tiles_per_slab;
+        } else {
+            char *bufs = rest + align256(r.pbytes);
+            st = mixed ? run_large<MixedTraits>(L, r.c, F, M, opts->tune, device, stream, bufs, partial, r.ls, n_items,
+                                                v3p, phase)
+                       : run_large<FP64Traits>(L, r.c, F, M, opts->tune, device, stream, bufs, partial, r.ls, n_items,
+                                               v3p, phase);
+            if (st != MBC_OK) return st;
+            tiles_per_slab = v3p / 32;
+        }
         int64_t outs = n_slabs * M.n_mom * L->n_comp;
         unsigned grid = (unsigned)std::min<int64_t>((outs + 255) / 256, 65535);
-        k_reduce_tiles<<<std::max(grid, 1u), 256, 0, stream>>>(partial, n_slabs, v3p / 32, M.n_mom, L->n_comp, n_t,
-                                                              li, n_lists, comp_max,
+        k_reduce_tiles<<<std::max(grid, 1u), 256, 0, stream>>>(partial, n_slabs, tiles_per_slab, M.n_mom, L->n_comp,
+                                                              n_t, li, n_lists, comp_max,
                                                               reinterpret_cast<double2 *>(dev_out));
         MBC_CUDA_TRY(cudaGetLastError());
     }
@@ -649,8 +727,8 @@ extern "C" mbc_status mbc_fma_probe(int32_t precision, double *flops) {
     int device = 0;
     MBC_CUDA_TRY(cudaGetDevice(&device));
     const int nsm = sm_count(device);
-    const int threads = 256, blocks = nsm * 8;
-    const int iters = precision == MBC_FP64 ? 4096 : 65536;
+    const int threads = 256, blocks = nsm * 4;
+    const int iters = precision == MBC_FP64 ? 1024 : 16384;
     void *buf = nullptr;
     MBC_CUDA_TRY(cudaMalloc(&buf, (size_t)threads * blocks * sizeof(double)));
     cudaEvent_t a, b;
@@ -677,3 +755,4 @@ extern "C" mbc_status mbc_fma_probe(int32_t precision, double *flops) {
     *flops = 2.0 * 8.0 * iters * (double)threads * blocks / (best * 1e-3);
     return MBC_OK;
 }
+

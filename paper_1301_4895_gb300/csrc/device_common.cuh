@@ -44,37 +44,42 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 
 struct MixedTraits {
     using V = float2;
+    // Kahan-compensated FP32 accumulation of FP32 complex products: value =
+    // s - c, where c carries the rounding lost by the running sum s.
     struct Acc {
-        float hr, hi, lr, li;  // high and low words of re and im
-        __device__ __forceinline__ void zero() { hr = hi = lr = li = 0.f; }
+        float sr, si, cr, ci;
+        __device__ __forceinline__ void zero() { sr = si = cr = ci = 0.f; }
+        __device__ __forceinline__ static void kahan(float &s, float &c, float p) {
+            float y = __fsub_rn(p, c);
+            float t = __fadd_rn(s, y);
+            c = __fsub_rn(__fsub_rn(t, s), y);
+            s = t;
+        }
         __device__ __forceinline__ void fma(float2 x, float2 y, uint32_t neg) {
             float xr = __int_as_float(__float_as_int(x.x) ^ (int)neg);
             float xi = __int_as_float(__float_as_int(x.y) ^ (int)neg);
-            float pr = __fmaf_rn(xr, y.x, -__fmul_rn(xi, y.y));
-            float pi = __fmaf_rn(xr, y.y, __fmul_rn(xi, y.x));
+            kahan(sr, cr, __fmaf_rn(xr, y.x, -__fmul_rn(xi, y.y)));
+            kahan(si, ci, __fmaf_rn(xr, y.y, __fmul_rn(xi, y.x)));
+        }
+        // combine with another accumulator (s2 - c2): two-sum of the sums
+        __device__ __forceinline__ void add(float s2r, float c2r, float s2i, float c2i) {
             float s, e;
-            two_sum(hr, pr, s, e);
-            hr = s;
-            lr = __fadd_rn(lr, e);
-            two_sum(hi, pi, s, e);
-            hi = s;
-            li = __fadd_rn(li, e);
+            two_sum(sr, s2r, s, e);
+            sr = s;
+            cr = __fsub_rn(__fadd_rn(cr, c2r), e);
+            two_sum(si, s2i, s, e);
+            si = s;
+            ci = __fsub_rn(__fadd_rn(ci, c2i), e);
         }
         __device__ __forceinline__ void add_shfl(unsigned mask, int off) {
-            float ohr = __shfl_xor_sync(mask, hr, off), olr = __shfl_xor_sync(mask, lr, off);
-            float ohi = __shfl_xor_sync(mask, hi, off), oli = __shfl_xor_sync(mask, li, off);
-            float s, e;
-            two_sum(hr, ohr, s, e);
-            hr = s;
-            lr = __fadd_rn(__fadd_rn(lr, olr), e);
-            two_sum(hi, ohi, s, e);
-            hi = s;
-            li = __fadd_rn(__fadd_rn(li, oli), e);
+            float a = __shfl_xor_sync(mask, sr, off), b = __shfl_xor_sync(mask, cr, off);
+            float c = __shfl_xor_sync(mask, si, off), d = __shfl_xor_sync(mask, ci, off);
+            add(a, b, c, d);
         }
         __device__ __forceinline__ double2 value() const {
-            return make_double2((double)hr + (double)lr, (double)hi + (double)li);
+            return make_double2((double)sr - (double)cr, (double)si - (double)ci);
         }
-        __device__ __forceinline__ V store() const { return make_float2(__fadd_rn(hr, lr), __fadd_rn(hi, li)); }
+        __device__ __forceinline__ V store() const { return make_float2(__fsub_rn(sr, cr), __fsub_rn(si, ci)); }
     };
     __device__ __forceinline__ static double2 to_d(V v) { return make_double2(v.x, v.y); }
     __device__ __forceinline__ static V from_d(double2 v) { return make_float2((float)v.x, (float)v.y); }
@@ -97,9 +102,12 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
     return make_float2(__fmaf_rn(a.x, b.x, __fmaf_rn(-a.y, b.y, c.x)), __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, c.y)));
 }
-template <class V>
-__device__ __forceinline__ V cneg_if(V a, int s) {
-    return s < 0 ? V{-a.x, -a.y} : a;
+// c - a * b with fused multiply-adds only
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+    return make_double2(__fma_rn(-a.x, b.x, __fma_rn(a.y, b.y, c.x)), __fma_rn(-a.x, b.y, __fma_rn(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
+    return make_float2(__fmaf_rn(-a.x, b.x, __fmaf_rn(a.y, b.y, c.x)), __fmaf_rn(-a.x, b.y, __fmaf_rn(-a.y, b.x, c.y)));
 }
 
 // ---- the G tensor (eq. def_g) in factorised form -----------------------------
@@ -121,8 +129,8 @@ __device__ __forceinline__ V diquark(const V *S, int ld, int nxi, int n_g2, int 
         int s2 = c_g2[g][0], s3 = c_g2[g][1], v = c_g2[g][2];
         for (int e = 0; e < 2; ++e) {
             int c2 = c_eps[c][e][0], c3 = c_eps[c][e][1], sg = c_eps[c][e][2] * v;
-            V t = cmul(S[(3 * s2 + c2) * ld + x2], S[(3 * s3 + c3) * ld + x3]);
-            acc = sg > 0 ? cadd(acc, t) : csub(acc, t);
+            const V a = S[(3 * s2 + c2) * ld + x2], b = S[(3 * s3 + c3) * ld + x3];
+            acc = sg > 0 ? cfma(a, b, acc) : cfms(a, b, acc);
         }
     }
     return acc;

@@ -93,10 +93,10 @@ __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, 
                 const V *Sr = Ss + (3 * dl + c) * nxi;
                 if (b == 0) {
                     acc = cfma(Sr[i], Qs[(c * nxi + j) * nxi + single], acc);
-                    acc = csub(acc, cmul(Sr[j], Qs[(c * nxi + i) * nxi + single]));
+                    acc = cfms(Sr[j], Qs[(c * nxi + i) * nxi + single], acc);
                 } else {
                     acc = cfma(Sr[i], Qs[(c * nxi + single) * nxi + j], acc);
-                    acc = csub(acc, cmul(Sr[j], Qs[(c * nxi + single) * nxi + i]));
+                    acc = cfms(Sr[j], Qs[(c * nxi + single) * nxi + i], acc);
                 }
             }
             out[(int64_t)e * wv.W + w0 + sl] = acc;
@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(256) k_large_contract(const int64_t *__restric
 // Momentum phases and the fixed-order sum over each 32-site group: one CTA
 // per group, partial[tile][mom][comp].
 __global__ void __launch_bounds__(256) k_large_sitesum(FieldDesc F, WaveDesc wv, MomDesc M, int n_comp,
+                                                       const double2 *__restrict__ phase,
                                                        const double2 *__restrict__ C, double2 *__restrict__ partial) {
     __shared__ double2 ph[32 * kMaxMom];
     const int g = blockIdx.x;
@@ -187,12 +188,7 @@ __global__ void __launch_bounds__(256) k_large_sitesum(FieldDesc F, WaveDesc wv,
         int s = i / M.n_mom, q = i % M.n_mom;
         int cfg, t, site;
         bool live = item_site(F, wv, wv.item0 + g * 32 + s, cfg, t, site);
-        double2 p = make_double2(0, 0);
-        if (live) {
-            int x = site % F.lx, y = (site / F.lx) % F.ly, z = site / (F.lx * F.ly);
-            p = mom_phase(M.mom[q], x, y, z, F.lx, F.ly, F.lz);
-        }
-        ph[i] = p;
+        ph[i] = live ? __ldg(phase + (int64_t)site * M.n_mom + q) : make_double2(0, 0);
     }
     __syncthreads();
     const int64_t tile = (wv.item0 >> 5) + g;
@@ -201,8 +197,8 @@ __global__ void __launch_bounds__(256) k_large_sitesum(FieldDesc F, WaveDesc wv,
         double re = 0.0, im = 0.0;
         for (int s = 0; s < 32; ++s) {
             double2 p = ph[s * M.n_mom + q], cv = C[(int64_t)c * wv.W + g * 32 + s];
-            re += p.x * cv.x - p.y * cv.y;
-            im += p.x * cv.y + p.y * cv.x;
+            re = __fma_rn(p.x, cv.x, __fma_rn(-p.y, cv.y, re));
+            im = __fma_rn(p.x, cv.y, __fma_rn(p.y, cv.x, im));
         }
         partial[tile * (int64_t)(M.n_mom * n_comp) + o] = make_double2(re, im);
     }

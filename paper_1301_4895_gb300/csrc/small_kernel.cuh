@@ -26,7 +26,8 @@ constexpr int kSmallMaxComp = 64;
 
 struct SmallStepDesc {
     int32_t n_z, k, g, x_off, y_off, z_off;
-    int64_t op_off;
+    int64_t op_off;   // warp-per-site layout [round][z][sub-lane]
+    int64_t zop_off;  // lanes-are-sites layout: z-major, k ops per z
 };
 
 struct SmallPlan {
@@ -39,6 +40,8 @@ struct SmallPlan {
     int32_t fin_g;                      // lanes per component in the contraction
     SmallStepDesc step[16];
     const uint32_t *ops;                // packed: x | y << 16 | sign << 31
+    const uint32_t *zops;               // the same ops, z-major
+    int32_t part_off;                   // lanes-are-sites: split partials (64 entries)
     const int64_t *fin_off;             // n_comp + 1
     const uint32_t *fin_z;
     const double *fin_l;                // integer L values
@@ -78,6 +81,8 @@ __device__ __forceinline__ double2 mom_phase(const int32_t *n, int x, int y, int
     return make_double2(c, s);
 }
 
+// Ops of a step are stored as [round j][z][sub-lane]: in round j the g lanes
+// of output z read ops j*g + sub, so a warp reads 32 consecutive words.
 template <class Tr>
 __device__ __forceinline__ void small_step(const SmallPlan &P, const SmallStepDesc &d, typename Tr::V *R,
                                            int lane) {
@@ -89,20 +94,20 @@ __device__ __forceinline__ void small_step(const SmallPlan &P, const SmallStepDe
     const int g = d.g;                 // lanes per z (power of two)
     const int per = 32 / g;            // z per round
     const int sub = lane & (g - 1);
-    const int kk = (d.k + g - 1) / g;  // ops per lane
+    const int64_t round_stride = (int64_t)d.n_z * g;
     const unsigned full = 0xffffffffu;
     for (int z0 = 0; z0 < d.n_z; z0 += per) {
         int z = z0 + lane / g;
         typename Tr::Acc acc;
         acc.zero();
         if (z < d.n_z) {
-            const uint32_t *oz = ops + (int64_t)z * d.k;
-            for (int j = 0; j < kk; ++j) {
-                int jj = j * g + sub;
-                if (jj < d.k) {
-                    uint32_t op = __ldg(oz + jj);
-                    acc.fma(X[op & 0xffffu], Y[(op >> 16) & 0x7fffu], op & 0x80000000u);
-                }
+            const uint32_t *oz = ops + z * g + sub;
+            const int rs = (int)round_stride;
+            const int jfull = (d.k - sub + g - 1) / g;  // rounds in which this lane has an op
+#pragma unroll 4
+            for (int j = 0; j < jfull; ++j) {
+                uint32_t op = __ldg(oz + j * rs);
+                acc.fma(X[op & 0xffffu], Y[(op >> 16) & 0x7fffu], op & 0x80000000u);
             }
         }
         for (int off = g >> 1; off > 0; off >>= 1) acc.add_shfl(full, off);
@@ -136,10 +141,10 @@ __device__ __forceinline__ void small_blocks(const SmallPlan &P, typename Tr::V 
                 const V *Sr = S + (3 * dl + c) * nxi;
                 if (b == 0) {  // proton: u pair (i, j) at slots 1, 2; d = single at slot 3
                     acc = cfma(Sr[i], Q[(c * nxi + j) * nxi + single], acc);
-                    acc = csub(acc, cmul(Sr[j], Q[(c * nxi + i) * nxi + single]));
+                    acc = cfms(Sr[j], Q[(c * nxi + i) * nxi + single], acc);
                 } else {  // neutron: d pair (i, k=j) at slots 1, 3; u = single at slot 2
                     acc = cfma(Sr[i], Q[(c * nxi + single) * nxi + j], acc);
-                    acc = csub(acc, cmul(Sr[j], Q[(c * nxi + single) * nxi + i]));
+                    acc = cfms(Sr[j], Q[(c * nxi + single) * nxi + i], acc);
                 }
             }
             F[e] = acc;
@@ -148,16 +153,27 @@ __device__ __forceinline__ void small_blocks(const SmallPlan &P, typename Tr::V 
     __syncwarp();
 }
 
+// Phase table of one slab geometry: tab[site][mom] = exp(-2 pi i n.x / L).
+__global__ void k_phase_table(FieldDesc F, MomDesc M, double2 *tab) {
+    const int v3 = F.lx * F.ly * F.lz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v3 * M.n_mom; i += gridDim.x * blockDim.x) {
+        int site = i / M.n_mom, q = i % M.n_mom;
+        int x = site % F.lx, y = (site / F.lx) % F.ly, z = site / (F.lx * F.ly);
+        tab[i] = mom_phase(M.mom[q], x, y, z, F.lx, F.ly, F.lz);
+    }
+}
+
+// Shared-memory kernel, one warp per site (FP64 path).
 template <class Tr>
 __global__ void __launch_bounds__(1024, 1)
-    k_small(SmallPlan P, FieldDesc F, MomDesc M, double2 *partial, int64_t n_tiles, int tiles_per_slab) {
+    k_small(SmallPlan P, FieldDesc F, MomDesc M, const double2 *__restrict__ phase, double2 *partial,
+            int64_t n_tiles, int tiles_per_slab) {
     using V = typename Tr::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int T = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     V *R = reinterpret_cast<V *>(smem_raw) + (int64_t)warp * P.site_entries;
     double2 *Cs = reinterpret_cast<double2 *>(reinterpret_cast<V *>(smem_raw) + (int64_t)T * P.site_entries);
-    double2 *Ph = Cs + T * P.n_comp;  // [T][n_mom]
     const int V3 = F.lx * F.ly * F.lz;
     const int nxi = P.nxi;
 
@@ -169,33 +185,15 @@ __global__ void __launch_bounds__(1024, 1)
         const bool live = site < V3;
         if (live) {
             const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * 144;
-            // 1. propagator tile (+ exact power-of-two scaling for MIXED)
-            double2 sv[5];
-            double amax = 0.0;
-            int nent = nxi * nxi;
-            for (int q = 0; q < 5; ++q) {
-                int e = lane + 32 * q;
-                sv[q] = make_double2(0, 0);
-                if (e < nent) {
-                    sv[q] = load_prop(F, base, (e / nxi) * 12 + (e % nxi));
-                    amax = fmax(amax, fmax(fabs(sv[q].x), fabs(sv[q].y)));
-                }
-            }
-            int sexp = 0;
-            if (sizeof(V) == sizeof(float2)) {
-                for (int off = 16; off > 0; off >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-                sexp = amax > 0.0 ? -ilogb(amax) : 0;
-            }
-            for (int q = 0; q < 5; ++q) {
-                int e = lane + 32 * q;
-                if (e < nent) R[P.s_off + e] = Tr::from_d(make_double2(scalbn(sv[q].x, sexp), scalbn(sv[q].y, sexp)));
-            }
+            // 1. propagator tile
+            const int nent = nxi * nxi;
+            for (int e = lane; e < nent; e += 32) R[P.s_off + e] = Tr::from_d(load_prop(F, base, (e / nxi) * 12 + (e % nxi)));
             __syncwarp();
             // 2. blocks
             small_blocks<Tr>(P, R, lane);
             // 3. recursion
             for (int m = 0; m < P.n_steps; ++m) small_step<Tr>(P, P.step[m], R, lane);
-            // 4. contraction with L, FP64, undo the scaling
+            // 4. contraction with L, FP64
             const V *FA = R + P.fin_off_buf;
             const int g = P.fin_g, per = 32 / g, sub = lane & (g - 1);
             for (int c0 = 0; c0 < P.n_comp; c0 += per) {
@@ -213,32 +211,274 @@ __global__ void __launch_bounds__(1024, 1)
                     re += __shfl_xor_sync(0xffffffffu, re, off);
                     im += __shfl_xor_sync(0xffffffffu, im, off);
                 }
-                if (c < P.n_comp && sub == 0) {
-                    int ue = -3 * P.A * sexp;
-                    Cs[warp * P.n_comp + c] = make_double2(scalbn(re * P.inv_norm, ue), scalbn(im * P.inv_norm, ue));
-                }
+                if (c < P.n_comp && sub == 0) Cs[warp * P.n_comp + c] = make_double2(re, im);
             }
-            // phases of this site
-            int x = site % F.lx, y = (site / F.lx) % F.ly, z = site / (F.lx * F.ly);
-            for (int q = lane; q < M.n_mom; q += 32) Ph[warp * M.n_mom + q] = mom_phase(M.mom[q], x, y, z, F.lx, F.ly, F.lz);
         } else {
             for (int c = lane; c < P.n_comp; c += 32) Cs[warp * P.n_comp + c] = make_double2(0, 0);
-            for (int q = lane; q < M.n_mom; q += 32) Ph[warp * M.n_mom + q] = make_double2(0, 0);
         }
         __syncthreads();
-        // tile partial: sum over the T sites in a fixed order
+        // tile partial: (1/N) sum over the T sites, in a fixed order, of phase * C
+        const int site0 = tin * T;
         for (int o = threadIdx.x; o < M.n_mom * P.n_comp; o += blockDim.x) {
             int q = o / P.n_comp, c = o % P.n_comp;
             double re = 0.0, im = 0.0;
-            for (int w = 0; w < T; ++w) {
-                double2 ph = Ph[w * M.n_mom + q], cv = Cs[w * P.n_comp + c];
-                re += ph.x * cv.x - ph.y * cv.y;
-                im += ph.x * cv.y + ph.y * cv.x;
+            for (int w = 0; w < T && site0 + w < V3; ++w) {
+                double2 ph = __ldg(phase + (int64_t)(site0 + w) * M.n_mom + q), cv = Cs[w * P.n_comp + c];
+                re = __fma_rn(ph.x, cv.x, __fma_rn(-ph.y, cv.y, re));
+                im = __fma_rn(ph.x, cv.y, __fma_rn(ph.y, cv.x, im));
             }
-            partial[tile * (int64_t)(M.n_mom * P.n_comp) + o] = make_double2(re, im);
+            partial[tile * (int64_t)(M.n_mom * P.n_comp) + o] = make_double2(re * P.inv_norm, im * P.inv_norm);
         }
         __syncthreads();
     }
+}
+
+// ---- lanes-are-sites kernel (mixed path) -------------------------------------
+// A CTA owns a tile of 32 sites, lane l of every warp works on site l; all
+// per-site values are rows of 32 lanes in shared memory ([entry][lane], 8 B
+// per lane), so every access of a warp is one conflict-free row. The warps
+// split the output components of each step (warp-uniform op stream, loaded
+// cooperatively and broadcast by shuffles); steps with fewer outputs than
+// warps split each output's terms over several warps and combine the
+// compensated partials in a fixed order.
+
+// RN(d * 2^e) as FP32 from the bits of an FP64 value, integer operations only
+// (GB300's FP64 pipe is 1/64 of FP32). Results below the FP32 normal range
+// flush to zero; inputs here are scaled to |d| < 2.
+__device__ __forceinline__ float f64_scaled_to_f32(double d, int e) {
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const uint32_t sign = hi & 0x80000000u;
+    const int eb = (int)((hi >> 20) & 0x7ffu);
+    const int ef = eb - 1023 + e + 127;
+    if (eb == 0 || ef <= 0) return __int_as_float((int)sign);
+    const uint32_t top = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rem = lo & 0x1fffffffu;
+    const uint32_t up = (rem > 0x10000000u) || (rem == 0x10000000u && (top & 1u));
+    return __int_as_float((int)(sign | (((uint32_t)ef << 23) + top + up)));
+}
+__device__ __forceinline__ int f64_exponent(double d) {
+    const uint32_t hi = (uint32_t)__double2hiint(d);
+    const int eb = (int)((hi >> 20) & 0x7ffu);
+    return eb == 0 ? -100000 : eb - 1023;
+}
+__device__ __forceinline__ float f32_scaled(float f, int e) {
+    const uint32_t b = (uint32_t)__float_as_int(f);
+    const int eb = (int)((b >> 23) & 0xffu);
+    const int en = eb + e;
+    if (eb == 0 || en <= 0) return __int_as_float((int)(b & 0x80000000u));
+    return __int_as_float((int)((b & 0x807fffffu) | ((uint32_t)en << 23)));
+}
+__device__ __forceinline__ int f32_exponent(float f) {
+    const int eb = (int)(((uint32_t)__float_as_int(f) >> 23) & 0xffu);
+    return eb == 0 ? -100000 : eb - 127;
+}
+
+template <class Tr>
+__global__ void __launch_bounds__(1024, 1)
+    k_small_ls(SmallPlan P, FieldDesc F, MomDesc M, const double2 *__restrict__ phase, double2 *partial,
+               int64_t n_tiles, int tiles_per_slab) {
+    using V = typename Tr::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *R = reinterpret_cast<V *>(smem_raw);  // [entry][32]
+    __shared__ int sexp_s[32];
+    const int NW = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int V3 = F.lx * F.ly * F.lz;
+    const int nxi = P.nxi, nent = nxi * nxi;
+    const unsigned full = 0xffffffffu;
+#define ROW(e) R[(int64_t)(e) * 32 + lane]
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t slab = tile / tiles_per_slab;
+        const int tin = (int)(tile % tiles_per_slab);
+        const int cfg = (int)(slab / F.n_t), t = F.t0 + (int)(slab % F.n_t);
+        const int site0 = tin * 32;
+        __syncthreads();  // the previous tile is done with shared memory
+        // 1. load and scale: one warp per site
+        for (int s = warp; s < 32; s += NW) {
+            const int site = site0 + s;
+            const bool live = site < V3;
+            const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * 144;
+            int emax = -100000;
+            float2 fv[5];
+            double2 dv[5];
+            for (int q = 0; q < 5; ++q) {
+                const int e = lane + 32 * q;
+                const int idx = (e / nxi) * 12 + (e % nxi);
+                if (live && e < nent) {
+                    if (F.dtype == 0) {
+                        dv[q] = __ldg(reinterpret_cast<const double2 *>(F.s) + base + idx);
+                        emax = max(emax, max(f64_exponent(dv[q].x), f64_exponent(dv[q].y)));
+                    } else {
+                        fv[q] = __ldg(reinterpret_cast<const float2 *>(F.s) + base + idx);
+                        emax = max(emax, max(f32_exponent(fv[q].x), f32_exponent(fv[q].y)));
+                    }
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(full, emax, off));
+            const int se = emax == -100000 ? 0 : -emax;  // largest entry scaled into [1, 2)
+            for (int q = 0; q < 5; ++q) {
+                const int e = lane + 32 * q;
+                if (e < nent) {
+                    float2 v = make_float2(0.f, 0.f);
+                    if (live) {
+                        if (F.dtype == 0)
+                            v = make_float2(f64_scaled_to_f32(dv[q].x, se), f64_scaled_to_f32(dv[q].y, se));
+                        else
+                            v = make_float2(f32_scaled(fv[q].x, se), f32_scaled(fv[q].y, se));
+                    }
+                    R[(int64_t)(P.s_off + e) * 32 + s] = V{v.x, v.y};
+                }
+            }
+            if (lane == 0) sexp_s[s] = se;
+        }
+        __syncthreads();
+        // 2. diquark and blocks (Sec. 2); lane = site
+        for (int e = warp; e < 3 * nent; e += NW) {
+            const int c = e / nent, r = e % nent, x2 = r / nxi, x3 = r % nxi;
+            V acc{0, 0};
+            for (int gg = 0; gg < P.n_g2; ++gg) {
+                const int s2 = c_g2[gg][0], s3 = c_g2[gg][1], v = c_g2[gg][2];
+                for (int q = 0; q < 2; ++q) {
+                    const int c2 = c_eps[c][q][0], c3 = c_eps[c][q][1], sg = c_eps[c][q][2] * v;
+                    const V a = ROW(P.s_off + (3 * s2 + c2) * nxi + x2), b = ROW(P.s_off + (3 * s3 + c3) * nxi + x3);
+                    acc = sg > 0 ? cfma(a, b, acc) : cfms(a, b, acc);
+                }
+            }
+            ROW(P.q_off + e) = acc;
+        }
+        __syncthreads();
+        const int per_spin = P.npair * nxi;
+        for (int b = 0; b < 2; ++b) {
+            if (!P.need_blk[b]) continue;
+            for (int e = warp; e < P.block_size; e += NW) {
+                const int dl = e / per_spin, r = e % per_spin;
+                const int pr = r / nxi, single = r % nxi;
+                const int i = c_pair_i[pr], j = c_pair_j[pr];
+                V acc{0, 0};
+                for (int c = 0; c < 3; ++c) {
+                    const int sr = P.s_off + (3 * dl + c) * nxi;
+                    if (b == 0) {
+                        acc = cfma(ROW(sr + i), ROW(P.q_off + (c * nxi + j) * nxi + single), acc);
+                        acc = cfms(ROW(sr + j), ROW(P.q_off + (c * nxi + i) * nxi + single), acc);
+                    } else {
+                        acc = cfma(ROW(sr + i), ROW(P.q_off + (c * nxi + single) * nxi + j), acc);
+                        acc = cfms(ROW(sr + j), ROW(P.q_off + (c * nxi + single) * nxi + i), acc);
+                    }
+                }
+                ROW(P.blk_off[b] + e) = acc;
+            }
+        }
+        __syncthreads();
+        // 3. recursion
+        for (int m = 0; m < P.n_steps; ++m) {
+            const SmallStepDesc &d = P.step[m];
+            const uint32_t *ops = P.zops + d.zop_off;
+            const int split = d.n_z < NW ? NW / d.n_z : 1;  // CTA-uniform
+            int64_t o_begin, o_end, zb;
+            int part = -1;
+            if (split <= 1) {
+                zb = (int64_t)warp * d.n_z / NW;
+                const int64_t ze = (int64_t)(warp + 1) * d.n_z / NW;
+                o_begin = zb * d.k;
+                o_end = ze * d.k;
+            } else {
+                const int u = warp;  // unit = (z, part)
+                if (u < d.n_z * split) {
+                    zb = u / split;
+                    part = u % split;
+                    o_begin = zb * d.k + (int64_t)part * d.k / split;
+                    o_end = zb * d.k + (int64_t)(part + 1) * d.k / split;
+                } else {
+                    zb = 0;
+                    o_begin = o_end = 0;
+                }
+            }
+            typename Tr::Acc acc;
+            acc.zero();
+            // 32-bit lane pointers: row e of lane l sits at R[e * 32 + l]
+            const V *Xl = R + (d.x_off << 5) + lane;
+            const V *Yl = R + (d.y_off << 5) + lane;
+            V *Zl = R + (d.z_off << 5) + lane;
+            int z = (int)zb;
+            int left = part < 0 ? d.k : 0x7fffffff;  // ops until the next output is complete
+            const int n_ops = (int)(o_end - o_begin);
+            const uint32_t *ob_ptr = ops + o_begin;
+            int done = 0;
+            for (; done + 32 <= n_ops; done += 32) {
+                const uint32_t mine = __ldg(ob_ptr + done + lane);
+#pragma unroll 8
+                for (int q = 0; q < 32; ++q) {
+                    const uint32_t op = __shfl_sync(full, mine, q);
+                    acc.fma(Xl[(op & 0xffffu) << 5], Yl[((op >> 16) & 0x7fffu) << 5], op & 0x80000000u);
+                    if (--left == 0) {
+                        Zl[z << 5] = acc.store();
+                        acc.zero();
+                        ++z;
+                        left = d.k;
+                    }
+                }
+            }
+            if (done < n_ops) {
+                const int nb = n_ops - done;
+                const uint32_t mine = lane < nb ? __ldg(ob_ptr + done + lane) : 0u;
+                for (int q = 0; q < nb; ++q) {
+                    const uint32_t op = __shfl_sync(full, mine, q);
+                    acc.fma(Xl[(op & 0xffffu) << 5], Yl[((op >> 16) & 0x7fffu) << 5], op & 0x80000000u);
+                    if (--left == 0) {
+                        Zl[z << 5] = acc.store();
+                        acc.zero();
+                        ++z;
+                        left = d.k;
+                    }
+                }
+            }
+            if (split > 1) {
+                if (part >= 0) {
+                    ROW(P.part_off + 2 * warp) = V{acc.sr, acc.cr};
+                    ROW(P.part_off + 2 * warp + 1) = V{acc.si, acc.ci};
+                }
+                __syncthreads();
+                for (int zz = warp; zz < d.n_z; zz += NW) {
+                    typename Tr::Acc a;
+                    a.zero();
+                    for (int pp = 0; pp < split; ++pp) {
+                        const V r0 = ROW(P.part_off + 2 * (zz * split + pp));
+                        const V r1 = ROW(P.part_off + 2 * (zz * split + pp) + 1);
+                        a.add(r0.x, r0.y, r1.x, r1.y);
+                    }
+                    ROW(d.z_off + zz) = a.store();
+                }
+            }
+            __syncthreads();
+        }
+        // 4. contraction with L in FP64, undo the scaling, phase, sum over the
+        //    32 sites of the tile by a fixed xor tree
+        const int site = site0 + lane;
+        const bool live = site < V3;
+        const int ue = -3 * P.A * sexp_s[lane];
+        for (int c = warp; c < P.n_comp; c += NW) {
+            double re = 0.0, im = 0.0;
+            for (int64_t e = P.fin_off[c]; e < P.fin_off[c + 1]; ++e) {
+                const double2 f = Tr::to_d(ROW(P.fin_off_buf + __ldg(P.fin_z + e)));
+                const double l = __ldg(P.fin_l + e);
+                re = __fma_rn(l, f.x, re);
+                im = __fma_rn(l, f.y, im);
+            }
+            re = live ? scalbn(re * P.inv_norm, ue) : 0.0;
+            im = live ? scalbn(im * P.inv_norm, ue) : 0.0;
+            for (int q = 0; q < M.n_mom; ++q) {
+                const double2 ph = live ? __ldg(phase + (int64_t)site * M.n_mom + q) : make_double2(0, 0);
+                double pr = __fma_rn(ph.x, re, -ph.y * im), pi = __fma_rn(ph.x, im, ph.y * re);
+                for (int off = 16; off > 0; off >>= 1) {
+                    pr += __shfl_xor_sync(full, pr, off);
+                    pi += __shfl_xor_sync(full, pi, off);
+                }
+                if (lane == 0) partial[tile * (int64_t)(M.n_mom * P.n_comp) + q * P.n_comp + c] = make_double2(pr, pi);
+            }
+        }
+    }
+#undef ROW
 }
 
 }  // namespace mbc
