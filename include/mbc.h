@@ -221,6 +221,46 @@ typedef struct {
 mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *const *lists, int32_t n_lists,
                         const mbc_contract_opts *opts, void *out, void *stream);
 
+/*
+ * mbc_contract without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc in steady
+ * state - for example code that runs between the set-up of a CUDA graph and
+ * its replays, services whose device memory is reserved up front by their
+ * own pool, or real-time loops that forbid allocator calls.
+ *
+ * Same arguments and output layout as mbc_contract with n_lists = 1:
+ * out is complex128 [n_cfg][1][t1 - t0][n_mom][max(1, n_comp)], device
+ * memory owned by the caller, written completely on each call.
+ * Supported: MBC_FP64, MBC_MEM_DEVICE, and lists that take the shared-memory
+ * kernel (the nonrelativistic nuclei); anything else returns
+ * MBC_ERR_UNSUPPORTED before touching the device.
+ *
+ * Scratch: one static device array of 8 MiB (MBC_NOALLOC_SCRATCH_BYTES)
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits. The momentum phase table (16 * L_x L_y L_z * n_mom bytes,
+ * rounded up to 256) plus the tile partials (16 * n_mom * n_comp bytes per
+ * tile of up to 32 sites) must fit; a larger request returns
+ * MBC_ERR_UNSUPPORTED before any device work.
+ *
+ * Preconditions and behaviour:
+ *   - the list must already have its device copy on the current device,
+ *     made by an earlier mbc_contract call with that list (that call may
+ *     allocate; do it during set-up); otherwise MBC_ERR_INVALID_ARG;
+ *   - the first call on a device looks up the device address of the static
+ *     array (cudaGetSymbolAddress, once per device, with that device current)
+ *     and loads the kernel constants; make that first call before any stream
+ *     capture begins;
+ *   - no cudaMalloc, cudaFree or other allocating routine is called;
+ *   - every call shares the one array and leaves the last call's contents in
+ *     it (nothing in it needs to start at zero: each entry is written before
+ *     it is read). Calls that overlap on the GPU - on different streams, or
+ *     from several host threads - race on the array and give wrong results:
+ *     serialise them.
+ */
+#define MBC_NOALLOC_SCRATCH_BYTES (8u << 20)
+mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_term_list *list, const mbc_contract_opts *opts,
+                                void *out, void *stream);
+
 /* Wait for the stream and report any deferred device-side status. */
 mbc_status mbc_sync_status(void *stream);
 

@@ -17,6 +17,7 @@ import numpy as np
 __all__ = [
     "MbcError", "load", "build_term_list", "TermList", "contract", "sync_status", "release_scratch",
     "FP64", "MIXED", "C128", "C64", "PROTON", "NEUTRON", "timing_enable", "timing_read", "fma_probe",
+    "contract_noalloc",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -103,6 +104,8 @@ def load(path: str | None = None):
         lib.mbc_contract.argtypes = [ctypes.POINTER(Props), ctypes.POINTER(V), ctypes.c_int32,
                                      ctypes.POINTER(ContractOpts), V, V]
         lib.mbc_contract.restype = ctypes.c_int
+        lib.mbc_contract_noalloc.argtypes = [ctypes.POINTER(Props), V, ctypes.POINTER(ContractOpts), V, V]
+        lib.mbc_contract_noalloc.restype = ctypes.c_int
         lib.mbc_sync_status.argtypes = [V]
         lib.mbc_sync_status.restype = ctypes.c_int
         lib.mbc_release_scratch.argtypes = []
@@ -264,6 +267,28 @@ def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0
     handles = (ctypes.c_void_p * len(lists))(*[tl.handle for tl in lists])
     rc = lib.mbc_contract(ctypes.byref(pr), handles, len(lists), ctypes.byref(op), optr, _stream_ptr(stream))
     _check(rc, "mbc_contract")
+    return out
+
+
+def contract_noalloc(field, term_list, out, moms=((0, 0, 0),), t0: int = 0, t1: int = 0, stream=None):
+    """``mbc_contract_noalloc``: FP64 contraction of one list into a
+    caller-allocated device tensor, with no device allocation inside the
+    library (its scratch is a static 8 MiB device array). The list must have
+    been used once with ``contract`` on this device. Returns ``out``."""
+    lib = load()
+    import torch
+    if field.dtype not in (torch.complex128, torch.complex64) or not field.is_contiguous():
+        raise ValueError("field must be a contiguous complex128/complex64 tensor")
+    if out.dtype != torch.complex128 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous complex128 tensor")
+    shape = tuple(field.shape)
+    n_cfg, nt, lz, ly, lx = shape[:5]
+    dtype = C128 if field.dtype == torch.complex128 else C64
+    moms = np.ascontiguousarray(np.array(moms, dtype=np.int32).reshape(-1, 3))
+    pr = Props(field.data_ptr(), field.data_ptr(), dtype, MEM_DEVICE, n_cfg, nt, lx, ly, lz, 0, 0)
+    op = ContractOpts(FP64, moms.shape[0], moms.ctypes.data, t0, t1, None)
+    _check(lib.mbc_contract_noalloc(ctypes.byref(pr), term_list.handle, ctypes.byref(op), out.data_ptr(),
+                                    _stream_ptr(stream)), "mbc_contract_noalloc")
     return out
 
 

@@ -756,3 +756,141 @@ extern "C" mbc_status mbc_fma_probe(int32_t precision, double *flops) {
     return MBC_OK;
 }
 
+// ---- contraction without allocation ------------------------------------------
+// Callers that must not allocate device memory in steady state (code running
+// between the set-up of a CUDA graph and its replays, services whose device
+// memory is fully reserved up front by their own pool, real-time loops) use
+// mbc_contract_noalloc. Its scratch - the momentum phase table and the
+// per-tile partial sums of the FP64 shared-memory kernel - lives in one
+// static device array of kStaticScratchBytes, which every GPU that loads the
+// library holds until the process exits.
+namespace {
+constexpr size_t kStaticScratchBytes = (size_t)8 << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+std::mutex g_static_mu;
+std::map<int, void *> g_static_addr;  // device ordinal -> device address of g_static_scratch
+
+// The host-side name of g_static_scratch is only a stand-in: the device
+// address comes from cudaGetSymbolAddress, once per device, with that device
+// current.
+mbc_status static_scratch_address(int device, void **ptr) {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    auto it = g_static_addr.find(device);
+    if (it != g_static_addr.end()) {
+        *ptr = it->second;
+        return MBC_OK;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        (void)cudaGetLastError();
+        return MBC_ERR_CUDA;
+    }
+    g_static_addr[device] = p;
+    *ptr = p;
+    return MBC_OK;
+}
+
+DeviceCache *find_cache(const mbc_term_list *Lc, int device) {
+    mbc_term_list *L = const_cast<mbc_term_list *>(Lc);
+    std::lock_guard<std::mutex> g(L->dev_mu);
+    return device < (int)L->dev.size() ? L->dev[(size_t)device] : nullptr;
+}
+}  // namespace
+
+extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_term_list *list,
+                                           const mbc_contract_opts *opts, void *out, void *stream_v) {
+    // ---- host-only checks: nothing below touches the device before they pass
+    if (!props || !list || !opts || !out || !props->s_u || !props->s_d) return MBC_ERR_INVALID_ARG;
+    if (props->s_u != props->s_d) return MBC_ERR_UNSUPPORTED;
+    if (props->memory != MBC_MEM_DEVICE || opts->precision != MBC_FP64) return MBC_ERR_UNSUPPORTED;
+    if (props->dtype != MBC_C128 && props->dtype != MBC_C64) return MBC_ERR_INVALID_ARG;
+    if (props->n_cfg < 1 || props->nt < 1 || props->lx < 1 || props->ly < 1 || props->lz < 1) return MBC_ERR_INVALID_ARG;
+    if (opts->n_mom < 1 || opts->n_mom > kMaxMom || !opts->mom) return MBC_ERR_INVALID_ARG;
+    const int t0 = opts->t0, t1 = opts->t1 == 0 ? props->nt : opts->t1;
+    if (t0 < 0 || t1 > props->nt || t1 <= t0) return MBC_ERR_INVALID_ARG;
+    const int64_t v3 = (int64_t)props->lx * props->ly * props->lz;
+    if (v3 > (1LL << 30)) return MBC_ERR_INVALID_ARG;
+    const int n_t = t1 - t0;
+    const int64_t n_slabs = (int64_t)props->n_cfg * n_t;
+    const int comp_max = std::max(1, (int)list->n_comp);
+    const size_t out_bytes = (size_t)n_slabs * opts->n_mom * comp_max * sizeof(double2);
+    SmallPlan hp;
+    int64_t site_entries = 0;
+    const bool zero = list->pauli_forbidden || list->n_comp == 0;
+    size_t phase_bytes = 0, part_bytes = 0;
+    int T = 0;
+    if (!zero) {
+        if (!plan_small(list, hp, site_entries)) return MBC_ERR_UNSUPPORTED;  // relativistic lists: no static variant
+        const int64_t per_site = site_entries * 16LL + 16LL * hp.n_comp;
+        T = (int)std::min<int64_t>(32, kSmemLimit / per_site);
+        if (opts->tune && opts->tune->sites_per_cta > 0) T = std::min(T, opts->tune->sites_per_cta);
+        if (T < 1) return MBC_ERR_UNSUPPORTED;
+        const int64_t tiles = n_slabs * ((v3 + T - 1) / T);
+        phase_bytes = align256((size_t)v3 * opts->n_mom * sizeof(double2));
+        part_bytes = (size_t)tiles * opts->n_mom * list->n_comp * sizeof(double2);
+        if (phase_bytes + part_bytes > kStaticScratchBytes) return MBC_ERR_UNSUPPORTED;  // beyond the 8 MiB array
+    }
+    // ---- device work: no allocation from here on
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_v);
+    int device = 0;
+    MBC_CUDA_TRY(cudaGetDevice(&device));
+    if (zero) {
+        MBC_CUDA_TRY(cudaMemsetAsync(out, 0, out_bytes, stream));
+        return MBC_OK;
+    }
+    DeviceCache *c = find_cache(list, device);
+    if (!c || !c->small_ok) return MBC_ERR_INVALID_ARG;  // the list's device copy must exist already
+    void *scr = nullptr;
+    mbc_status st = static_scratch_address(device, &scr);
+    if (st != MBC_OK) return st;
+    if ((st = ensure_constants(device)) != MBC_OK) return st;
+    const int64_t stride_t = props->stride_t ? props->stride_t : v3 * 144;
+    FieldDesc F;
+    F.s = props->s_u;
+    F.dtype = props->dtype == MBC_C128 ? 0 : 1;
+    F.n_cfg = props->n_cfg;
+    F.nt = props->nt;
+    F.lx = props->lx;
+    F.ly = props->ly;
+    F.lz = props->lz;
+    F.stride_t = stride_t;
+    F.stride_cfg = props->stride_cfg ? props->stride_cfg : stride_t * props->nt;
+    F.t0 = t0;
+    F.n_t = n_t;
+    MomDesc M;
+    std::memset(&M, 0, sizeof(M));
+    M.n_mom = opts->n_mom;
+    for (int q = 0; q < opts->n_mom; ++q)
+        for (int dd = 0; dd < 3; ++dd) M.mom[q][dd] = opts->mom[3 * q + dd];
+    double2 *phase = reinterpret_cast<double2 *>(scr);
+    double2 *partial = reinterpret_cast<double2 *>(reinterpret_cast<char *>(scr) + phase_bytes);
+    // every phase-table entry and every tile partial is written before it is
+    // read, so nothing in the shared array has to start at zero
+    unsigned pgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((v3 * M.n_mom + 255) / 256, 4096));
+    k_phase_table<<<pgrid, 256, 0, stream>>>(F, M, phase);
+    MBC_CUDA_TRY(cudaGetLastError());
+    SmallLaunch l;
+    l.T = T;
+    l.threads = 32 * T;
+    l.smem = (size_t)T * (c->site_entries * 16 + 16LL * c->sp.n_comp);
+    l.tiles_per_slab = (int)((v3 + T - 1) / T);
+    l.n_tiles = n_slabs * l.tiles_per_slab;
+    l.ok = true;
+    const SmallPlan &P = c->sp;
+    MBC_CUDA_TRY(cudaFuncSetAttribute(k_small<FP64Traits>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem));
+    int per_sm = 0;
+    MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small<FP64Traits>, l.threads, l.smem));
+    if (per_sm < 1) return MBC_ERR_UNSUPPORTED;
+    const int64_t grid = std::min<int64_t>(l.n_tiles, (int64_t)per_sm * sm_count(device));
+    k_small<FP64Traits><<<(unsigned)grid, l.threads, l.smem, stream>>>(P, F, M, phase, partial, l.n_tiles,
+                                                                     l.tiles_per_slab);
+    MBC_CUDA_TRY(cudaGetLastError());
+    const int64_t outs = n_slabs * M.n_mom * list->n_comp;
+    const unsigned rgrid = (unsigned)std::min<int64_t>((outs + 255) / 256, 65535);
+    k_reduce_tiles<<<std::max(rgrid, 1u), 256, 0, stream>>>(partial, n_slabs, l.tiles_per_slab, M.n_mom,
+                                                            list->n_comp, n_t, 0, 1, comp_max,
+                                                            reinterpret_cast<double2 *>(out));
+    MBC_CUDA_TRY(cudaGetLastError());
+    return MBC_OK;
+}
