@@ -41,6 +41,9 @@ WORKLOADS = {
                [(2, 2, 4, None)], (16, 16, 16), 32, 2, 0.4, "c128"),
     "be8": ("8Be relativistic (0,1,2,3,0,1,2,3), 16^3 x t-subset, complex64 storage, seed 4",
             [(4, 4, 4, [((0, 1, 2, 3, 0, 1, 2, 3), (0, 1, 2, 3, 0, 1, 2, 3))])], (16, 16, 16), 32, 4, 0.4, "c64"),
+    "batched": ("batched: pn, 3He, 4He nonrel + 4He rel (0,1,0,1), 24^3x48 per configuration, complex64, seed 3",
+                [(1, 1, 2, None), (2, 1, 2, None), (2, 2, 2, None), (2, 2, 4, [((0, 1, 0, 1), (0, 1, 0, 1))])],
+                (24, 24, 24), 48, 3, 0.4, "c64"),
 }
 
 
@@ -52,6 +55,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nonrel", choices=sorted(WORKLOADS))
     ap.add_argument("--nt", type=int, default=0, help="time slices (0: workload default)")
+    ap.add_argument("--cfgs", type=int, default=1, help="configurations per rank")
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -132,11 +139,11 @@ def measured_peaks():
     return {}
 
 
-def make_field(wl, cfg, nt):
+def make_field(wl, cfgs, nt):
     import synth
     _, _, dims, _, seed, lam, dt = wl
-    return synth.field(seed, cfg + 1, nt, dims, lam, dtype=np.complex64 if dt == "c64" else np.complex128,
-                       cfgs=[cfg])
+    return synth.field(seed, max(cfgs) + 1, nt, dims, lam, dtype=np.complex64 if dt == "c64" else np.complex128,
+                       cfgs=list(cfgs))
 
 
 def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0):
@@ -240,14 +247,33 @@ def main():
         nt = 1  # one time slice: 4096 sinks
     lists = [mbc.build_term_list(n_p, n_n, D, spins=spins) for (n_p, n_n, D, spins) in nuclei]
     stats = [tl.stats() for tl in lists]
-    field_np = make_field(wl, rank, nt)
+    field_np = make_field(wl, range(rank * args.cfgs, (rank + 1) * args.cfgs), nt)
     v3 = dims[0] * dims[1] * dims[2]
     field = torch.from_numpy(field_np).to(dev)
-    stream = torch.cuda.current_stream(dev)
-    units_per_step = v3 * nt * len(lists)
+    stream = torch.cuda.Stream(dev)
+    units_per_step = v3 * nt * len(lists) * args.cfgs
+    tunes = {0: None, 1: None}
+    if args.autotune:
+        from paper_1301_4895_gb300.autotune import autotune
+        for p in (0, 1):
+            tunes[p] = autotune(field, lists, precision=p, stream=stream)
+    graphs = {}
 
     def step(precision):
-        return mbc.contract(field, lists, precision=precision, stream=stream)
+        if not args.graph:
+            return mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision])
+        if precision not in graphs:
+            with torch.cuda.stream(stream):
+                out = mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision])
+            stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision], out=out)
+            graphs[precision] = (g, out)
+        g, out = graphs[precision]
+        with torch.cuda.stream(stream):
+            g.replay()
+        return out
 
     def barrier():
         if world > 1:
@@ -279,10 +305,14 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item()), kms, launches, out
 
+    nan = float("nan")
     with ClockSampler(local) as clk:
-        ms64, k64, n64, _ = timed(0, args.steps, args.warmup)
-        msmx, kmx, nmx, _ = timed(1, args.steps, args.warmup)
+        ms64, k64, n64 = (timed(0, args.steps, args.warmup)[:3] if args.precision in ("both", "fp64")
+                          else (nan, 0.0, 0))
+        msmx, kmx, nmx = (timed(1, args.steps, args.warmup)[:3] if args.precision in ("both", "mixed")
+                          else (nan, 0.0, 0))
     clocks = clk.summary()
+    primary = 0 if args.precision in ("both", "fp64") else 1
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
@@ -291,11 +321,11 @@ def main():
         pinned.copy_(torch.from_numpy(field_np))
         host = pinned.numpy()
         for _ in range(max(1, args.warmup)):
-            mbc.contract(host, lists, precision=0)
+            mbc.contract(host, lists, precision=primary)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            res = mbc.contract(host, lists, precision=0)
+            res = mbc.contract(host, lists, precision=primary)
             _ = complex(res.reshape(-1)[0])  # the step's result read on the host
         dt_s = time.perf_counter() - t0
         tt = torch.tensor([dt_s], dtype=torch.float64, device=dev)
@@ -309,41 +339,55 @@ def main():
     if rank != 0:
         return 0
 
-    value = units_per_step * world * args.steps / (ms64 * 1e-3)
+    value64 = units_per_step * world * args.steps / (ms64 * 1e-3)
     value_mx = units_per_step * world * args.steps / (msmx * 1e-3)
+    value = value64 if primary == 0 else value_mx
     # roofline of the dominant kernel (the contraction kernel; FP64 pipe)
     fl = [site_flops(st, n[2]) for st, n in zip(stats, nuclei)]
-    flops_step = sum(f["total"] for f in fl) * v3 * nt
+    flops_step = sum(f["total"] for f in fl) * v3 * nt * args.cfgs
     peaks = measured_peaks()
     probe64 = mbc.fma_probe(0)
     probe32 = mbc.fma_probe(1)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     nominal64 = 152 * 2 * 2 * sm_max * 1e6  # 2 DFMA / clk / SM (1.25 TFLOP/s class), 2 flop each
     nominal32 = 152 * 128 * 2 * sm_max * 1e6
-    ach64 = flops_step * args.steps / (k64 * 1e-3) if k64 > 0 else None
-    ach32 = flops_step * args.steps / (kmx * 1e-3) if kmx > 0 else None
-    roof = {"bound": "alu", "achieved": ach64 / 1e12 if ach64 else None, "peak": nominal64 / 1e12,
-            "unit": "TFLOP/s", "frac": (ach64 / nominal64) if ach64 else None, "traffic": None,
-            "peak_kind": "FP64 vector, derived: 152 SMs x 2 DFMA/clk x max SM clock",
-            "measured_fma_peak": probe64 / 1e12, "frac_of_measured_fma": (ach64 / probe64) if ach64 else None,
-            "kernel": "k_small<FP64>", "kernel_ms_per_step": k64 / args.steps, "launches_timed": n64,
-            "flops_per_step": flops_step}
-    roof_mx = {"bound": "alu", "achieved": ach32 / 1e12 if ach32 else None, "peak": nominal32 / 1e12,
-               "unit": "TFLOP/s", "frac": (ach32 / nominal32) if ach32 else None,
-               "peak_kind": "FP32 vector, derived: 152 SMs x 128 FFMA/clk x max SM clock",
-               "measured_fma_peak": probe32 / 1e12, "kernel": "k_small_ls<Mixed>",
-               "kernel_ms_per_step": kmx / args.steps}
+    has_small = any(n[2] == 2 for n in nuclei)
+    has_large = any(n[2] == 4 for n in nuclei)
+    kname = {0: " + ".join(k for k, on in (("k_small<FP64>", has_small), ("k_large_step<FP64>", has_large)) if on),
+             1: " + ".join(k for k, on in (("k_small_ls<Mixed>", has_small), ("k_large_step<Mixed>", has_large))
+                           if on)}
+
+    def roofline(kms, ms, launches, peak, probe, kind, prec):
+        # kernel time from the library's CUDA events; with graph replay those
+        # are not recorded and the whole step time is used instead
+        t_ms, basis = (kms, "kernel events") if kms > 0 else (ms, "whole step")
+        if not (t_ms == t_ms) or t_ms <= 0:
+            return None
+        ach = flops_step * args.steps / (t_ms * 1e-3)
+        return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_kind": kind, "measured_fma_peak": probe / 1e12,
+                "frac_of_measured_fma": ach / probe, "kernel": kname[prec], "time_basis": basis,
+                "kernel_ms_per_step": t_ms / args.steps, "launches_timed": launches, "flops_per_step": flops_step}
+
+    roof64 = roofline(k64, ms64, n64, nominal64, probe64, "FP64 vector, derived: 152 SMs x 2 DFMA/clk x max SM clock", 0)
+    roof_mx = roofline(kmx, msmx, nmx, nominal32, probe32,
+                       "FP32 vector, derived: 152 SMs x 128 FFMA/clk x max SM clock", 1)
+    roof = roof64 if primary == 0 else roof_mx
     line = {
         "metric": "sink-site correlators/s", "value": value, "unit": "sink-site correlators/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (ms64 if primary == 0 else msmx) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if primary == 0 else "f32+f64", "data": "synthetic",
         "config": {"workload": desc, "nuclei": [f"({n[0]},{n[1]}) D={n[2]}" for n in nuclei],
-                   "sites_per_step": v3 * nt, "units_per_step": units_per_step,
+                   "sites_per_step": v3 * nt * args.cfgs, "units_per_step": units_per_step,
+                   "configurations_per_rank": args.cfgs, "graph": bool(args.graph),
+                   "tune": {"fp64": tunes[0], "mixed": tunes[1]},
                    "l2": "inputs larger than L2 (field %.0f MB)" % (field_np.nbytes / 2 ** 20),
                    "parallelism": f"configurations sharded over {world} GPU(s)"},
         "roofline": roof,
-        "mixed": {"value": value_mx, "ms_per_step": msmx / args.steps, "speedup_vs_fp64": value_mx / value,
-                  "dtype": "f32 products, float-float accumulation, f64 contraction", "roofline": roof_mx},
+        "fp64": {"value": value64, "ms_per_step": ms64 / args.steps, "roofline": roof64},
+        "mixed": {"value": value_mx, "ms_per_step": msmx / args.steps, "speedup_vs_fp64": value_mx / value64,
+                  "dtype": "f32 products, Kahan-compensated f32 accumulation, f64 contraction and site sums", "roofline": roof_mx},
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": int((1 + 2 * len(lists)) * args.steps),

@@ -180,10 +180,11 @@ typedef struct {
 
 /* Launch tuning; zero fields select the library's choice. */
 typedef struct {
-    int32_t sites_per_cta;      /* small-stage kernel: sites per CTA           */
-    int32_t threads_per_cta;    /* small-stage kernel: threads per CTA         */
+    int32_t sites_per_cta;      /* FP64 small-stage kernel: sites per CTA      */
+    int32_t threads_per_cta;    /* mixed small-stage kernel: threads per CTA   */
     int32_t wave_sites;         /* large-stage kernels: sites in flight        */
     int32_t regime;             /* 0 auto, 1 force small-stage, 2 force large  */
+    int32_t zchunk;             /* large-stage step kernel: outputs per warp item */
 } mbc_tune;
 
 /*

@@ -66,7 +66,9 @@ class Props(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("sites_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
-                ("wave_sites", ctypes.c_int32), ("regime", ctypes.c_int32)]
+                ("wave_sites", ctypes.c_int32), ("regime", ctypes.c_int32), ("zchunk", ctypes.c_int32)]
+
+    FIELDS = ("sites_per_cta", "threads_per_cta", "wave_sites", "regime", "zchunk")
 
 
 class ContractOpts(ctypes.Structure):
@@ -261,8 +263,10 @@ def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0
     pr = Props(ptr, ptr, dtype, MEM_HOST if is_np else MEM_DEVICE, n_cfg, nt, lx, ly, lz, 0, 0)
     tn = None
     if tune is not None:
-        tn = Tune(tune.get("sites_per_cta", 0), tune.get("threads_per_cta", 0), tune.get("wave_sites", 0),
-                  tune.get("regime", 0))
+        unknown = set(tune) - set(Tune.FIELDS)
+        if unknown:
+            raise ValueError(f"unknown tune fields {sorted(unknown)}")
+        tn = Tune(*[int(tune.get(f, 0)) for f in Tune.FIELDS])
     op = ContractOpts(precision, moms.shape[0], moms.ctypes.data, t0, t1, ctypes.addressof(tn) if tn else None)
     handles = (ctypes.c_void_p * len(lists))(*[tl.handle for tl in lists])
     rc = lib.mbc_contract(ctypes.byref(pr), handles, len(lists), ctypes.byref(op), optr, _stream_ptr(stream))

@@ -338,55 +338,61 @@ int sm_count(int device) {
 // ---- launchers -------------------------------------------------------------
 
 // Small-stage kernels. FP64: one warp per site (k_small). MIXED: 32 sites
-// per CTA, lanes are sites (k_small_ls). A call with partial_out == nullptr
-// only sizes the launch (tiles and scratch).
+// per CTA, lanes are sites (k_small_ls). Lists of this regime are contracted
+// in batches of up to kMaxBatch by one persistent launch each.
 struct SmallLaunch {
     bool ok = false;
     int T = 0;            // sites per tile
     int threads = 0;
     size_t smem = 0;
     int tiles_per_slab = 0;
-    int64_t n_tiles = 0;
 };
 
-SmallLaunch size_small(const DeviceCache *c, const FieldDesc &F, const MomDesc &M, const mbc_tune *tune,
-                       bool mixed) {
+SmallLaunch size_small_batch(const std::vector<const DeviceCache *> &cs, const FieldDesc &F, const mbc_tune *tune,
+                             bool mixed, int32_t &site_stride, int32_t &comp_stride) {
     SmallLaunch l;
-    const SmallPlan &P = c->sp;
+    site_stride = 0;
+    comp_stride = 0;
+    for (auto *c : cs) {
+        site_stride = std::max(site_stride, (int32_t)c->site_entries);
+        comp_stride = std::max(comp_stride, c->sp.n_comp);
+    }
     if (!mixed) {
-        const int64_t per_site = c->site_entries * 16LL + 16LL * P.n_comp;
+        const int64_t per_site = site_stride * 16LL + 16LL * comp_stride;
         l.T = (int)std::min<int64_t>(32, kSmemLimit / per_site);
         if (tune && tune->sites_per_cta > 0) l.T = std::min(l.T, tune->sites_per_cta);
         l.threads = 32 * l.T;
         l.smem = (size_t)l.T * per_site;
     } else {
         l.T = 32;
-        l.smem = (size_t)(c->site_entries + 64) * 32 * sizeof(float2);
+        l.smem = (size_t)(site_stride + 64) * 32 * sizeof(float2);
         l.threads = (tune && tune->threads_per_cta > 0) ? tune->threads_per_cta : 1024;
         l.threads = std::max(64, std::min(1024, l.threads / 32 * 32));
-        if (l.smem > (size_t)kSmemLimit - 1024) return l;
+        if (l.smem > (size_t)kSmemLimit - 2048) return l;
     }
     if (l.T < 1) return l;
     const int v3 = F.lx * F.ly * F.lz;
     l.tiles_per_slab = (v3 + l.T - 1) / l.T;
-    l.n_tiles = (int64_t)F.n_cfg * F.n_t * l.tiles_per_slab;
     l.ok = true;
     return l;
 }
 
-mbc_status run_small(const DeviceCache *c, const FieldDesc &F, const MomDesc &M, const SmallLaunch &l, bool mixed,
-                     int device, cudaStream_t stream, const double2 *phase, double2 *partial_out) {
-    const SmallPlan &P = c->sp;
+mbc_status launch_small_batch(const SmallBatch &B, const FieldDesc &F, const MomDesc &M, const SmallLaunch &l,
+                              bool mixed, int device, cudaStream_t stream, const double2 *phase, double2 *partial,
+                              bool timed) {
     auto kern = mixed ? k_small_ls<MixedTraits> : k_small<FP64Traits>;
     MBC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem));
     int per_sm = 0;
     MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, l.threads, l.smem));
     if (per_sm < 1) return MBC_ERR_UNSUPPORTED;
-    int64_t grid = std::min<int64_t>(l.n_tiles, (int64_t)per_sm * sm_count(device));
+    int64_t grid = std::min<int64_t>(B.total_items, (int64_t)per_sm * sm_count(device));
     if (grid < 1) return MBC_OK;
-    {
+    MBC_CUDA_TRY(cudaMemsetAsync(B.counter, 0, sizeof(unsigned long long), stream));
+    if (timed) {
         TimedLaunch tl(stream);
-        kern<<<(unsigned)grid, l.threads, l.smem, stream>>>(P, F, M, phase, partial_out, l.n_tiles, l.tiles_per_slab);
+        kern<<<(unsigned)grid, l.threads, l.smem, stream>>>(B, F, M, phase, partial);
+    } else {
+        kern<<<(unsigned)grid, l.threads, l.smem, stream>>>(B, F, M, phase, partial);
     }
     MBC_CUDA_TRY(cudaGetLastError());
     return MBC_OK;
@@ -463,7 +469,7 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
             int64_t ngroups = W / 32;
             int64_t zchunk = (s.n_z * ngroups + 8 * total_warps - 1) / (8 * total_warps);
             zchunk = std::max<int64_t>(1, std::min<int64_t>(zchunk, 256));
-            if (tune && tune->regime == 2 && tune->threads_per_cta > 0) zchunk = tune->threads_per_cta;
+            if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
             int64_t items = ((s.n_z + zchunk - 1) / zchunk) * ngroups;
             int64_t grid = std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8);
             grid = std::max<int64_t>(grid, 1);
@@ -585,78 +591,125 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     const int64_t n_slabs = (int64_t)props->n_cfg * n_t;
     const bool mixed = opts->precision == MBC_MIXED;
 
-    // plan every list: regime, launch shape, scratch bytes
-    struct ListRun {
-        DeviceCache *c = nullptr;
-        bool skip = true, small = false;
-        SmallLaunch sl;
-        LargeSizes ls{};
-        size_t need = 0, pbytes = 0;
-    };
+    // plan every list: regime and scratch bytes; small-regime lists go into
+    // batches (most operations per site first) contracted by one launch each
     const int v3p = (int)((v3 + 31) / 32 * 32);
     const int64_t n_items = n_slabs * v3p;
     const int regime = opts->tune ? opts->tune->regime : 0;
-    std::vector<ListRun> runs((size_t)n_lists);
-    size_t max_need = 0;
+    std::vector<DeviceCache *> caches((size_t)n_lists, nullptr);
+    std::vector<int> small_ids, large_ids;
     for (int li = 0; li < n_lists; ++li) {
         const mbc_term_list *L = lists[li];
-        ListRun &r = runs[(size_t)li];
         if (L->pauli_forbidden || L->n_comp == 0) continue;  // identically zero
-        r.skip = false;
-        r.c = get_cache(L, device, st);
-        if (!r.c) return st;
-        if (regime == 1 && !r.c->small_ok) return MBC_ERR_UNSUPPORTED;
-        if (r.c->small_ok && regime != 2) {
-            r.sl = size_small(r.c, F, M, opts->tune, mixed);
-            r.small = r.sl.ok;
+        caches[(size_t)li] = get_cache(L, device, st);
+        if (!caches[(size_t)li]) return st;
+        bool small = caches[(size_t)li]->small_ok && regime != 2;
+        if (small) {  // the list alone must fit the shared-memory kernel
+            int32_t ss, cs;
+            small = size_small_batch({caches[(size_t)li]}, F, opts->tune, mixed, ss, cs).ok;
         }
-        if (regime == 1 && !r.small) return MBC_ERR_UNSUPPORTED;
-        if (r.small) {
-            r.pbytes = (size_t)r.sl.n_tiles * M.n_mom * L->n_comp * sizeof(double2);
-            r.need = align256(r.pbytes);
-        } else {
-            r.ls = mixed ? large_sizes<MixedTraits>(L, r.c, opts->tune, n_items)
-                         : large_sizes<FP64Traits>(L, r.c, opts->tune, n_items);
-            r.pbytes = (size_t)(n_items / 32) * M.n_mom * L->n_comp * sizeof(double2);
-            r.need = align256(r.pbytes) + 2 * align256(r.ls.blk_bytes) + 2 * align256(r.ls.stage_bytes) +
-                     align256(r.ls.c_bytes) + align256(r.ls.sexp_bytes);
+        if (regime == 1 && !small) return MBC_ERR_UNSUPPORTED;
+        (small ? small_ids : large_ids).push_back(li);
+    }
+    std::stable_sort(small_ids.begin(), small_ids.end(), [&](int a, int b) {
+        return lists[a]->stats.n_ops_total > lists[b]->stats.n_ops_total;
+    });
+    struct BatchRun {
+        std::vector<int> ids;
+        SmallLaunch sl;
+        SmallBatch B;
+        size_t part_bytes = 0;
+    };
+    std::vector<BatchRun> batches;
+    for (size_t i = 0; i < small_ids.size();) {
+        // grow the batch while the combined shared-memory footprint still fits
+        BatchRun br;
+        std::vector<const DeviceCache *> cs;
+        while (i < small_ids.size() && (int)br.ids.size() < kMaxBatch) {
+            std::vector<const DeviceCache *> trial = cs;
+            trial.push_back(caches[(size_t)small_ids[i]]);
+            int32_t ss, cc;
+            SmallLaunch l = size_small_batch(trial, F, opts->tune, mixed, ss, cc);
+            if (!l.ok && !br.ids.empty()) break;
+            cs = trial;
+            br.ids.push_back(small_ids[i]);
+            ++i;
         }
-        max_need = std::max(max_need, r.need);
+        std::memset(&br.B, 0, sizeof(br.B));
+        br.sl = size_small_batch(cs, F, opts->tune, mixed, br.B.site_stride, br.B.comp_stride);
+        br.B.n_lists = (int)br.ids.size();
+        br.B.tiles_per_slab = br.sl.tiles_per_slab;
+        int64_t items = 0, poff = 0;
+        for (int j = 0; j < br.B.n_lists; ++j) {
+            const DeviceCache *c = caches[(size_t)br.ids[(size_t)j]];
+            br.B.plan[j] = c->sp;
+            br.B.item_base[j] = items;
+            br.B.partial_off[j] = poff;
+            const int64_t tiles = n_slabs * br.sl.tiles_per_slab;
+            items += tiles;
+            poff += tiles * M.n_mom * c->sp.n_comp;
+        }
+        br.B.item_base[br.B.n_lists] = items;
+        br.B.total_items = items;
+        br.part_bytes = (size_t)poff * sizeof(double2);
+        batches.push_back(br);
+    }
+    size_t small_bytes = 0;
+    for (auto &br : batches) small_bytes += 256 + align256(br.part_bytes);
+    size_t large_bytes = 0;
+    std::vector<LargeSizes> lsz((size_t)n_lists);
+    for (int li : large_ids) {
+        const mbc_term_list *L = lists[li];
+        DeviceCache *c = caches[(size_t)li];
+        lsz[(size_t)li] = mixed ? large_sizes<MixedTraits>(L, c, opts->tune, n_items)
+                                : large_sizes<FP64Traits>(L, c, opts->tune, n_items);
+        const LargeSizes &ls = lsz[(size_t)li];
+        const size_t pbytes = (size_t)(n_items / 32) * M.n_mom * L->n_comp * sizeof(double2);
+        large_bytes = std::max(large_bytes, align256(pbytes) + 2 * align256(ls.blk_bytes) +
+                                                2 * align256(ls.stage_bytes) + align256(ls.c_bytes) +
+                                                align256(ls.sexp_bytes));
     }
     const size_t phase_bytes = align256((size_t)v3 * M.n_mom * sizeof(double2));
     void *scr = nullptr;
-    if ((st = scratch_get(device, stream, phase_bytes + max_need, &scr)) != MBC_OK) return st;
+    if ((st = scratch_get(device, stream, phase_bytes + small_bytes + large_bytes, &scr)) != MBC_OK) return st;
     double2 *phase = reinterpret_cast<double2 *>(scr);
     {
         unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((v3 * M.n_mom + 255) / 256, 4096));
         k_phase_table<<<grid, 256, 0, stream>>>(F, M, phase);
         MBC_CUDA_TRY(cudaGetLastError());
     }
-    char *rest = reinterpret_cast<char *>(scr) + phase_bytes;
-    for (int li = 0; li < n_lists; ++li) {
+    char *cur = reinterpret_cast<char *>(scr) + phase_bytes;
+    auto reduce = [&](int li, const double2 *partial, int tiles_per_slab) -> mbc_status {
         const mbc_term_list *L = lists[li];
-        ListRun &r = runs[(size_t)li];
-        if (r.skip) continue;
-        double2 *partial = reinterpret_cast<double2 *>(rest);
-        int tiles_per_slab;
-        if (r.small) {
-            if ((st = run_small(r.c, F, M, r.sl, mixed, device, stream, phase, partial)) != MBC_OK) return st;
-            tiles_per_slab = r.sl.tiles_per_slab;
-        } else {
-            char *bufs = rest + align256(r.pbytes);
-            st = mixed ? run_large<MixedTraits>(L, r.c, F, M, opts->tune, device, stream, bufs, partial, r.ls, n_items,
-                                                v3p, phase)
-                       : run_large<FP64Traits>(L, r.c, F, M, opts->tune, device, stream, bufs, partial, r.ls, n_items,
-                                               v3p, phase);
-            if (st != MBC_OK) return st;
-            tiles_per_slab = v3p / 32;
-        }
         int64_t outs = n_slabs * M.n_mom * L->n_comp;
         unsigned grid = (unsigned)std::min<int64_t>((outs + 255) / 256, 65535);
         k_reduce_tiles<<<std::max(grid, 1u), 256, 0, stream>>>(partial, n_slabs, tiles_per_slab, M.n_mom, L->n_comp,
                                                               n_t, li, n_lists, comp_max,
                                                               reinterpret_cast<double2 *>(dev_out));
         MBC_CUDA_TRY(cudaGetLastError());
+        return MBC_OK;
+    };
+    for (auto &br : batches) {
+        br.B.counter = reinterpret_cast<unsigned long long *>(cur);
+        double2 *partial = reinterpret_cast<double2 *>(cur + 256);
+        cur += 256 + align256(br.part_bytes);
+        if ((st = launch_small_batch(br.B, F, M, br.sl, mixed, device, stream, phase, partial, true)) != MBC_OK)
+            return st;
+        for (int j = 0; j < br.B.n_lists; ++j)
+            if ((st = reduce(br.ids[(size_t)j], partial + br.B.partial_off[j], br.sl.tiles_per_slab)) != MBC_OK)
+                return st;
+    }
+    for (int li : large_ids) {
+        const mbc_term_list *L = lists[li];
+        double2 *partial = reinterpret_cast<double2 *>(cur);
+        const size_t pbytes = (size_t)(n_items / 32) * M.n_mom * L->n_comp * sizeof(double2);
+        char *bufs = cur + align256(pbytes);
+        st = mixed ? run_large<MixedTraits>(L, caches[(size_t)li], F, M, opts->tune, device, stream, bufs, partial,
+                                            lsz[(size_t)li], n_items, v3p, phase)
+                   : run_large<FP64Traits>(L, caches[(size_t)li], F, M, opts->tune, device, stream, bufs, partial,
+                                           lsz[(size_t)li], n_items, v3p, phase);
+        if (st != MBC_OK) return st;
+        if ((st = reduce(li, partial, v3p / 32)) != MBC_OK) return st;
     }
 
     if (props->memory == MBC_MEM_HOST) {
@@ -829,7 +882,7 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
         const int64_t tiles = n_slabs * ((v3 + T - 1) / T);
         phase_bytes = align256((size_t)v3 * opts->n_mom * sizeof(double2));
         part_bytes = (size_t)tiles * opts->n_mom * list->n_comp * sizeof(double2);
-        if (phase_bytes + part_bytes > kStaticScratchBytes) return MBC_ERR_UNSUPPORTED;  // beyond the 8 MiB array
+        if (phase_bytes + 256 + part_bytes > kStaticScratchBytes) return MBC_ERR_UNSUPPORTED;  // beyond 8 MiB
     }
     // ---- device work: no allocation from here on
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_v);
@@ -864,31 +917,27 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     for (int q = 0; q < opts->n_mom; ++q)
         for (int dd = 0; dd < 3; ++dd) M.mom[q][dd] = opts->mom[3 * q + dd];
     double2 *phase = reinterpret_cast<double2 *>(scr);
-    double2 *partial = reinterpret_cast<double2 *>(reinterpret_cast<char *>(scr) + phase_bytes);
+    unsigned long long *counter = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scr) + phase_bytes);
+    double2 *partial = reinterpret_cast<double2 *>(reinterpret_cast<char *>(scr) + phase_bytes + 256);
     // every phase-table entry and every tile partial is written before it is
-    // read, so nothing in the shared array has to start at zero
+    // read; the work counter is set to zero below
     unsigned pgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((v3 * M.n_mom + 255) / 256, 4096));
     k_phase_table<<<pgrid, 256, 0, stream>>>(F, M, phase);
     MBC_CUDA_TRY(cudaGetLastError());
-    SmallLaunch l;
-    l.T = T;
-    l.threads = 32 * T;
-    l.smem = (size_t)T * (c->site_entries * 16 + 16LL * c->sp.n_comp);
-    l.tiles_per_slab = (int)((v3 + T - 1) / T);
-    l.n_tiles = n_slabs * l.tiles_per_slab;
-    l.ok = true;
-    const SmallPlan &P = c->sp;
-    MBC_CUDA_TRY(cudaFuncSetAttribute(k_small<FP64Traits>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem));
-    int per_sm = 0;
-    MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small<FP64Traits>, l.threads, l.smem));
-    if (per_sm < 1) return MBC_ERR_UNSUPPORTED;
-    const int64_t grid = std::min<int64_t>(l.n_tiles, (int64_t)per_sm * sm_count(device));
-    k_small<FP64Traits><<<(unsigned)grid, l.threads, l.smem, stream>>>(P, F, M, phase, partial, l.n_tiles,
-                                                                     l.tiles_per_slab);
-    MBC_CUDA_TRY(cudaGetLastError());
+    SmallBatch B;
+    std::memset(&B, 0, sizeof(B));
+    SmallLaunch l = size_small_batch({c}, F, opts->tune, false, B.site_stride, B.comp_stride);
+    if (!l.ok || l.T != T) return MBC_ERR_UNSUPPORTED;
+    B.n_lists = 1;
+    B.tiles_per_slab = l.tiles_per_slab;
+    B.total_items = n_slabs * l.tiles_per_slab;
+    B.item_base[1] = B.total_items;
+    B.counter = counter;
+    B.plan[0] = c->sp;
+    if ((st = launch_small_batch(B, F, M, l, false, device, stream, phase, partial, false)) != MBC_OK) return st;
     const int64_t outs = n_slabs * M.n_mom * list->n_comp;
     const unsigned rgrid = (unsigned)std::min<int64_t>((outs + 255) / 256, 65535);
-    k_reduce_tiles<<<std::max(rgrid, 1u), 256, 0, stream>>>(partial, n_slabs, l.tiles_per_slab, M.n_mom,
+    k_reduce_tiles<<<std::max(rgrid, 1u), 256, 0, stream>>>(partial, n_slabs, B.tiles_per_slab, M.n_mom,
                                                             list->n_comp, n_t, 0, 1, comp_max,
                                                             reinterpret_cast<double2 *>(out));
     MBC_CUDA_TRY(cudaGetLastError());

@@ -48,6 +48,36 @@ struct SmallPlan {
     double inv_norm;
 };
 
+// A batch of term lists contracted by one persistent launch: the work items
+// are (list, tile) pairs, numbered list by list in the order given (the host
+// puts the most expensive list first), handed out by an atomic counter.
+constexpr int kMaxBatch = 8;
+struct SmallBatch {
+    int32_t n_lists;
+    int32_t site_stride;      // warp-per-site kernel: entries of one site region (max over lists)
+    int32_t comp_stride;      // warp-per-site kernel: components per site in the C area (max)
+    int32_t tiles_per_slab;
+    int64_t total_items;
+    int64_t item_base[kMaxBatch + 1];
+    int64_t partial_off[kMaxBatch];  // in double2 units
+    unsigned long long *counter;     // zeroed before the launch
+    SmallPlan plan[kMaxBatch];
+};
+
+// next work item of the CTA (thread 0 draws, everyone reads); returns the list
+__device__ __forceinline__ int next_item(const SmallBatch &B, int64_t &tile) {
+    __shared__ long long s_item;
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(B.counter, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= B.total_items) return -1;
+    int l = 0;
+    while (l + 1 < B.n_lists && item >= B.item_base[l + 1]) ++l;
+    tile = item - B.item_base[l];
+    return l;
+}
+
 struct FieldDesc {
     const void *s;        // u = d field
     int32_t dtype;        // 0: complex double, 1: complex float
@@ -166,18 +196,21 @@ __global__ void k_phase_table(FieldDesc F, MomDesc M, double2 *tab) {
 // Shared-memory kernel, one warp per site (FP64 path).
 template <class Tr>
 __global__ void __launch_bounds__(1024, 1)
-    k_small(SmallPlan P, FieldDesc F, MomDesc M, const double2 *__restrict__ phase, double2 *partial,
-            int64_t n_tiles, int tiles_per_slab) {
+    k_small(const __grid_constant__ SmallBatch B, FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
+            double2 *partial_base) {
     using V = typename Tr::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int T = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    V *R = reinterpret_cast<V *>(smem_raw) + (int64_t)warp * P.site_entries;
-    double2 *Cs = reinterpret_cast<double2 *>(reinterpret_cast<V *>(smem_raw) + (int64_t)T * P.site_entries);
+    V *R = reinterpret_cast<V *>(smem_raw) + (int64_t)warp * B.site_stride;
+    double2 *Cs = reinterpret_cast<double2 *>(reinterpret_cast<V *>(smem_raw) + (int64_t)T * B.site_stride);
     const int V3 = F.lx * F.ly * F.lz;
-    const int nxi = P.nxi;
-
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int tiles_per_slab = B.tiles_per_slab;
+    int64_t tile;
+    for (int li; (li = next_item(B, tile)) >= 0;) {
+        const SmallPlan &P = B.plan[li];
+        double2 *partial = partial_base + B.partial_off[li];
+        const int nxi = P.nxi;
         const int64_t slab = tile / tiles_per_slab;
         const int tin = (int)(tile % tiles_per_slab);
         const int cfg = (int)(slab / F.n_t), t = F.t0 + (int)(slab % F.n_t);
@@ -211,10 +244,10 @@ __global__ void __launch_bounds__(1024, 1)
                     re += __shfl_xor_sync(0xffffffffu, re, off);
                     im += __shfl_xor_sync(0xffffffffu, im, off);
                 }
-                if (c < P.n_comp && sub == 0) Cs[warp * P.n_comp + c] = make_double2(re, im);
+                if (c < P.n_comp && sub == 0) Cs[warp * B.comp_stride + c] = make_double2(re, im);
             }
         } else {
-            for (int c = lane; c < P.n_comp; c += 32) Cs[warp * P.n_comp + c] = make_double2(0, 0);
+            for (int c = lane; c < P.n_comp; c += 32) Cs[warp * B.comp_stride + c] = make_double2(0, 0);
         }
         __syncthreads();
         // tile partial: (1/N) sum over the T sites, in a fixed order, of phase * C
@@ -223,13 +256,12 @@ __global__ void __launch_bounds__(1024, 1)
             int q = o / P.n_comp, c = o % P.n_comp;
             double re = 0.0, im = 0.0;
             for (int w = 0; w < T && site0 + w < V3; ++w) {
-                double2 ph = __ldg(phase + (int64_t)(site0 + w) * M.n_mom + q), cv = Cs[w * P.n_comp + c];
+                double2 ph = __ldg(phase + (int64_t)(site0 + w) * M.n_mom + q), cv = Cs[w * B.comp_stride + c];
                 re = __fma_rn(ph.x, cv.x, __fma_rn(-ph.y, cv.y, re));
                 im = __fma_rn(ph.x, cv.y, __fma_rn(ph.y, cv.x, im));
             }
             partial[tile * (int64_t)(M.n_mom * P.n_comp) + o] = make_double2(re * P.inv_norm, im * P.inv_norm);
         }
-        __syncthreads();
     }
 }
 
@@ -275,8 +307,8 @@ __device__ __forceinline__ int f32_exponent(float f) {
 
 template <class Tr>
 __global__ void __launch_bounds__(1024, 1)
-    k_small_ls(SmallPlan P, FieldDesc F, MomDesc M, const double2 *__restrict__ phase, double2 *partial,
-               int64_t n_tiles, int tiles_per_slab) {
+    k_small_ls(const __grid_constant__ SmallBatch B, FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
+               double2 *partial_base) {
     using V = typename Tr::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *R = reinterpret_cast<V *>(smem_raw);  // [entry][32]
@@ -284,51 +316,52 @@ __global__ void __launch_bounds__(1024, 1)
     const int NW = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int V3 = F.lx * F.ly * F.lz;
-    const int nxi = P.nxi, nent = nxi * nxi;
     const unsigned full = 0xffffffffu;
+    const int tiles_per_slab = B.tiles_per_slab;
 #define ROW(e) R[(int64_t)(e) * 32 + lane]
 
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    int64_t tile;
+    for (int li; (li = next_item(B, tile)) >= 0;) {  // next_item synchronises the CTA
+        const SmallPlan &P = B.plan[li];
+        double2 *partial = partial_base + B.partial_off[li];
+        const int nxi = P.nxi, nent = nxi * nxi;
         const int64_t slab = tile / tiles_per_slab;
         const int tin = (int)(tile % tiles_per_slab);
         const int cfg = (int)(slab / F.n_t), t = F.t0 + (int)(slab % F.n_t);
         const int site0 = tin * 32;
-        __syncthreads();  // the previous tile is done with shared memory
         // 1. load and scale: one warp per site
         for (int s = warp; s < 32; s += NW) {
             const int site = site0 + s;
             const bool live = site < V3;
             const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * 144;
+            // two passes over the tile (the second one hits L1): exponent, then values
             int emax = -100000;
-            float2 fv[5];
-            double2 dv[5];
-            for (int q = 0; q < 5; ++q) {
-                const int e = lane + 32 * q;
+            for (int e = lane; e < nent; e += 32) {
                 const int idx = (e / nxi) * 12 + (e % nxi);
-                if (live && e < nent) {
-                    if (F.dtype == 0) {
-                        dv[q] = __ldg(reinterpret_cast<const double2 *>(F.s) + base + idx);
-                        emax = max(emax, max(f64_exponent(dv[q].x), f64_exponent(dv[q].y)));
-                    } else {
-                        fv[q] = __ldg(reinterpret_cast<const float2 *>(F.s) + base + idx);
-                        emax = max(emax, max(f32_exponent(fv[q].x), f32_exponent(fv[q].y)));
-                    }
+                if (!live) break;
+                if (F.dtype == 0) {
+                    const double2 v = __ldg(reinterpret_cast<const double2 *>(F.s) + base + idx);
+                    emax = max(emax, max(f64_exponent(v.x), f64_exponent(v.y)));
+                } else {
+                    const float2 v = __ldg(reinterpret_cast<const float2 *>(F.s) + base + idx);
+                    emax = max(emax, max(f32_exponent(v.x), f32_exponent(v.y)));
                 }
             }
             for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(full, emax, off));
             const int se = emax == -100000 ? 0 : -emax;  // largest entry scaled into [1, 2)
-            for (int q = 0; q < 5; ++q) {
-                const int e = lane + 32 * q;
-                if (e < nent) {
-                    float2 v = make_float2(0.f, 0.f);
-                    if (live) {
-                        if (F.dtype == 0)
-                            v = make_float2(f64_scaled_to_f32(dv[q].x, se), f64_scaled_to_f32(dv[q].y, se));
-                        else
-                            v = make_float2(f32_scaled(fv[q].x, se), f32_scaled(fv[q].y, se));
+            for (int e = lane; e < nent; e += 32) {
+                const int idx = (e / nxi) * 12 + (e % nxi);
+                float2 v = make_float2(0.f, 0.f);
+                if (live) {
+                    if (F.dtype == 0) {
+                        const double2 dvv = __ldg(reinterpret_cast<const double2 *>(F.s) + base + idx);
+                        v = make_float2(f64_scaled_to_f32(dvv.x, se), f64_scaled_to_f32(dvv.y, se));
+                    } else {
+                        const float2 fvv = __ldg(reinterpret_cast<const float2 *>(F.s) + base + idx);
+                        v = make_float2(f32_scaled(fvv.x, se), f32_scaled(fvv.y, se));
                     }
-                    R[(int64_t)(P.s_off + e) * 32 + s] = V{v.x, v.y};
                 }
+                R[(int64_t)(P.s_off + e) * 32 + s] = V{v.x, v.y};
             }
             if (lane == 0) sexp_s[s] = se;
         }
@@ -400,37 +433,24 @@ __global__ void __launch_bounds__(1024, 1)
             const V *Xl = R + (d.x_off << 5) + lane;
             const V *Yl = R + (d.y_off << 5) + lane;
             V *Zl = R + (d.z_off << 5) + lane;
-            int z = (int)zb;
-            int left = part < 0 ? d.k : 0x7fffffff;  // ops until the next output is complete
-            const int n_ops = (int)(o_end - o_begin);
-            const uint32_t *ob_ptr = ops + o_begin;
-            int done = 0;
-            for (; done + 32 <= n_ops; done += 32) {
-                const uint32_t mine = __ldg(ob_ptr + done + lane);
-#pragma unroll 8
-                for (int q = 0; q < 32; ++q) {
-                    const uint32_t op = __shfl_sync(full, mine, q);
-                    acc.fma(Xl[(op & 0xffffu) << 5], Yl[((op >> 16) & 0x7fffu) << 5], op & 0x80000000u);
-                    if (--left == 0) {
-                        Zl[z << 5] = acc.store();
-                        acc.zero();
-                        ++z;
-                        left = d.k;
+            // output by output: each output's k terms are contiguous, loaded
+            // 32 at a time and broadcast by shuffles; no per-term branch
+            const int n_out = part < 0 ? (int)((o_end - o_begin) / d.k) : 1;
+            const int len = part < 0 ? d.k : (int)(o_end - o_begin);
+            const uint32_t *op_ptr = ops + o_begin;
+            for (int zz = 0; zz < n_out; ++zz, op_ptr += len) {
+                for (int b0 = 0; b0 < len; b0 += 32) {
+                    const int nb = min(32, len - b0);
+                    const uint32_t mine = lane < nb ? __ldg(op_ptr + b0 + lane) : 0u;
+#pragma unroll 4
+                    for (int q = 0; q < nb; ++q) {
+                        const uint32_t op = __shfl_sync(full, mine, q);
+                        acc.fma(Xl[(op & 0xffffu) << 5], Yl[((op >> 16) & 0x7fffu) << 5], op & 0x80000000u);
                     }
                 }
-            }
-            if (done < n_ops) {
-                const int nb = n_ops - done;
-                const uint32_t mine = lane < nb ? __ldg(ob_ptr + done + lane) : 0u;
-                for (int q = 0; q < nb; ++q) {
-                    const uint32_t op = __shfl_sync(full, mine, q);
-                    acc.fma(Xl[(op & 0xffffu) << 5], Yl[((op >> 16) & 0x7fffu) << 5], op & 0x80000000u);
-                    if (--left == 0) {
-                        Zl[z << 5] = acc.store();
-                        acc.zero();
-                        ++z;
-                        left = d.k;
-                    }
+                if (part < 0) {
+                    Zl[((int)zb + zz) << 5] = acc.store();
+                    acc.zero();
                 }
             }
             if (split > 1) {

@@ -170,3 +170,108 @@ def test_be8_large_path(mbc):
     sp = (0, 1, 2, 3, 0, 1, 2, 3)
     tl = mbc.build_term_list(4, 4, 4, spins=[(sp, sp)])
     check_slabs(mbc, field, [tl], [(4, 4, 4)], dims)
+
+
+def test_batched_launch_mixed_regimes(mbc):
+    """One call over several configurations, time slices and nuclei of both
+    regimes (the nonrelativistic ones share one persistent launch)."""
+    dims = (2, 2, 3)
+    field = synth.field(3, 2, 2, dims, 0.4, dtype=np.complex64)
+    sp = (0, 1, 0, 1)
+    lists = [mbc.build_term_list(1, 1, 2), mbc.build_term_list(2, 1, 2), mbc.build_term_list(2, 2, 2),
+             mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])]
+    specs = [(1, 1, 2), (2, 1, 2), (2, 2, 2), (2, 2, 4)]
+    check_slabs(mbc, field, lists, specs, dims)
+
+
+def test_graph_capture_replays_bitwise(mbc):
+    """The whole contraction captured in a CUDA graph replays to the same bits."""
+    import torch
+    dims = (4, 4, 4)
+    field = torch.from_numpy(synth.field(12, 2, 3, dims, 0.4, dtype=np.complex64)).to("cuda:0")
+    sp = (0, 1, 0, 1)
+    lists = [mbc.build_term_list(2, 2, 2), mbc.build_term_list(1, 1, 2),
+             mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])]
+    for prec in (0, 1):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            ref = mbc.contract(field, lists, precision=prec, stream=s)  # warm-up: scratch and lists resident
+            out = torch.zeros_like(ref)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            mbc.contract(field, lists, precision=prec, out=out, stream=s)
+        for _ in range(2):
+            out.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref)
+
+
+def _sparse_slab_field(seed, dims, lam, sites, dtype=np.complex128):
+    """Full-size slab whose propagators vanish except at the listed sites:
+    every other site contributes exactly zero, so the slab sum is the sum
+    over the listed sites, which the oracle evaluates one by one."""
+    full = synth.field(seed, 1, 1, dims, lam, dtype=dtype)
+    out = np.zeros_like(full)
+    flat_o = out.reshape(-1, 12, 12)
+    flat_f = full.reshape(-1, 12, 12)
+    flat_o[sites] = flat_f[sites]
+    return out
+
+
+def _check_sparse(mbc, field, tl, spec, dims, sites, precisions=(0, 1)):
+    from oracle import site_sum
+    coords = synth.site_coords(dims)[sites]
+    plan = oracle_plan(*spec, tl.components())
+    C, sc = plan.evaluate(field.reshape(-1, 12, 12)[sites].astype(np.complex128))
+    ref = site_sum.site_sum(C, coords, tuple(dims[::-1]), [(0, 0, 0)])
+    scale = site_sum.scale_sum(sc)
+    for p in precisions:
+        got = run(mbc, field, [tl], p)[0, 0, 0, :, : len(tl.components())]
+        assert max_rel_err(got, ref, scale) <= TOL[p], p
+
+
+def test_he4_rel_all_components_full_lattice_sampled(mbc):
+    """16^3 slab (the relativistic 4He configuration's geometry and launch
+    shape), all 1296 components, four live sites."""
+    dims = (16, 16, 16)
+    sites = [0, 1337, 2048, 4095]
+    field = _sparse_slab_field(2, dims, 0.4, sites)
+    _check_sparse(mbc, field, mbc.build_term_list(2, 2, 4), (2, 2, 4), dims, sites, precisions=(1,))
+
+
+def test_be8_full_lattice_sampled(mbc):
+    dims = (16, 16, 16)
+    sites = [5, 3000]
+    field = _sparse_slab_field(4, dims, 0.4, sites, dtype=np.complex64)
+    sp = (0, 1, 2, 3, 0, 1, 2, 3)
+    _check_sparse(mbc, field, mbc.build_term_list(4, 4, 4, spins=[(sp, sp)]), (4, 4, 4), dims, sites,
+                  precisions=(1,))
+
+
+def test_batched_geometry_sampled(mbc):
+    """24^3 geometry of the batched configuration, complex64, four nuclei."""
+    dims = (24, 24, 24)
+    sites = [0, 7777, 13823]
+    field = _sparse_slab_field(3, dims, 0.4, sites, dtype=np.complex64)
+    sp = (0, 1, 0, 1)
+    for tl, spec in ((mbc.build_term_list(1, 1, 2), (1, 1, 2)), (mbc.build_term_list(2, 2, 2), (2, 2, 2)),
+                     (mbc.build_term_list(2, 2, 4, spins=[(sp, sp)]), (2, 2, 4))):
+        _check_sparse(mbc, field, tl, spec, dims, sites)
+
+
+def test_out_of_memory_is_a_clean_error(mbc):
+    """A scratch request beyond the device's memory returns MBC_ERR_OOM and
+    leaves the context usable."""
+    import torch
+    dims = (16, 16, 16)
+    field = torch.zeros((1, 1) + dims + (12, 12), dtype=torch.complex128, device="cuda:0")
+    tl = mbc.build_term_list(2, 2, 4)  # ~135 MB of stage buffers per site in FP64
+    with pytest.raises(mbc.MbcError) as ei:
+        mbc.contract(field, [tl], precision=0, tune={"wave_sites": 4096, "regime": 2})
+    assert ei.value.status == 3
+    small = mbc.build_term_list(1, 1, 2)
+    out = mbc.contract(field[..., :, :], [small], precision=0)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0
