@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
     ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner first")
+    ap.add_argument("--tune", default="", help='fixed launch shape as JSON, e.g. {"wave_sites": 256}')
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -129,6 +130,29 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def profiled_traffic(name, sites):
+    """DRAM bytes per launch of a kernel from its committed ncu summary
+    (bytes per site x sites), or None when the kernel source changed since
+    the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_site", "kernel_source_sha256_16"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for src in ("small_kernel.cuh", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1301_4895_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16] or "traffic_bytes_per_site" not in vals:
+        return None
+    return float(vals["traffic_bytes_per_site"]) * sites
 
 
 def measured_peaks():
@@ -253,6 +277,8 @@ def main():
     stream = torch.cuda.Stream(dev)
     units_per_step = v3 * nt * len(lists) * args.cfgs
     tunes = {0: None, 1: None}
+    if args.tune:
+        tunes = {0: json.loads(args.tune), 1: json.loads(args.tune)}
     if args.autotune:
         from paper_1301_4895_gb300.autotune import autotune
         for p in (0, 1):
@@ -373,6 +399,10 @@ def main():
     roof_mx = roofline(kmx, msmx, nmx, nominal32, probe32,
                        "FP32 vector, derived: 152 SMs x 128 FFMA/clk x max SM clock", 1)
     roof = roof64 if primary == 0 else roof_mx
+    if roof is not None and args.workload == "nonrel" and primary == 0 and not has_large:
+        roof["traffic"] = profiled_traffic("k_small_fp64_he3_he4_16x16x16x16.md", v3 * nt * args.cfgs)
+        roof["traffic_note"] = ("DRAM bytes per launch (one launch per step) from the committed ncu summary, "
+                                "scaled from 65,536 to the step's sites")
     line = {
         "metric": "sink-site correlators/s", "value": value, "unit": "sink-site correlators/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,

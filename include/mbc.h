@@ -156,6 +156,7 @@ void mbc_free_term_list(mbc_term_list *list);
 enum { MBC_C128 = 0, MBC_C64 = 1 };              /* propagator storage */
 enum { MBC_FP64 = 0, MBC_MIXED = 1 };            /* arithmetic          */
 enum { MBC_MEM_DEVICE = 0, MBC_MEM_HOST = 1 };   /* where s_u/s_d/out live */
+enum { MBC_SINK_POINT = 0, MBC_SINK_BLOCK_MOMENTUM = 1 };  /* sink function   */
 
 /*
  * Propagator fields, layout [cfg][t][z][y][x][row 12][col 12] complex,
@@ -185,6 +186,9 @@ typedef struct {
     int32_t wave_sites;         /* large-stage kernels: sites in flight        */
     int32_t regime;             /* 0 auto, 1 force small-stage, 2 force large  */
     int32_t zchunk;             /* large-stage step kernel: outputs per warp item */
+    int32_t wave_order;         /* large-stage step kernel: 0 site groups of a chunk
+                                   side by side, 1 a CTA's warps on consecutive chunks
+                                   of one site group                              */
 } mbc_tune;
 
 /*
@@ -198,6 +202,13 @@ typedef struct {
  *                integers (host pointer, read during the call).
  *   t0, t1       time slices [t0, t1) are evaluated; t1 == 0 means nt.
  *   tune         NULL or launch tuning.
+ *   sink_mode    MBC_SINK_POINT: the correlator of all baryons at one sink
+ *                point, summed over sites with the momentum phase.
+ *                MBC_SINK_BLOCK_MOMENTUM: every baryon's block is projected to
+ *                the momentum first, f_B = sum_x exp(-2 pi i n.x / L) f_B(x)
+ *                (Sec. 2 sink function s(x)), and the recursion runs once
+ *                per (configuration, time slice, momentum) on those blocks.
+ *                The block sums are FP64 in both precisions.
  */
 typedef struct {
     int32_t precision;
@@ -205,6 +216,7 @@ typedef struct {
     const int32_t *mom;
     int32_t t0, t1;
     const mbc_tune *tune;
+    int32_t sink_mode;
 } mbc_contract_opts;
 
 /*
@@ -232,8 +244,8 @@ mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *const *list
  * Same arguments and output layout as mbc_contract with n_lists = 1:
  * out is complex128 [n_cfg][1][t1 - t0][n_mom][max(1, n_comp)], device
  * memory owned by the caller, written completely on each call.
- * Supported: MBC_FP64, MBC_MEM_DEVICE, and lists that take the shared-memory
- * kernel (the nonrelativistic nuclei); anything else returns
+ * Supported: MBC_FP64, MBC_MEM_DEVICE, MBC_SINK_POINT, and lists that take the
+ * shared-memory kernel (the nonrelativistic nuclei); anything else returns
  * MBC_ERR_UNSUPPORTED before touching the device.
  *
  * Scratch: one static device array of 8 MiB (MBC_NOALLOC_SCRATCH_BYTES)

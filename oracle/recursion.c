@@ -384,115 +384,156 @@ static void eval_cb(void *vctx, key_t32 x, key_t32 y, int sgn) {
     }
 }
 
+/* 5a: raw blocks f(delta; xi1, xi2, xi3) = sum G(delta; xi') S S S of nb
+ * sites and their antisymmetric components for P and N; fm[b], fmm[b] are
+ * [site][4*12*12*12] (values and magnitudes), allocated here. */
+static void blocks_batch(const o3_plan *p, int nb, const cplx *S, cplx *fm[2], double *fmm[2]) {
+    const int64_t NB = 4 * 12 * 12 * 12;
+    cplx *fraw = (cplx *)calloc((size_t)(NB * nb), sizeof(cplx));
+    double *fmag = (double *)calloc((size_t)(NB * nb), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int s = 0; s < nb; ++s) {
+        const cplx *Ss = S + (int64_t)s * 144;
+        for (int a = 0; a < 4; ++a)
+            for (int p1 = 0; p1 < 12; ++p1)
+                for (int p2 = 0; p2 < 12; ++p2)
+                    for (int p3 = 0; p3 < 12; ++p3) {
+                        int g = p->G[((a * 12 + p1) * 12 + p2) * 12 + p3];
+                        if (!g) continue;
+                        for (int i = 0; i < 12; ++i)
+                            for (int j = 0; j < 12; ++j)
+                                for (int k = 0; k < 12; ++k) {
+                                    int64_t idx = ((int64_t)(a * 12 + i) * 12 + j) * 12 + k;
+                                    cplx t = cmul(cmul(Ss[p1 * 12 + i], Ss[p2 * 12 + j]), Ss[p3 * 12 + k]);
+                                    fraw[s * NB + idx].re += g * t.re;
+                                    fraw[s * NB + idx].im += g * t.im;
+                                    fmag[s * NB + idx] += abs(g) * cabs2(Ss[p1 * 12 + i]) *
+                                                          cabs2(Ss[p2 * 12 + j]) * cabs2(Ss[p3 * 12 + k]);
+                                }
+                    }
+    }
+    for (int b = 0; b < 2; ++b) {
+        fm[b] = (cplx *)calloc((size_t)(NB * nb), sizeof(cplx));
+        fmm[b] = (double *)calloc((size_t)(NB * nb), sizeof(double));
+    }
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < nb; ++s)
+        for (int a = 0; a < 4; ++a)
+            for (int i = 0; i < 12; ++i)
+                for (int j = 0; j < 12; ++j)
+                    for (int k = 0; k < 12; ++k) {
+                        int64_t idx = ((int64_t)(a * 12 + i) * 12 + j) * 12 + k;
+                        int64_t sw_p = ((int64_t)(a * 12 + j) * 12 + i) * 12 + k; /* f(a; j, i, k) */
+                        int64_t sw_n = ((int64_t)(a * 12 + k) * 12 + j) * 12 + i; /* f(a; k, j, i) */
+                        const int64_t o = s * NB;
+                        if (i < j) {
+                            fm[0][o + idx].re = fraw[o + idx].re - fraw[o + sw_p].re;
+                            fm[0][o + idx].im = fraw[o + idx].im - fraw[o + sw_p].im;
+                            fmm[0][o + idx] = fmag[o + idx] + fmag[o + sw_p];
+                        }
+                        if (i < k) {
+                            fm[1][o + idx].re = fraw[o + idx].re - fraw[o + sw_n].re;
+                            fm[1][o + idx].im = fraw[o + idx].im - fraw[o + sw_n].im;
+                            fmm[1][o + idx] = fmag[o + idx] + fmag[o + sw_n];
+                        }
+                    }
+    free(fraw);
+    free(fmag);
+}
+
+/* 5b-5d for nb items whose blocks are given ([item][4*12*12*12]); results to
+ * out/scale rows o0 .. o0 + nb - 1. */
+static void recursion_batch(const o3_plan *p, int nb, cplx *const fm[2], double *const fmm[2], int64_t o0,
+                            double *out, double *scale) {
+    const int A = p->A;
+    const int64_t NB = 4 * 12 * 12 * 12;
+    /* 5b: F^(1) = f_{B1} on the needed keys of stage 1 */
+    int b0 = p->path[0];
+    cplx *X = (cplx *)calloc((size_t)(p->n_need[0] * nb), sizeof(cplx));
+    double *Xm = (double *)calloc((size_t)(p->n_need[0] * nb), sizeof(double));
+    for (int64_t i = 0; i < p->n_need[0]; ++i) {
+        int64_t iy = block_index(p->need[0][i], b0);
+        for (int s = 0; s < nb; ++s) { X[i * nb + s] = fm[b0][s * NB + iy]; Xm[i * nb + s] = fmm[b0][s * NB + iy]; }
+    }
+    /* 5c: F^(m+1)[z] = sum over splits sgn(x|y) F^(m)[x] f[y] */
+    for (int m = 1; m < A; ++m) {
+        int b = p->path[m];
+        int64_t nz = p->n_need[m];
+        cplx *Z = (cplx *)calloc((size_t)(nz * nb), sizeof(cplx));
+        double *Zm = (double *)calloc((size_t)(nz * nb), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t i = 0; i < nz; ++i) {
+            eval_ctx c;
+            c.p = p; c.nb = nb; c.X = X; c.Xm = Xm; c.Y = fm[b]; c.Ym = fmm[b];
+            c.nX = p->n_need[m - 1]; c.kX = p->need[m - 1];
+            c.acc = Z + i * nb; c.accm = Zm + i * nb;
+            for_splits(p->need[m][i], b, eval_cb, &c);
+        }
+        free(X); free(Xm);
+        X = Z; Xm = Zm;
+    }
+    /* 5d: C(r) = (1/N) sum F^(A)[(sink set, U, D)] L(source set; U, D) */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < p->n_req; ++r)
+        for (int s = 0; s < nb; ++s) {
+            double re = 0, im = 0, mg = 0;
+            for (int64_t e = p->req_off[r]; e < p->req_off[r + 1]; ++e) {
+                int64_t iz = find_key(p->need[A - 1], p->n_need[A - 1], p->req_key[e]);
+                double l = (double)p->req_lval[e];
+                re += X[iz * nb + s].re * l;
+                im += X[iz * nb + s].im * l;
+                mg += Xm[iz * nb + s] * fabs(l);
+            }
+            int64_t o = (o0 + s) * p->n_req + r;
+            out[2 * o] = re / p->norm;
+            out[2 * o + 1] = im / p->norm;
+            if (scale) scale[o] = mg / p->norm;
+        }
+    free(X); free(Xm);
+}
+
 /*
  * Evaluate the plan on n_sites sites. S: [site][12][12] complex (re, im
  * interleaved), u = d. out: [site][n_req] complex; scale: [site][n_req]
  * (the magnitude recursion). batch: sites evaluated together.
  */
 int o3_eval(const o3_plan *p, int64_t n_sites, const double *S_in, double *out, double *scale, int batch) {
-    const int A = p->A;
     if (batch < 1) batch = 1;
-    const int64_t NB = 4 * 12 * 12 * 12;
     for (int64_t s0 = 0; s0 < n_sites; s0 += batch) {
         int nb = (int)((n_sites - s0) < batch ? (n_sites - s0) : batch);
-        const cplx *S = (const cplx *)S_in + s0 * 144;
-        /* 5a: raw blocks f(delta; xi1, xi2, xi3) = sum G(delta; xi') S S S
-         * and their antisymmetric components for P and N, [index][site] */
-        cplx *fraw = (cplx *)calloc((size_t)(NB * nb), sizeof(cplx));
-        double *fmag = (double *)calloc((size_t)(NB * nb), sizeof(double));
-#pragma omp parallel for schedule(dynamic, 1)
-        for (int s = 0; s < nb; ++s) {
-            const cplx *Ss = S + (int64_t)s * 144;
-            for (int a = 0; a < 4; ++a)
-                for (int p1 = 0; p1 < 12; ++p1)
-                    for (int p2 = 0; p2 < 12; ++p2)
-                        for (int p3 = 0; p3 < 12; ++p3) {
-                            int g = p->G[((a * 12 + p1) * 12 + p2) * 12 + p3];
-                            if (!g) continue;
-                            for (int i = 0; i < 12; ++i)
-                                for (int j = 0; j < 12; ++j)
-                                    for (int k = 0; k < 12; ++k) {
-                                        int64_t idx = ((int64_t)(a * 12 + i) * 12 + j) * 12 + k;
-                                        cplx t = cmul(cmul(Ss[p1 * 12 + i], Ss[p2 * 12 + j]), Ss[p3 * 12 + k]);
-                                        fraw[s * NB + idx].re += g * t.re;
-                                        fraw[s * NB + idx].im += g * t.im;
-                                        fmag[s * NB + idx] += abs(g) * cabs2(Ss[p1 * 12 + i]) *
-                                                              cabs2(Ss[p2 * 12 + j]) * cabs2(Ss[p3 * 12 + k]);
-                                    }
-                        }
-        }
         cplx *fm[2]; double *fmm[2];
-        for (int b = 0; b < 2; ++b) {
-            fm[b] = (cplx *)calloc((size_t)(NB * nb), sizeof(cplx));
-            fmm[b] = (double *)calloc((size_t)(NB * nb), sizeof(double));
-        }
-#pragma omp parallel for schedule(static)
-        for (int s = 0; s < nb; ++s)
-            for (int a = 0; a < 4; ++a)
-                for (int i = 0; i < 12; ++i)
-                    for (int j = 0; j < 12; ++j)
-                        for (int k = 0; k < 12; ++k) {
-                            int64_t idx = ((int64_t)(a * 12 + i) * 12 + j) * 12 + k;
-                            int64_t sw_p = ((int64_t)(a * 12 + j) * 12 + i) * 12 + k; /* f(a; j, i, k) */
-                            int64_t sw_n = ((int64_t)(a * 12 + k) * 12 + j) * 12 + i; /* f(a; k, j, i) */
-                            const int64_t o = s * NB;
-                            if (i < j) {
-                                fm[0][o + idx].re = fraw[o + idx].re - fraw[o + sw_p].re;
-                                fm[0][o + idx].im = fraw[o + idx].im - fraw[o + sw_p].im;
-                                fmm[0][o + idx] = fmag[o + idx] + fmag[o + sw_p];
-                            }
-                            if (i < k) {
-                                fm[1][o + idx].re = fraw[o + idx].re - fraw[o + sw_n].re;
-                                fm[1][o + idx].im = fraw[o + idx].im - fraw[o + sw_n].im;
-                                fmm[1][o + idx] = fmag[o + idx] + fmag[o + sw_n];
-                            }
-                        }
-        free(fraw); free(fmag);
-
-        /* 5b: F^(1) = f_{B1} on the needed keys of stage 1 */
-        int b0 = p->path[0];
-        cplx *X = (cplx *)calloc((size_t)(p->n_need[0] * nb), sizeof(cplx));
-        double *Xm = (double *)calloc((size_t)(p->n_need[0] * nb), sizeof(double));
-        for (int64_t i = 0; i < p->n_need[0]; ++i) {
-            int64_t iy = block_index(p->need[0][i], b0);
-            for (int s = 0; s < nb; ++s) { X[i * nb + s] = fm[b0][s * NB + iy]; Xm[i * nb + s] = fmm[b0][s * NB + iy]; }
-        }
-        /* 5c: F^(m+1)[z] = sum over splits sgn(x|y) F^(m)[x] f[y] */
-        for (int m = 1; m < A; ++m) {
-            int b = p->path[m];
-            int64_t nz = p->n_need[m];
-            cplx *Z = (cplx *)calloc((size_t)(nz * nb), sizeof(cplx));
-            double *Zm = (double *)calloc((size_t)(nz * nb), sizeof(double));
-#pragma omp parallel for schedule(dynamic, 64)
-            for (int64_t i = 0; i < nz; ++i) {
-                eval_ctx c;
-                c.p = p; c.nb = nb; c.X = X; c.Xm = Xm; c.Y = fm[b]; c.Ym = fmm[b];
-                c.nX = p->n_need[m - 1]; c.kX = p->need[m - 1];
-                c.acc = Z + i * nb; c.accm = Zm + i * nb;
-                for_splits(p->need[m][i], b, eval_cb, &c);
-            }
-            free(X); free(Xm);
-            X = Z; Xm = Zm;
-        }
-        /* 5d: C(r) = (1/N) sum F^(A)[(sink set, U, D)] L(source set; U, D) */
-#pragma omp parallel for schedule(dynamic, 1)
-        for (int r = 0; r < p->n_req; ++r)
-            for (int s = 0; s < nb; ++s) {
-                double re = 0, im = 0, mg = 0;
-                for (int64_t e = p->req_off[r]; e < p->req_off[r + 1]; ++e) {
-                    int64_t iz = find_key(p->need[A - 1], p->n_need[A - 1], p->req_key[e]);
-                    double l = (double)p->req_lval[e];
-                    re += X[iz * nb + s].re * l;
-                    im += X[iz * nb + s].im * l;
-                    mg += Xm[iz * nb + s] * fabs(l);
-                }
-                int64_t o = (s0 + s) * p->n_req + r;
-                out[2 * o] = re / p->norm;
-                out[2 * o + 1] = im / p->norm;
-                if (scale) scale[o] = mg / p->norm;
-            }
-        free(X); free(Xm);
+        blocks_batch(p, nb, (const cplx *)S_in + s0 * 144, fm, fmm);
+        recursion_batch(p, nb, fm, fmm, s0, out, scale);
         for (int b = 0; b < 2; ++b) { free(fm[b]); free(fmm[b]); }
     }
+    return 0;
+}
+
+/* Antisymmetric block components of n_sites sites (Sec. 2, Sec. 4):
+ * out_fm[b]: [site][4][12][12][12] complex (re, im interleaved), out_mag[b]
+ * the magnitudes, for b = 0 (proton) and 1 (neutron); entries that are not
+ * independent components are zero. */
+int o3_blocks(const o3_plan *p, int64_t n_sites, const double *S_in, double *fm_p, double *fm_n, double *mag_p,
+              double *mag_n) {
+    const int64_t NB = 4 * 12 * 12 * 12;
+    cplx *fm[2]; double *fmm[2];
+    blocks_batch(p, (int)n_sites, (const cplx *)S_in, fm, fmm);
+    memcpy(fm_p, fm[0], sizeof(cplx) * (size_t)(NB * n_sites));
+    memcpy(fm_n, fm[1], sizeof(cplx) * (size_t)(NB * n_sites));
+    memcpy(mag_p, fmm[0], sizeof(double) * (size_t)(NB * n_sites));
+    memcpy(mag_n, fmm[1], sizeof(double) * (size_t)(NB * n_sites));
+    for (int b = 0; b < 2; ++b) { free(fm[b]); free(fmm[b]); }
+    return 0;
+}
+
+/* The recursion and contraction (eq. recr_F, eq. C_final) for n_items sets of
+ * given blocks, e.g. blocks summed over sink sites with a momentum phase
+ * (Sec. 2). Layouts as o3_blocks; out: [item][n_req] complex, scale:
+ * [item][n_req] (the magnitude recursion run on the given magnitudes). */
+int o3_eval_blocks(const o3_plan *p, int64_t n_items, const double *fm_p, const double *fm_n, const double *mag_p,
+                   const double *mag_n, double *out, double *scale) {
+    cplx *fm[2] = {(cplx *)fm_p, (cplx *)fm_n};
+    double *fmm[2] = {(double *)mag_p, (double *)mag_n};
+    recursion_batch(p, (int)n_items, fm, fmm, 0, out, scale);
     return 0;
 }

@@ -50,6 +50,10 @@ def _load():
             lib.o3_norm.restype = ctypes.c_double
             lib.o3_eval.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_int]
             lib.o3_eval.restype = ctypes.c_int
+            lib.o3_blocks.argtypes = [P, ctypes.c_int64, P, P, P, P, P]
+            lib.o3_blocks.restype = ctypes.c_int
+            lib.o3_eval_blocks.argtypes = [P, ctypes.c_int64, P, P, P, P, P, P]
+            lib.o3_eval_blocks.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -120,4 +124,29 @@ class Plan:
         rc = self._lib.o3_eval(self._h, n, S.ctypes.data, out.ctypes.data, sc.ctypes.data, int(batch))
         if rc != 0:
             raise RuntimeError("o3_eval failed")
+        return out, sc
+
+    def blocks(self, S: np.ndarray):
+        """Antisymmetric block components per site (Sec. 2, Sec. 4):
+        (f_P, f_N, |f_P|, |f_N|), each (n_sites, 4, 12, 12, 12)."""
+        S = np.ascontiguousarray(np.asarray(S, dtype=np.complex128).reshape(-1, 12, 12))
+        n = S.shape[0]
+        shp = (n, 4, 12, 12, 12)
+        fp = np.zeros(shp, dtype=np.complex128)
+        fn = np.zeros(shp, dtype=np.complex128)
+        mp = np.zeros(shp)
+        mn = np.zeros(shp)
+        self._lib.o3_blocks(self._h, n, S.ctypes.data, fp.ctypes.data, fn.ctypes.data, mp.ctypes.data, mn.ctypes.data)
+        return fp, fn, mp, mn
+
+    def evaluate_blocks(self, fp, fn, mp, mn):
+        """Recursion and contraction from given blocks (e.g. momentum-projected
+        ones): arrays (n_items, 4, 12, 12, 12) as from ``blocks``. Returns
+        (C, scale), each (n_items, n_req)."""
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=t)) for a, t in
+                ((fp, np.complex128), (fn, np.complex128), (mp, np.float64), (mn, np.float64))]
+        n = arrs[0].shape[0]
+        out = np.zeros((n, len(self.requests)), dtype=np.complex128)
+        sc = np.zeros((n, len(self.requests)), dtype=np.float64)
+        self._lib.o3_eval_blocks(self._h, n, *[a.ctypes.data for a in arrs], out.ctypes.data, sc.ctypes.data)
         return out, sc

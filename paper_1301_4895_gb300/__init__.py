@@ -66,14 +66,16 @@ class Props(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("sites_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
-                ("wave_sites", ctypes.c_int32), ("regime", ctypes.c_int32), ("zchunk", ctypes.c_int32)]
+                ("wave_sites", ctypes.c_int32), ("regime", ctypes.c_int32), ("zchunk", ctypes.c_int32),
+                ("wave_order", ctypes.c_int32)]
 
-    FIELDS = ("sites_per_cta", "threads_per_cta", "wave_sites", "regime", "zchunk")
+    FIELDS = ("sites_per_cta", "threads_per_cta", "wave_sites", "regime", "zchunk", "wave_order")
 
 
 class ContractOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("n_mom", ctypes.c_int32), ("mom", ctypes.c_void_p),
-                ("t0", ctypes.c_int32), ("t1", ctypes.c_int32), ("tune", ctypes.c_void_p)]
+                ("t0", ctypes.c_int32), ("t1", ctypes.c_int32), ("tune", ctypes.c_void_p),
+                ("sink_mode", ctypes.c_int32)]
 
 
 _lib = None
@@ -221,8 +223,11 @@ def _stream_ptr(stream):
     return int(stream.cuda_stream)
 
 
+SINK_POINT, SINK_BLOCK_MOMENTUM = 0, 1
+
+
 def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0, t1: int = 0, tune=None,
-             out=None, stream=None, dims=None):
+             out=None, stream=None, dims=None, sink: int = SINK_POINT):
     """``mbc_contract`` on a u = d propagator field.
 
     field: torch tensor (device memory) or numpy array (host memory) of shape
@@ -258,7 +263,7 @@ def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0
             out = np.zeros(oshape, dtype=np.complex128)
         else:
             import torch
-            out = torch.zeros(oshape, dtype=torch.complex128, device=field.device)
+            out = torch.empty(oshape, dtype=torch.complex128, device=field.device)  # the library zero-fills
     optr = out.ctypes.data if is_np else out.data_ptr()
     pr = Props(ptr, ptr, dtype, MEM_HOST if is_np else MEM_DEVICE, n_cfg, nt, lx, ly, lz, 0, 0)
     tn = None
@@ -267,7 +272,7 @@ def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0
         if unknown:
             raise ValueError(f"unknown tune fields {sorted(unknown)}")
         tn = Tune(*[int(tune.get(f, 0)) for f in Tune.FIELDS])
-    op = ContractOpts(precision, moms.shape[0], moms.ctypes.data, t0, t1, ctypes.addressof(tn) if tn else None)
+    op = ContractOpts(precision, moms.shape[0], moms.ctypes.data, t0, t1, ctypes.addressof(tn) if tn else None, sink)
     handles = (ctypes.c_void_p * len(lists))(*[tl.handle for tl in lists])
     rc = lib.mbc_contract(ctypes.byref(pr), handles, len(lists), ctypes.byref(op), optr, _stream_ptr(stream))
     _check(rc, "mbc_contract")
@@ -290,7 +295,7 @@ def contract_noalloc(field, term_list, out, moms=((0, 0, 0),), t0: int = 0, t1: 
     dtype = C128 if field.dtype == torch.complex128 else C64
     moms = np.ascontiguousarray(np.array(moms, dtype=np.int32).reshape(-1, 3))
     pr = Props(field.data_ptr(), field.data_ptr(), dtype, MEM_DEVICE, n_cfg, nt, lx, ly, lz, 0, 0)
-    op = ContractOpts(FP64, moms.shape[0], moms.ctypes.data, t0, t1, None)
+    op = ContractOpts(FP64, moms.shape[0], moms.ctypes.data, t0, t1, None, SINK_POINT)
     _check(lib.mbc_contract_noalloc(ctypes.byref(pr), term_list.handle, ctypes.byref(op), out.data_ptr(),
                                     _stream_ptr(stream)), "mbc_contract_noalloc")
     return out

@@ -45,15 +45,15 @@ def candidates(lists, precision):
     small = any(tl.spec["dirac_dim"] == 2 for tl in lists)  # nonrelativistic: shared-memory kernels
     large = any(tl.spec["dirac_dim"] == 4 for tl in lists)  # relativistic: wave kernels
     fp64 = precision == FP64
-    opt_small = [{"sites_per_cta": s} for s in (8, 12, 16, 20, 24, 32)] if fp64 else \
+    opt_small = [{"sites_per_cta": s} for s in (2, 4, 8, 12, 16, 20, 24, 32)] if fp64 else \
         [{"threads_per_cta": t} for t in (256, 512, 768, 1024)]
     if not small:
         opt_small = [{}]
     opt_large = [{}]
     if large:
-        opt_large = [dict(w, **z) for w, z in itertools.product(
+        opt_large = [dict(w, **z, **o) for w, z, o in itertools.product(
             [{}, {"wave_sites": 128}, {"wave_sites": 512}, {"wave_sites": 2048}],
-            [{}, {"zchunk": 4}, {"zchunk": 32}])]
+            [{}, {"zchunk": 4}, {"zchunk": 32}], [{}, {"wave_order": 1}])]
     for a, b in itertools.product(opt_small, opt_large):
         yield dict(a, **b)
 

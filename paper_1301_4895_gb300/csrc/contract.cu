@@ -11,12 +11,14 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <vector>
 
 #include "large_kernel.cuh"
 #include "mbc_internal.h"
 #include "probe.cuh"
+#include "project_kernel.cuh"
 #include "small_kernel.cuh"
 
 namespace mbc {
@@ -335,6 +337,31 @@ int sm_count(int device) {
     return n;
 }
 
+// cudaFuncSetAttribute / occupancy queries cost host time on every call;
+// both are cached per (kernel, device, block size, shared memory)
+mbc_status prepare_kernel(const void *kern, int device, int threads, size_t smem, int *per_sm) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, size_t>, int> occ;
+    static std::map<std::pair<const void *, int>, size_t> smem_set;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_tuple(kern, device, threads, smem);
+    auto it = occ.find(key);
+    if (it != occ.end()) {
+        *per_sm = it->second;
+        return MBC_OK;
+    }
+    size_t &have = smem_set[{kern, device}];
+    if (smem > have) {
+        MBC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        have = smem;
+    }
+    int n = 0;
+    MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem));
+    occ[key] = n;
+    *per_sm = n;
+    return MBC_OK;
+}
+
 // ---- launchers -------------------------------------------------------------
 
 // Small-stage kernels. FP64: one warp per site (k_small). MIXED: 32 sites
@@ -349,7 +376,7 @@ struct SmallLaunch {
 };
 
 SmallLaunch size_small_batch(const std::vector<const DeviceCache *> &cs, const FieldDesc &F, const mbc_tune *tune,
-                             bool mixed, int32_t &site_stride, int32_t &comp_stride) {
+                             bool mixed, int32_t &site_stride, int32_t &comp_stride, int n_sm = 0) {
     SmallLaunch l;
     site_stride = 0;
     comp_stride = 0;
@@ -360,7 +387,13 @@ SmallLaunch size_small_batch(const std::vector<const DeviceCache *> &cs, const F
     if (!mixed) {
         const int64_t per_site = site_stride * 16LL + 16LL * comp_stride;
         l.T = (int)std::min<int64_t>(32, kSmemLimit / per_site);
-        if (tune && tune->sites_per_cta > 0) l.T = std::min(l.T, tune->sites_per_cta);
+        if (tune && tune->sites_per_cta > 0) {
+            l.T = std::min(l.T, tune->sites_per_cta);
+        } else if (n_sm > 0) {
+            // small lattices: fewer sites per CTA so that every SM gets a tile
+            const int64_t sites = (int64_t)F.n_cfg * F.n_t * F.lx * F.ly * F.lz;
+            l.T = (int)std::max<int64_t>(1, std::min<int64_t>(l.T, (sites + n_sm - 1) / n_sm));
+        }
         l.threads = 32 * l.T;
         l.smem = (size_t)l.T * per_site;
     } else {
@@ -381,9 +414,9 @@ mbc_status launch_small_batch(const SmallBatch &B, const FieldDesc &F, const Mom
                               bool mixed, int device, cudaStream_t stream, const double2 *phase, double2 *partial,
                               bool timed) {
     auto kern = mixed ? k_small_ls<MixedTraits> : k_small<FP64Traits>;
-    MBC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem));
     int per_sm = 0;
-    MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, l.threads, l.smem));
+    mbc_status pst = prepare_kernel((const void *)kern, device, l.threads, l.smem, &per_sm);
+    if (pst != MBC_OK) return pst;
     if (per_sm < 1) return MBC_ERR_UNSUPPORTED;
     int64_t grid = std::min<int64_t>(B.total_items, (int64_t)per_sm * sm_count(device));
     if (grid < 1) return MBC_OK;
@@ -447,7 +480,11 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
     const int nsm = sm_count(device);
     const int nxi = L->nxi;
     const size_t blk_smem = (size_t)16 * 4 * nxi * nxi * sizeof(V);
-    MBC_CUDA_TRY(cudaFuncSetAttribute(k_large_blocks<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk_smem));
+    {
+        int per_sm = 0;
+        mbc_status pst = prepare_kernel((const void *)k_large_blocks<Tr>, device, 512, blk_smem, &per_sm);
+        if (pst != MBC_OK) return pst;
+    }
     for (int64_t item0 = 0; item0 < n_items; item0 += W) {
         WaveDesc wv;
         wv.item0 = item0;
@@ -476,7 +513,8 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
             {
                 TimedLaunch tl(stream);
                 k_large_step<Tr><<<(unsigned)grid, threads, 0, stream>>>(c->d_opx[m], c->d_opy[m], s.n_z, s.k,
-                                                                         zchunk, W, X, Y, Z);
+                                                                         zchunk, W, tune ? tune->wave_order : 0, X,
+                                                                         Y, Z);
             }
             MBC_CUDA_TRY(cudaGetLastError());
             X = Z;
@@ -485,7 +523,7 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
             int64_t items = (int64_t)L->n_comp * (W / 32);
             int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
             k_large_contract<Tr><<<(unsigned)grid, 256, 0, stream>>>(c->d_fin_off, c->d_fin_z, c->d_fin_l, L->n_comp,
-                                                                     W, X, sexp, L->A, 1.0 / L->norm, Cb);
+                                                                     W, X, sexp, 3 * L->A, 1.0 / L->norm, Cb);
             MBC_CUDA_TRY(cudaGetLastError());
         }
         {
@@ -495,6 +533,107 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
         }
     }
     return MBC_OK;
+}
+
+// Momentum-projected blocks: per-site blocks summed over sites with the phase
+// (FP64), then the recursion once per (slab, momentum) item on the wave kernels.
+template <class Tr>
+mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const FieldDesc &F, const MomDesc &M,
+                         const mbc_tune *tune, int device, cudaStream_t stream, char *scratch, const double2 *phase,
+                         int li, int n_lists, int comp_max, double2 *out, int64_t n_slabs, const LargeSizes &ls) {
+    using V = typename Tr::V;
+    const int nxi = L->nxi, bs = (int)L->block_size;
+    const int v3 = F.lx * F.ly * F.lz;
+    const int tps = (v3 + 15) / 16;
+    const int64_t n_tiles = n_slabs * tps;
+    const int64_t n_out = 2LL * bs;
+    char *p = scratch;
+    double2 *partial = reinterpret_cast<double2 *>(p);
+    p += align256((size_t)n_tiles * M.n_mom * n_out * sizeof(double2));
+    double2 *Pf = reinterpret_cast<double2 *>(p);
+    p += align256((size_t)n_slabs * M.n_mom * n_out * sizeof(double2));
+    const int W = ls.W;
+    V *fP = reinterpret_cast<V *>(p);
+    p += align256(ls.blk_bytes);
+    V *fN = reinterpret_cast<V *>(p);
+    p += align256(ls.blk_bytes);
+    V *buf[2];
+    buf[0] = reinterpret_cast<V *>(p);
+    p += align256(ls.stage_bytes);
+    buf[1] = reinterpret_cast<V *>(p);
+    p += align256(ls.stage_bytes);
+    double2 *Cb = reinterpret_cast<double2 *>(p);
+    p += align256(ls.c_bytes);
+    int32_t *sexp = reinterpret_cast<int32_t *>(p);
+    const int nsm = sm_count(device);
+    // 1. blocks of every site, phase-weighted tile sums, reduction over tiles
+    const size_t smem = (size_t)16 * 4 * nxi * nxi * sizeof(double2);
+    {
+        int per_sm = 0;
+        mbc_status pst = prepare_kernel((const void *)k_project_blocks, device, 512, smem, &per_sm);
+        if (pst != MBC_OK) return pst;
+    }
+    {
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)nsm * 8));
+        k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nxi, L->dim == 4 ? 4 : 2, bs,
+                                                                (int)binom64(nxi, 2), L->need_block[0],
+                                                                L->need_block[1], tps, n_tiles, partial);
+        MBC_CUDA_TRY(cudaGetLastError());
+        const int64_t outs = n_slabs * M.n_mom * n_out;
+        const unsigned rg = (unsigned)std::min<int64_t>((outs + 7) / 8, 65535);
+        k_reduce_tiles<<<std::max(rg, 1u), 256, 0, stream>>>(partial, n_slabs, tps, M.n_mom, (int)n_out, F.n_t, 0, 1,
+                                                            (int)n_out, Pf);
+        MBC_CUDA_TRY(cudaGetLastError());
+    }
+    // 2. recursion and contraction per item, a wave of W items at a time
+    const int64_t n_items = n_slabs * M.n_mom;
+    for (int64_t item0 = 0; item0 < n_items; item0 += W) {
+        k_load_proj_blocks<Tr><<<(unsigned)((W + 7) / 8), 256, 0, stream>>>(Pf, n_items, item0, W, bs, fP, fN, sexp);
+        MBC_CUDA_TRY(cudaGetLastError());
+        const V *X = L->path[0] == MBC_PROTON ? fP : fN;
+        for (size_t m = 0; m < L->steps.size(); ++m) {
+            const Step &s = L->steps[m];
+            V *Z = buf[(m + 1) & 1];
+            const V *Y = s.baryon == MBC_PROTON ? fP : fN;
+            const int threads = 256;
+            const int64_t total_warps = (int64_t)nsm * 8 * (threads / 32);
+            const int64_t ngroups = W / 32;
+            int64_t zchunk = (s.n_z * ngroups + 8 * total_warps - 1) / (8 * total_warps);
+            zchunk = std::max<int64_t>(1, std::min<int64_t>(zchunk, 256));
+            if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
+            const int64_t items = ((s.n_z + zchunk - 1) / zchunk) * ngroups;
+            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
+            {
+                TimedLaunch tl(stream);
+                k_large_step<Tr><<<(unsigned)grid, threads, 0, stream>>>(c->d_opx[m], c->d_opy[m], s.n_z, s.k,
+                                                                         zchunk, W, tune ? tune->wave_order : 0, X,
+                                                                         Y, Z);
+            }
+            MBC_CUDA_TRY(cudaGetLastError());
+            X = Z;
+        }
+        {
+            const int64_t items = (int64_t)L->n_comp * (W / 32);
+            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
+            k_large_contract<Tr><<<(unsigned)grid, 256, 0, stream>>>(c->d_fin_off, c->d_fin_z, c->d_fin_l, L->n_comp,
+                                                                     W, X, sexp, L->A, 1.0 / L->norm, Cb);
+            MBC_CUDA_TRY(cudaGetLastError());
+            const int64_t tot = (int64_t)L->n_comp * W;
+            const unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 65535));
+            k_write_items<<<g2, 256, 0, stream>>>(Cb, n_items, item0, W, L->n_comp, M.n_mom, F.n_t, li, n_lists,
+                                                  comp_max, out);
+            MBC_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    return MBC_OK;
+}
+
+size_t projected_bytes(const mbc_term_list *L, const MomDesc &M, int v3, int64_t n_slabs, const LargeSizes &ls) {
+    const int tps = (v3 + 15) / 16;
+    const int64_t n_out = 2 * L->block_size;
+    return align256((size_t)n_slabs * tps * M.n_mom * n_out * sizeof(double2)) +
+           align256((size_t)n_slabs * M.n_mom * n_out * sizeof(double2)) + 2 * align256(ls.blk_bytes) +
+           2 * align256(ls.stage_bytes) + align256(ls.c_bytes) + align256(ls.sexp_bytes);
 }
 
 }  // namespace
@@ -591,6 +730,41 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     const int64_t n_slabs = (int64_t)props->n_cfg * n_t;
     const bool mixed = opts->precision == MBC_MIXED;
 
+    if (opts->sink_mode != MBC_SINK_POINT && opts->sink_mode != MBC_SINK_BLOCK_MOMENTUM) return MBC_ERR_INVALID_ARG;
+    if (opts->sink_mode == MBC_SINK_BLOCK_MOMENTUM) {
+        // every baryon's block projected to the momentum, one recursion per item
+        const int64_t n_items_p = n_slabs * M.n_mom;
+        std::vector<DeviceCache *> cs((size_t)n_lists, nullptr);
+        std::vector<LargeSizes> lsz((size_t)n_lists);
+        size_t need = 0;
+        for (int li = 0; li < n_lists; ++li) {
+            const mbc_term_list *L = lists[li];
+            if (L->pauli_forbidden || L->n_comp == 0) continue;
+            cs[(size_t)li] = get_cache(L, device, st);
+            if (!cs[(size_t)li]) return st;
+            lsz[(size_t)li] = mixed ? large_sizes<MixedTraits>(L, cs[(size_t)li], opts->tune, n_items_p)
+                                    : large_sizes<FP64Traits>(L, cs[(size_t)li], opts->tune, n_items_p);
+            need = std::max(need, projected_bytes(L, M, (int)v3, n_slabs, lsz[(size_t)li]));
+        }
+        const size_t phase_bytes_p = align256((size_t)v3 * M.n_mom * sizeof(double2));
+        void *scr_p = nullptr;
+        if ((st = scratch_get(device, stream, phase_bytes_p + need, &scr_p)) != MBC_OK) return st;
+        double2 *phase_p = reinterpret_cast<double2 *>(scr_p);
+        unsigned pg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((v3 * M.n_mom + 255) / 256, 4096));
+        k_phase_table<<<pg, 256, 0, stream>>>(F, M, phase_p);
+        MBC_CUDA_TRY(cudaGetLastError());
+        for (int li = 0; li < n_lists; ++li) {
+            if (!cs[(size_t)li]) continue;
+            char *rest_p = reinterpret_cast<char *>(scr_p) + phase_bytes_p;
+            st = mixed ? run_projected<MixedTraits>(lists[li], cs[(size_t)li], F, M, opts->tune, device, stream,
+                                                    rest_p, phase_p, li, n_lists, comp_max,
+                                                    reinterpret_cast<double2 *>(dev_out), n_slabs, lsz[(size_t)li])
+                       : run_projected<FP64Traits>(lists[li], cs[(size_t)li], F, M, opts->tune, device, stream, rest_p,
+                                                   phase_p, li, n_lists, comp_max,
+                                                   reinterpret_cast<double2 *>(dev_out), n_slabs, lsz[(size_t)li]);
+            if (st != MBC_OK) return st;
+        }
+    } else {
     // plan every list: regime and scratch bytes; small-regime lists go into
     // batches (most operations per site first) contracted by one launch each
     const int v3p = (int)((v3 + 31) / 32 * 32);
@@ -636,7 +810,7 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
             ++i;
         }
         std::memset(&br.B, 0, sizeof(br.B));
-        br.sl = size_small_batch(cs, F, opts->tune, mixed, br.B.site_stride, br.B.comp_stride);
+        br.sl = size_small_batch(cs, F, opts->tune, mixed, br.B.site_stride, br.B.comp_stride, sm_count(device));
         br.B.n_lists = (int)br.ids.size();
         br.B.tiles_per_slab = br.sl.tiles_per_slab;
         int64_t items = 0, poff = 0;
@@ -682,7 +856,7 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     auto reduce = [&](int li, const double2 *partial, int tiles_per_slab) -> mbc_status {
         const mbc_term_list *L = lists[li];
         int64_t outs = n_slabs * M.n_mom * L->n_comp;
-        unsigned grid = (unsigned)std::min<int64_t>((outs + 255) / 256, 65535);
+        unsigned grid = (unsigned)std::min<int64_t>((outs + 7) / 8, 65535);
         k_reduce_tiles<<<std::max(grid, 1u), 256, 0, stream>>>(partial, n_slabs, tiles_per_slab, M.n_mom, L->n_comp,
                                                               n_t, li, n_lists, comp_max,
                                                               reinterpret_cast<double2 *>(dev_out));
@@ -711,6 +885,8 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
         if (st != MBC_OK) return st;
         if ((st = reduce(li, partial, v3p / 32)) != MBC_OK) return st;
     }
+
+    }  // point sinks
 
     if (props->memory == MBC_MEM_HOST) {
         MBC_CUDA_TRY(cudaMemcpyAsync(out, dev_out, out_bytes, cudaMemcpyDeviceToHost, stream));
@@ -857,6 +1033,7 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     if (!props || !list || !opts || !out || !props->s_u || !props->s_d) return MBC_ERR_INVALID_ARG;
     if (props->s_u != props->s_d) return MBC_ERR_UNSUPPORTED;
     if (props->memory != MBC_MEM_DEVICE || opts->precision != MBC_FP64) return MBC_ERR_UNSUPPORTED;
+    if (opts->sink_mode != MBC_SINK_POINT) return MBC_ERR_UNSUPPORTED;
     if (props->dtype != MBC_C128 && props->dtype != MBC_C64) return MBC_ERR_INVALID_ARG;
     if (props->n_cfg < 1 || props->nt < 1 || props->lx < 1 || props->ly < 1 || props->lz < 1) return MBC_ERR_INVALID_ARG;
     if (opts->n_mom < 1 || opts->n_mom > kMaxMom || !opts->mom) return MBC_ERR_INVALID_ARG;
@@ -936,7 +1113,7 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     B.plan[0] = c->sp;
     if ((st = launch_small_batch(B, F, M, l, false, device, stream, phase, partial, false)) != MBC_OK) return st;
     const int64_t outs = n_slabs * M.n_mom * list->n_comp;
-    const unsigned rgrid = (unsigned)std::min<int64_t>((outs + 255) / 256, 65535);
+    const unsigned rgrid = (unsigned)std::min<int64_t>((outs + 7) / 8, 65535);
     k_reduce_tiles<<<std::max(rgrid, 1u), 256, 0, stream>>>(partial, n_slabs, B.tiles_per_slab, M.n_mom,
                                                             list->n_comp, n_t, 0, 1, comp_max,
                                                             reinterpret_cast<double2 *>(out));

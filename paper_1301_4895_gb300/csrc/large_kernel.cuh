@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, 
 // entries and nearby rows of X.
 template <class Tr>
 __global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__ opx, const uint16_t *__restrict__ opy,
-                                                    int64_t n_z, int64_t k, int64_t zchunk, int W,
+                                                    int64_t n_z, int64_t k, int64_t zchunk, int W, int order,
                                                     const typename Tr::V *__restrict__ X,
                                                     const typename Tr::V *__restrict__ Y, typename Tr::V *__restrict__ Z) {
     const int lane = threadIdx.x & 31;
@@ -117,9 +117,22 @@ __global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int ngroups = W >> 5;
     const int64_t nchunks = (n_z + zchunk - 1) / zchunk;
+    const int wpb = blockDim.x >> 5;
     for (int64_t item = warp_global; item < nchunks * ngroups; item += nwarps) {
-        const int64_t chunk = item / ngroups;
-        const int col = (int)(item % ngroups) * 32 + lane;
+        // order 0: consecutive warps take the site groups of one chunk (they
+        // share op words); order 1: the warps of a CTA take consecutive chunks
+        // of one site group (they share rows of X and Y in L1)
+        int64_t chunk;
+        int group;
+        if (order == 0 || nchunks % wpb != 0) {
+            chunk = item / ngroups;
+            group = (int)(item % ngroups);
+        } else {
+            const int64_t blk = item / wpb;
+            group = (int)(blk % ngroups);
+            chunk = (blk / ngroups) * wpb + item % wpb;
+        }
+        const int col = group * 32 + lane;
         const int64_t z_begin = chunk * zchunk;
         const int64_t z_end = min(n_z, z_begin + zchunk);
         const int64_t o_begin = z_begin * k, o_end = z_end * k;
@@ -156,8 +169,8 @@ __global__ void __launch_bounds__(256) k_large_contract(const int64_t *__restric
                                                         const uint32_t *__restrict__ fin_z,
                                                         const double *__restrict__ fin_l, int n_comp, int W,
                                                         const typename Tr::V *__restrict__ FA,
-                                                        const int32_t *__restrict__ sexp, int A, double inv_norm,
-                                                        double2 *__restrict__ Cout) {
+                                                        const int32_t *__restrict__ sexp, int degree,
+                                                        double inv_norm, double2 *__restrict__ Cout) {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(256) k_large_contract(const int64_t *__restric
             re = __fma_rn(l, f.x, re);
             im = __fma_rn(l, f.y, im);
         }
-        int ue = -3 * A * sexp[col];
+        int ue = -degree * sexp[col];  // C is homogeneous of this degree in the scaled inputs
         Cout[(int64_t)c * W + col] = make_double2(scalbn(re * inv_norm, ue), scalbn(im * inv_norm, ue));
     }
 }
@@ -204,29 +217,50 @@ __global__ void __launch_bounds__(256) k_large_sitesum(FieldDesc F, WaveDesc wv,
     }
 }
 
-// Final reduction over the tiles of each slab (Neumaier-compensated, fixed
-// order): out[cfg][list][t - t0][mom][comp_stride].
+// Final reduction over the tiles of each slab: one warp per output, lanes
+// take tiles lane, lane + 32, ... with Neumaier compensation, then a fixed
+// xor tree combines the lanes' (sum, compensation) pairs - a fixed order, so
+// results are bitwise reproducible. out[cfg][list][t - t0][mom][comp_stride].
+__device__ __forceinline__ void neumaier(double &s, double &c, double v) {
+    const double t = s + v;
+    c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+}
 __global__ void k_reduce_tiles(const double2 *__restrict__ partial, int64_t n_slabs, int tiles_per_slab, int n_mom,
                                int n_comp, int n_t, int list_idx, int n_lists, int comp_stride, double2 *out) {
     const int64_t per_slab = (int64_t)n_mom * n_comp;
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_slabs * per_slab;
-         o += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t o = wid; o < n_slabs * per_slab; o += nw) {
         const int64_t slab = o / per_slab;
         const int r = (int)(o % per_slab);
         double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
-        for (int tl = 0; tl < tiles_per_slab; ++tl) {
-            double2 v = partial[(slab * tiles_per_slab + tl) * per_slab + r];
-            double t = sr + v.x;
-            cr += fabs(sr) >= fabs(v.x) ? (sr - t) + v.x : (v.x - t) + sr;
-            sr = t;
-            t = si + v.y;
-            ci += fabs(si) >= fabs(v.y) ? (si - t) + v.y : (v.y - t) + si;
-            si = t;
+        for (int tl = lane; tl < tiles_per_slab; tl += 32) {
+            const double2 v = partial[(slab * tiles_per_slab + tl) * per_slab + r];
+            neumaier(sr, cr, v.x);
+            neumaier(si, ci, v.y);
         }
-        const int cfg = (int)(slab / n_t), tt = (int)(slab % n_t);
-        const int q = r / n_comp, c = r % n_comp;
-        int64_t oi = ((((int64_t)cfg * n_lists + list_idx) * n_t + tt) * n_mom + q) * comp_stride + c;
-        out[oi] = make_double2(sr + cr, si + ci);
+        for (int off = 16; off > 0; off >>= 1) {
+            const double osr = __shfl_xor_sync(0xffffffffu, sr, off), ocr = __shfl_xor_sync(0xffffffffu, cr, off);
+            const double osi = __shfl_xor_sync(0xffffffffu, si, off), oci = __shfl_xor_sync(0xffffffffu, ci, off);
+            // both partners add in the same order, so they agree bit for bit
+            double ar = lane & off ? osr : sr, br = lane & off ? sr : osr;
+            double ai = lane & off ? osi : si, bi = lane & off ? si : osi;
+            double ccr = cr + ocr, cci = ci + oci;
+            sr = ar;
+            cr = ccr;
+            neumaier(sr, cr, br);
+            si = ai;
+            ci = cci;
+            neumaier(si, ci, bi);
+        }
+        if (lane == 0) {
+            const int cfg = (int)(slab / n_t), tt = (int)(slab % n_t);
+            const int q = r / n_comp, c = r % n_comp;
+            const int64_t oi = ((((int64_t)cfg * n_lists + list_idx) * n_t + tt) * n_mom + q) * comp_stride + c;
+            out[oi] = make_double2(sr + cr, si + ci);
+        }
     }
 }
 

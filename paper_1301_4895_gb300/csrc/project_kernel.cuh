@@ -1,0 +1,139 @@
+// Momentum-projected blocks (Sec. 2: blocks carry a sink function s(x); here
+// every baryon uses s(x) = exp(-2 pi i n.x / L)), then one recursion per
+// (configuration, time slice, momentum) on the summed blocks.
+//
+//   k_project_blocks   per-site antisymmetric blocks in FP64, multiplied by
+//                      the phase and summed over the 16 sites of a tile by a
+//                      fixed half-warp tree -> tile partials, reduced over
+//                      tiles by k_reduce_tiles (compensated, fixed order);
+//   k_load_proj_blocks copies the summed blocks of a wave of items into the
+//                      [component][item] layout of the wave kernels (MIXED:
+//                      exact power-of-two scaling per item);
+//   k_write_items      writes each item's contracted components to out.
+#pragma once
+
+#include "large_kernel.cuh"
+
+namespace mbc {
+
+__global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
+                                                        int nxi, int n_g2, int block_size, int npair, int need_p,
+                                                        int need_n, int tiles_per_slab, int64_t n_tiles,
+                                                        double2 *__restrict__ partial) {
+    constexpr int NS = 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *S = reinterpret_cast<double2 *>(smem_raw);  // [NS][nxi*nxi]
+    double2 *Q = S + NS * nxi * nxi;                     // [NS][3*nxi*nxi]
+    const int sl = threadIdx.x % NS, slice = threadIdx.x / NS, nslice = blockDim.x / NS;
+    const int nent = nxi * nxi;
+    const int v3 = F.lx * F.ly * F.lz;
+    const int n_out = 2 * block_size;  // proton block, then neutron block
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t slab = tile / tiles_per_slab;
+        const int tin = (int)(tile % tiles_per_slab);
+        const int cfg = (int)(slab / F.n_t), t = F.t0 + (int)(slab % F.n_t);
+        __syncthreads();  // shared memory of the previous tile is free
+        for (int s = threadIdx.x >> 5; s < NS; s += blockDim.x >> 5) {
+            const int lane = threadIdx.x & 31;
+            const int site = tin * NS + s;
+            const bool live = site < v3;
+            const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * 144;
+            for (int e = lane; e < nent; e += 32)
+                S[s * nent + e] = live ? load_prop(F, base, (e / nxi) * 12 + (e % nxi)) : make_double2(0, 0);
+        }
+        __syncthreads();
+        for (int e = slice; e < 3 * nent; e += nslice) {
+            const int c = e / nent, r = e % nent;
+            Q[sl * 3 * nent + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
+        }
+        __syncthreads();
+        const int site = tin * NS + sl;
+        const bool live = site < v3;
+        const double2 *Ss = S + sl * nent;
+        const double2 *Qs = Q + sl * 3 * nent;
+        const int per_spin = npair * nxi;
+        for (int b = 0; b < 2; ++b) {
+            const bool need = b == 0 ? need_p : need_n;
+            // warp w takes entries (e0, e0 + 1) with e0 = 2w, 2w + nslice, ...: the
+            // trip count is uniform over the warp, so every shuffle has all lanes
+            for (int e0 = (threadIdx.x >> 5) * 2; e0 < block_size; e0 += nslice) {
+                const int e = e0 + ((threadIdx.x >> 4) & 1);
+                const bool ok = e < block_size;
+                double2 f = make_double2(0, 0);
+                if (need && live && ok) {
+                    const int dl = e / per_spin, r = e % per_spin;
+                    const int pr = r / nxi, single = r % nxi;
+                    const int i = c_pair_i[pr], j = c_pair_j[pr];
+                    for (int c = 0; c < 3; ++c) {
+                        const double2 *Sr = Ss + (3 * dl + c) * nxi;
+                        if (b == 0) {
+                            f = cfma(Sr[i], Qs[(c * nxi + j) * nxi + single], f);
+                            f = cfms(Sr[j], Qs[(c * nxi + i) * nxi + single], f);
+                        } else {
+                            f = cfma(Sr[i], Qs[(c * nxi + single) * nxi + j], f);
+                            f = cfms(Sr[j], Qs[(c * nxi + single) * nxi + i], f);
+                        }
+                    }
+                }
+                for (int q = 0; q < M.n_mom; ++q) {
+                    const double2 ph = live ? __ldg(phase + (int64_t)site * M.n_mom + q) : make_double2(0, 0);
+                    double re = __fma_rn(ph.x, f.x, -ph.y * f.y), im = __fma_rn(ph.x, f.y, ph.y * f.x);
+                    for (int off = NS >> 1; off > 0; off >>= 1) {  // fixed tree over the tile's 16 sites
+                        re += __shfl_xor_sync(0xffffffffu, re, off);
+                        im += __shfl_xor_sync(0xffffffffu, im, off);
+                    }
+                    if (sl == 0 && ok)
+                        partial[(tile * M.n_mom + q) * (int64_t)n_out + b * block_size + e] = make_double2(re, im);
+                }
+            }
+        }
+    }
+}
+
+// One warp per item (slab, momentum) of the wave: summed blocks -> wave layout.
+template <class Tr>
+__global__ void __launch_bounds__(256) k_load_proj_blocks(const double2 *__restrict__ Pf, int64_t n_items,
+                                                          int64_t item0, int W, int block_size,
+                                                          typename Tr::V *__restrict__ fP,
+                                                          typename Tr::V *__restrict__ fN, int32_t *__restrict__ sexp) {
+    const int lane = threadIdx.x & 31;
+    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (col >= W) return;
+    const int64_t item = item0 + col;
+    const bool live = item < n_items;
+    const double2 *src = Pf + (live ? item : 0) * 2 * (int64_t)block_size;
+    int se = 0;
+    if (sizeof(typename Tr::V) == sizeof(float2)) {
+        double amax = 0.0;
+        for (int e = lane; live && e < 2 * block_size; e += 32) {
+            const double2 v = src[e];
+            amax = fmax(amax, fmax(fabs(v.x), fabs(v.y)));
+        }
+        for (int off = 16; off > 0; off >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        se = amax > 0.0 ? -ilogb(amax) : 0;
+    }
+    for (int e = lane; e < block_size; e += 32) {
+        const double2 p = live ? src[e] : make_double2(0, 0);
+        const double2 n = live ? src[block_size + e] : make_double2(0, 0);
+        fP[(int64_t)e * W + col] = Tr::from_d(make_double2(scalbn(p.x, se), scalbn(p.y, se)));
+        fN[(int64_t)e * W + col] = Tr::from_d(make_double2(scalbn(n.x, se), scalbn(n.y, se)));
+    }
+    if (lane == 0) sexp[col] = se;
+}
+
+// out[cfg][list][t - t0][mom][comp_stride] = C[comp][item] for the wave's items
+__global__ void k_write_items(const double2 *__restrict__ C, int64_t n_items, int64_t item0, int W, int n_comp,
+                              int n_mom, int n_t, int list_idx, int n_lists, int comp_stride, double2 *out) {
+    const int64_t total = (int64_t)n_comp * W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / W), col = (int)(i % W);
+        const int64_t item = item0 + col;
+        if (item >= n_items) continue;
+        const int64_t slab = item / n_mom;
+        const int q = (int)(item % n_mom);
+        const int cfg = (int)(slab / n_t), tt = (int)(slab % n_t);
+        out[((((int64_t)cfg * n_lists + list_idx) * n_t + tt) * n_mom + q) * comp_stride + c] = C[i];
+    }
+}
+
+}  // namespace mbc

@@ -275,3 +275,51 @@ def test_out_of_memory_is_a_clean_error(mbc):
     out = mbc.contract(field[..., :, :], [small], precision=0)
     torch.cuda.synchronize()
     assert torch.count_nonzero(out).item() == 0
+
+
+def test_wave_order_and_chunking_variants(mbc):
+    """Every launch shape the autotuner may pick gives the oracle's result."""
+    dims = (2, 2, 2)
+    field = synth.field(14, 1, 2, dims, 0.4)
+    sp = (0, 1, 0, 1)
+    tl = mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])
+    for tune in ({"wave_order": 1, "zchunk": 8}, {"wave_order": 1, "zchunk": 3, "wave_sites": 32},
+                 {"wave_order": 0, "zchunk": 1}):
+        check_slabs(mbc, field, [tl], [(2, 2, 4)], dims, tune=tune)
+
+
+@pytest.mark.parametrize("n_p,n_n,D,spins", [(1, 0, 4, None), (1, 1, 2, None), (2, 1, 2, None), (2, 2, 2, None),
+                                             (2, 2, 4, [((0, 1, 0, 1), (0, 1, 0, 1))])])
+def test_momentum_projected_blocks(mbc, n_p, n_n, D, spins):
+    """Every baryon's block projected to the momentum before the recursion
+    (Sec. 2 sink functions), against the oracle's projection."""
+    from oracle import projection
+    dims = (2, 3, 4)
+    field = synth.field(21, 2, 2, dims, 0.4)
+    moms = ((0, 0, 0), (1, 0, 0), (0, 1, 3))
+    tl = mbc.build_term_list(n_p, n_n, D, spins=spins)
+    comps = tl.components()
+    plan = oracle_plan(n_p, n_n, D, comps)
+    outs = {p: run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM) for p in (0, 1)}
+    for cfg in range(2):
+        for t in range(2):
+            C, sc = projection.projected_correlators(plan, field[cfg, t], dims, moms)
+            for p in (0, 1):
+                got = outs[p][cfg, 0, t, :, : len(comps)]
+                assert np.all(np.abs(got - C) <= TOL[p] * sc), (p, cfg, t, float(np.max(np.abs(got - C) / sc)))
+
+
+def test_momentum_projected_blocks_full_slab(mbc):
+    """One 16^3 slab, relativistic 4He (0,1,0,1): the launch shape of a real
+    lattice, few items (one per momentum)."""
+    from oracle import projection
+    dims = (16, 16, 16)
+    field = synth.field(22, 1, 1, dims, 0.4)
+    moms = ((0, 0, 0), (1, 0, 0))
+    sp = (0, 1, 0, 1)
+    tl = mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])
+    plan = oracle_plan(2, 2, 4, tl.components())
+    C, sc = projection.projected_correlators(plan, field[0, 0], dims, moms)
+    for p in (0, 1):
+        got = run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM)[0, 0, 0, :, :1]
+        assert np.all(np.abs(got - C) <= TOL[p] * sc), p

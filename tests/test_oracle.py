@@ -300,3 +300,38 @@ def test_he4_rel_all_components_count():
     tot, per, stages = plan.ops()
     assert tot == 531321120  # Table 1
     assert len(plan.requests) == 36 * 36
+
+
+# ---- momentum-projected blocks (Sec. 2 sink functions) ----------------------------
+
+def test_projected_blocks_pins(rng):
+    from oracle import projection
+    plan = recursion.Plan(2, 2, 2)
+    S0 = rand_prop(rng)
+    # one site: projection is the point correlator
+    C1, _ = projection.projected_correlators(plan, S0.reshape(1, 1, 1, 12, 12), (1, 1, 1), [(0, 0, 0)])
+    Cs, _ = plan.evaluate(S0[None])
+    assert np.allclose(C1, Cs, rtol=1e-13, atol=0)
+    # uniform field: every block is V times the site's block, C scales as V^A;
+    # any nonzero momentum sums the phases to zero
+    dims = (2, 3, 4)
+    V = 24
+    uni = np.broadcast_to(S0, dims + (12, 12)).copy()
+    C, sc = projection.projected_correlators(plan, uni, dims, [(0, 0, 0), (1, 0, 0), (0, 1, 2)])
+    assert abs(C[0, 0] - V ** 4 * Cs[0, 0]) <= 1e-12 * sc[0, 0]
+    assert np.all(np.abs(C[1:]) <= 1e-13 * sc[0, 0])
+
+
+def test_projected_blocks_translation_phase(rng):
+    """Shifting the field by a along x multiplies every momentum-n block by
+    exp(-2 pi i n_x a / L_x), so C picks up exp(-2 pi i A n_x a / L_x)."""
+    from oracle import projection
+    plan = recursion.Plan(1, 1, 2)
+    dims = (1, 2, 4)  # (Lz, Ly, Lx)
+    field = rand_prop(rng, 8).reshape(dims + (12, 12))
+    moved = np.roll(field, 1, axis=2)  # S'(x) = S(x - 1)
+    mom = [(1, 0, 0)]
+    C, sc = projection.projected_correlators(plan, field, dims, mom)
+    C2, _ = projection.projected_correlators(plan, moved, dims, mom)
+    expect = C * np.exp(-2j * np.pi * 2 * 1 / 4)
+    assert np.all(np.abs(C2 - expect) <= 1e-13 * sc)
