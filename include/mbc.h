@@ -69,7 +69,7 @@ const char *mbc_status_string(mbc_status s);
  * Term lists (host, once per nucleus)
  * ---------------------------------------------------------------------- */
 
-enum { MBC_SPIN_ALL = 0, MBC_SPIN_LISTED = 1 };
+enum { MBC_SPIN_ALL = 0, MBC_SPIN_LISTED = 1, MBC_SPIN_PROJECTED = 2 };
 enum { MBC_PROTON = 0, MBC_NEUTRON = 1 };
 
 /*
@@ -77,14 +77,31 @@ enum { MBC_PROTON = 0, MBC_NEUTRON = 1 };
  *   n_p, n_n     number of protons and neutrons, A = n_p + n_n, 1 <= A <= 16.
  *   dirac_dim    4 = relativistic (Gamma_1 = 1, Gamma_2 = C gamma_5),
  *                2 = nonrelativistic (Gamma_1 = P_nr, Gamma_2 = C gamma_5 P_nr).
- *   n_sources    number of quark sources; only 1 is built.
+ *   n_sources    number of mutually orthogonal quark sources N_s (Sec. 6):
+ *                source baryon indices become spin x source, chi = N_s alpha + s,
+ *                quark indices spinor-colour x source, xi = N_s kappa + s, and
+ *                G carries the source deltas (eq. G_tilde); 3 dirac_dim N_s
+ *                must not exceed 24. Contraction kernels are built for N_s = 1.
+ *   n_sinks      number of sink functions N_k for the sink baryon indices
+ *                psi = N_k alpha + k (Sec. 6); 0 or 1 = one sink. Term lists
+ *                with N_k > 1 are built (operation counts, Tables 3 and 6);
+ *                contraction kernels are built for N_k = 1.
  *   spin_mode    MBC_SPIN_ALL: every independent component, i.e. every pair
  *                (sink spin set, source spin set) (Sec. 4); the output
  *                component index is snk_index * n_sets + src_index with the
  *                sets ordered as by mbc_term_list_components.
  *                MBC_SPIN_LISTED: the n_spin_sel pairs given by snk_spins and
- *                src_spins (each n_spin_sel * A int8 values, protons first,
- *                each species ascending) (Sec. 5, Sec. 8 delta projection).
+ *                src_spins (each n_spin_sel * A int8 values, protons first;
+ *                within a species any order, the antisymmetry sign is
+ *                applied) (Sec. 5, Sec. 8 delta projection).
+ *                MBC_SPIN_PROJECTED: n_proj outputs, each a projection
+ *                C_M = sum_t w_t C(snk_t; src_t) of Sec. 5: the n_spin_sel
+ *                terms give snk_spins / src_spins (A entries each, protons
+ *                first, any order within a species: the antisymmetry sign is
+ *                applied, repeated spins make the term vanish), term_proj[t]
+ *                (the output it belongs to) and term_coef[t] (a real weight).
+ *                The builder folds each projection into one modified list
+ *                L_M, so only the components it needs are computed.
  *   path         NULL, or path_len == A entries MBC_PROTON / MBC_NEUTRON: the
  *                order in which baryons are added (Sec. 7). NULL selects the
  *                paper's rule: the more numerous species first, neutrons
@@ -101,6 +118,10 @@ typedef struct {
     const int8_t *src_spins;
     int32_t path_len;
     const int8_t *path;
+    int32_t n_proj;
+    const int32_t *term_proj;
+    const double *term_coef;
+    int32_t n_sinks;
 } mbc_op_spec;
 
 typedef struct mbc_term_list mbc_term_list; /* opaque, library-owned */
@@ -139,7 +160,8 @@ mbc_status mbc_build_term_list(const mbc_op_spec *spec, mbc_term_list **out);
 mbc_status mbc_term_list_stats(const mbc_term_list *list, mbc_list_stats *st);
 
 /* Spin labels of the output components: snk and src each receive
- * n_comp * A int8 values (caller-owned), protons first. */
+ * n_comp * A int8 values (caller-owned), protons first; -1 for the outputs
+ * of MBC_SPIN_PROJECTED lists. */
 mbc_status mbc_term_list_components(const mbc_term_list *list, int8_t *snk, int8_t *src);
 
 /* Number of nonzero L entries of output component c (N_L, Tables 4-6). */

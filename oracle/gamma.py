@@ -101,3 +101,22 @@ def g_nonzeros(dirac_dim: int):
 
 # Flavour of each quark slot of a baryon (Sec. 7): 0 = u, 1 = d.
 SLOT_FLAVOURS = {"P": (0, 0, 1), "N": (1, 0, 1)}
+
+
+def g_tensor_sources(dirac_dim: int, n_sources: int) -> np.ndarray:
+    """G~(chi; xi1, xi2, xi3) of Sec. 6 eq. G_tilde for n_sources mutually
+    orthogonal quark sources: chi = n_sources * alpha + s and xi =
+    n_sources * kappa + s (the combined spin-source index 2 alpha + s of
+    Table 6 for two sources); G~ is G(alpha; kappa1, kappa2, kappa3) when all
+    three quarks come from source s, else zero.
+    Shape (dirac_dim * n_sources, 3 * dirac_dim * n_sources, ...)."""
+    G = g_tensor(dirac_dim)
+    nk = 3 * dirac_dim
+    nc, nx = dirac_dim * n_sources, nk * n_sources
+    out = np.zeros((nc, nx, nx, nx))
+    for a in range(dirac_dim):
+        for s in range(n_sources):
+            chi = n_sources * a + s
+            for k1, k2, k3 in zip(*np.nonzero(G[a, :nk, :nk, :nk])):
+                out[chi, n_sources * k1 + s, n_sources * k2 + s, n_sources * k3 + s] = G[a, k1, k2, k3]
+    return out

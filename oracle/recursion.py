@@ -70,7 +70,7 @@ class Plan:
     """Symbolic part of O3 for one nucleus and a list of (sink, source) spin
     assignments (protons first, each species sorted ascending)."""
 
-    def __init__(self, n_p: int, n_n: int, dirac_dim: int, requests=None, path=None):
+    def __init__(self, n_p: int, n_n: int, dirac_dim: int, requests=None, path=None, G=None):
         lib = _load()
         self.n_p, self.n_n, self.dim = n_p, n_n, dirac_dim
         self.A = n_p + n_n
@@ -79,7 +79,12 @@ class Plan:
             requests = [(d, a) for d in comps for a in comps]
         self.requests = [(tuple(d), tuple(a)) for d, a in requests]
         self.path = list(paper_path(n_p, n_n) if path is None else path)
-        G = np.ascontiguousarray(np.rint(g_tensor(dirac_dim)).astype(np.int8))
+        # G: optional replacement tensor (e.g. the two-source G~ of Sec. 6),
+        # at most (4, 12, 12, 12), zero-padded to that shape
+        Gd = g_tensor(dirac_dim) if G is None else np.asarray(G)
+        Gp = np.zeros((4, 12, 12, 12))
+        Gp[: Gd.shape[0], : Gd.shape[1], : Gd.shape[2], : Gd.shape[3]] = Gd
+        G = np.ascontiguousarray(np.rint(Gp).astype(np.int8))
         snk = np.ascontiguousarray(np.array([d for d, _ in self.requests], dtype=np.int8).reshape(-1))
         src = np.ascontiguousarray(np.array([a for _, a in self.requests], dtype=np.int8).reshape(-1))
         pa = np.ascontiguousarray(np.array(self.path, dtype=np.int8))

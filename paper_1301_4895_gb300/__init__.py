@@ -27,7 +27,7 @@ FP64, MIXED = 0, 1
 C128, C64 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 PROTON, NEUTRON = 0, 1
-SPIN_ALL, SPIN_LISTED = 0, 1
+SPIN_ALL, SPIN_LISTED, SPIN_PROJECTED = 0, 1, 2
 MAX_A = 16
 MAX_MOM = 32
 
@@ -45,7 +45,8 @@ class OpSpec(ctypes.Structure):
     _fields_ = [("n_p", ctypes.c_int32), ("n_n", ctypes.c_int32), ("dirac_dim", ctypes.c_int32),
                 ("n_sources", ctypes.c_int32), ("spin_mode", ctypes.c_int32), ("n_spin_sel", ctypes.c_int32),
                 ("snk_spins", ctypes.c_void_p), ("src_spins", ctypes.c_void_p), ("path_len", ctypes.c_int32),
-                ("path", ctypes.c_void_p)]
+                ("path", ctypes.c_void_p), ("n_proj", ctypes.c_int32), ("term_proj", ctypes.c_void_p),
+                ("term_coef", ctypes.c_void_p), ("n_sinks", ctypes.c_int32)]
 
 
 class ListStats(ctypes.Structure):
@@ -186,15 +187,34 @@ class TermList:
             pass
 
 
-def build_term_list(n_p: int, n_n: int, dirac_dim: int = 4, spins=None, path=None, n_sources: int = 1) -> TermList:
+def build_term_list(n_p: int, n_n: int, dirac_dim: int = 4, spins=None, path=None, n_sources: int = 1,
+                    projections=None, n_sinks: int = 1) -> TermList:
     """``mbc_build_term_list``. spins: None for every independent component,
-    or a list of (sink spins, source spins) pairs, protons first."""
+    or a list of (sink spins, source spins) pairs, protons first.
+    projections: instead of spins, a list of projections, each a list of
+    (sink spins, source spins, real weight) terms (Sec. 5); one output each."""
     lib = load()
     A = n_p + n_n
     spec = OpSpec()
     spec.n_p, spec.n_n, spec.dirac_dim, spec.n_sources = n_p, n_n, dirac_dim, n_sources
+    spec.n_sinks = n_sinks
     keep = []
-    if spins is None:
+    if projections is not None:
+        if spins is not None:
+            raise ValueError("give spins or projections, not both")
+        terms = [(p, s, a, w) for p, proj in enumerate(projections) for (s, a, w) in proj]
+        snk = np.ascontiguousarray(np.array([t[1] for t in terms], dtype=np.int8).reshape(-1))
+        src = np.ascontiguousarray(np.array([t[2] for t in terms], dtype=np.int8).reshape(-1))
+        tp = np.ascontiguousarray(np.array([t[0] for t in terms], dtype=np.int32))
+        tw = np.ascontiguousarray(np.array([t[3] for t in terms], dtype=np.float64))
+        if snk.size != len(terms) * A or src.size != len(terms) * A:
+            raise ValueError("each spin assignment needs A entries")
+        spec.spin_mode = SPIN_PROJECTED
+        spec.n_spin_sel, spec.n_proj = len(terms), len(projections)
+        spec.snk_spins, spec.src_spins = snk.ctypes.data, src.ctypes.data
+        spec.term_proj, spec.term_coef = tp.ctypes.data, tw.ctypes.data
+        keep += [snk, src, tp, tw]
+    elif spins is None:
         spec.spin_mode = SPIN_ALL
     else:
         spec.spin_mode = SPIN_LISTED
@@ -212,7 +232,8 @@ def build_term_list(n_p: int, n_n: int, dirac_dim: int = 4, spins=None, path=Non
     h = ctypes.c_void_p()
     rc = lib.mbc_build_term_list(ctypes.byref(spec), ctypes.byref(h))
     _check(rc, "mbc_build_term_list", ok=(0, 2))
-    return TermList(h, rc, {"n_p": n_p, "n_n": n_n, "dirac_dim": dirac_dim, "spins": spins, "path": path})
+    return TermList(h, rc, {"n_p": n_p, "n_n": n_n, "dirac_dim": dirac_dim, "spins": spins, "path": path,
+                            "projections": projections, "n_sources": n_sources, "n_sinks": n_sinks})
 
 
 def _stream_ptr(stream):

@@ -234,21 +234,30 @@ struct SparseEntry {
     Key k;
     i64 v;
 };
-std::vector<SparseEntry> g_minus(int dim, int b) {
+// With ns quark sources (Sec. 6 eq. G_tilde) the source baryon index is
+// chi = ns * alpha + s and a quark index xi = ns * kappa + s: G~ is G on
+// (alpha; kappa1, kappa2, kappa3) when all three quarks come from source s.
+std::vector<SparseEntry> g_minus(int dim, int b, int ns = 1) {
     std::vector<SparseEntry> out;
-    for (int a = 0; a < dim; ++a) {
+    for (int chi = 0; chi < dim * ns; ++chi) {
+        const int a = chi / ns, src = chi % ns;
         auto ge = g_entries(dim, a);
+        for (auto &e : ge) {
+            e.x1 = e.x1 * ns + src;
+            e.x2 = e.x2 * ns + src;
+            e.x3 = e.x3 * ns + src;
+        }
         std::vector<SparseEntry> acc;
         for (auto &e : ge) {
             Key k;
             int sign = 1;
             if (b == MBC_PROTON) {  // u at slots 1, 2; d at slot 3
                 if (e.x1 == e.x2) continue;
-                k = {1u << a, 0, (1u << e.x1) | (1u << e.x2), 1u << e.x3};
+                k = {1u << chi, 0, (1u << e.x1) | (1u << e.x2), 1u << e.x3};
                 if (e.x1 > e.x2) sign = -1;
             } else {  // d at slots 1, 3; u at slot 2
                 if (e.x1 == e.x3) continue;
-                k = {0, 1u << a, 1u << e.x2, (1u << e.x1) | (1u << e.x3)};
+                k = {0, 1u << chi, 1u << e.x2, (1u << e.x1) | (1u << e.x3)};
                 if (e.x1 > e.x3) sign = -1;
             }
             bool found = false;
@@ -280,12 +289,12 @@ StageCounts counts_after(const int8_t *path, int m) {  // stage m (1-based)
 }
 
 // Sec. 7 bounds: P(n_P, n_N) and Q_P / Q_N for adding baryon b.
-i64 p_bound(int dim, int np, int nn) {
-    int n3 = 3 * dim;
+// dim: spin (or spin-sink) values of a baryon index, n3: quark index values
+// (Sec. 7 with D; Sec. 6 with 4 N_s and 12 N_s)
+i64 p_bound(int dim, int np, int nn, int n3) {
     return binom(dim, np) * binom(dim, nn) * binom(n3, 2 * np + nn) * binom(n3, np + 2 * nn);
 }
-i64 q_bound(int dim, int np, int nn, int b) {
-    int n3 = 3 * dim;
+i64 q_bound(int dim, int np, int nn, int b, int n3) {
     int nu = 2 * np + nn, nd = np + 2 * nn;
     if (b == MBC_PROTON)
         return multinom3(np, 1, dim - 1 - np) * multinom3(nn, 0, dim - nn) * multinom3(nu, 2, n3 - 2 - nu) *
@@ -301,9 +310,13 @@ double factorial(int n) {
 }
 
 mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
-    const int np = spec->n_p, nn = spec->n_n, A = np + nn, dim = spec->dirac_dim;
-    const int nxi = 3 * dim;
-    L->A = A; L->n_p = np; L->n_n = nn; L->dim = dim; L->n_sources = 1; L->nxi = nxi;
+    const int np = spec->n_p, nn = spec->n_n, A = np + nn, D = spec->dirac_dim;
+    const int ns = std::max(1, spec->n_sources), nk = std::max(1, spec->n_sinks);
+    const int dim = D * nk;        // sink baryon index: spin x sink function (Sec. 6 psi)
+    const int dim_src = D * ns;    // source baryon index: spin x source (Sec. 6 chi)
+    const int nxi = 3 * D * ns;    // quark index: spinor-colour x source
+    L->A = A; L->n_p = np; L->n_n = nn; L->dim = D; L->n_sources = ns; L->n_sinks = nk; L->nxi = nxi;
+    L->dim_snk = dim; L->dim_src = dim_src;
     L->block_size = (i64)dim * binom(nxi, 2) * nxi;
     L->norm = factorial(np) * factorial(nn);
     L->norm *= L->norm;
@@ -317,47 +330,80 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
     for (int i = 0; i < A; ++i) L->need_block[L->path[i]] = true;
 
     // requested components
-    auto sets = [&](int k) {
+    auto sets = [&](int k, int n) {
         std::vector<std::vector<int8_t>> out;
-        for (i64 r = 0; r < binom(dim, k); ++r) {
-            u32 m = colex_unrank(r, k, dim);
+        for (i64 r = 0; r < binom(n, k); ++r) {
+            u32 m = colex_unrank(r, k, n);
             std::vector<int8_t> v;
-            for (int s = 0; s < dim; ++s)
+            for (int s = 0; s < n; ++s)
                 if (m & (1u << s)) v.push_back((int8_t)s);
             out.push_back(v);
         }
         return out;
     };
-    bool forbidden = np > dim || nn > dim || 2 * np + nn > nxi || np + 2 * nn > nxi;
-    std::vector<std::vector<int8_t>> comps;
+    bool forbidden = np > std::min(dim, dim_src) || nn > std::min(dim, dim_src) || 2 * np + nn > nxi ||
+                     np + 2 * nn > nxi;
     if (spec->spin_mode == MBC_SPIN_ALL) {
-        if (!forbidden)
-            for (auto &p : sets(np))
-                for (auto &n : sets(nn)) {
+        std::vector<std::vector<int8_t>> snk_comps, src_comps;
+        if (!forbidden) {
+            for (auto &p : sets(np, dim))
+                for (auto &n : sets(nn, dim)) {
                     std::vector<int8_t> v = p;
                     v.insert(v.end(), n.begin(), n.end());
-                    comps.push_back(v);
+                    snk_comps.push_back(v);
                 }
-        for (auto &a : comps)
-            for (auto &b : comps) {
+            for (auto &p : sets(np, dim_src))
+                for (auto &n : sets(nn, dim_src)) {
+                    std::vector<int8_t> v = p;
+                    v.insert(v.end(), n.begin(), n.end());
+                    src_comps.push_back(v);
+                }
+        }
+        for (auto &a : snk_comps)
+            for (auto &b : src_comps) {
                 L->comp_snk.insert(L->comp_snk.end(), a.begin(), a.end());
                 L->comp_src.insert(L->comp_src.end(), b.begin(), b.end());
             }
-        L->n_comp = (int32_t)(comps.size() * comps.size());
-    } else {
+        L->n_comp = (int32_t)(snk_comps.size() * src_comps.size());
+    } else if (spec->spin_mode == MBC_SPIN_LISTED) {
         L->n_comp = spec->n_spin_sel;
         L->comp_snk.assign(spec->snk_spins, spec->snk_spins + (size_t)A * spec->n_spin_sel);
         L->comp_src.assign(spec->src_spins, spec->src_spins + (size_t)A * spec->n_spin_sel);
+    } else {  // MBC_SPIN_PROJECTED: one output per projection; labels are not single spin tuples
+        L->n_comp = spec->n_proj;
+        L->comp_snk.assign((size_t)A * spec->n_proj, (int8_t)-1);
+        L->comp_src.assign((size_t)A * spec->n_proj, (int8_t)-1);
     }
     L->fin_off.assign((size_t)L->n_comp + 1, 0);
-    auto spin_mask = [&](const int8_t *s, int off, int n) {
-        u32 m = 0;
+    // a spin tuple of one species -> (set bitmask, sign of the sorting
+    // permutation); repeated or out-of-range spins give the Pauli zero (Sec. 3)
+    auto spin_set = [&](const int8_t *s, int off, int n, int range, u32 &mask, int &sign) {
+        mask = 0;
+        int inv = 0;
         for (int i = 0; i < n; ++i) {
-            if (s[off + i] < 0 || s[off + i] >= dim || (m & (1u << s[off + i]))) return (u32)0xFFFFFFFFu;
-            m |= 1u << s[off + i];
+            const int v = s[off + i];
+            if (v < 0 || v >= range || (mask & (1u << v))) return false;
+            for (int j = 0; j < i; ++j) inv += s[off + j] > v;
+            mask |= 1u << v;
         }
-        return m;
+        sign = (inv & 1) ? -1 : 1;
+        return true;
     };
+    // terms: (projection, sink spins, source spins, weight)
+    struct Term {
+        int proj;
+        const int8_t *snk, *src;
+        double w;
+    };
+    std::vector<Term> terms;
+    if (spec->spin_mode == MBC_SPIN_PROJECTED) {
+        for (int t = 0; t < spec->n_spin_sel; ++t)
+            terms.push_back({spec->term_proj[t], spec->snk_spins + (size_t)A * t, spec->src_spins + (size_t)A * t,
+                             spec->term_coef[t]});
+    } else {
+        for (int c = 0; c < L->n_comp; ++c)
+            terms.push_back({c, L->comp_snk.data() + (size_t)A * c, L->comp_src.data() + (size_t)A * c, 1.0});
+    }
 
     mbc_list_stats &st = L->stats;
     std::memset(&st, 0, sizeof(st));
@@ -368,8 +414,8 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
     st.norm = L->norm;
     for (int m = 1; m <= A; ++m) {
         auto c = counts_after(L->path, m);
-        st.stage_bound[m - 1] = p_bound(dim, c.kp, c.kn);
-        if (m < A) st.q_bound[m - 1] = q_bound(dim, c.kp, c.kn, L->path[m]);
+        st.stage_bound[m - 1] = p_bound(dim, c.kp, c.kn, nxi);
+        if (m < A) st.q_bound[m - 1] = q_bound(dim, c.kp, c.kn, L->path[m], nxi);
     }
     if (forbidden) {
         L->pauli_forbidden = true;
@@ -377,13 +423,13 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
     }
 
     // ---- L^(A) by the bullet recursion (eq. recr_L) -------------------------
-    std::vector<SparseEntry> gm[2] = {g_minus(dim, MBC_PROTON), g_minus(dim, MBC_NEUTRON)};
+    std::vector<SparseEntry> gm[2] = {g_minus(D, MBC_PROTON, ns), g_minus(D, MBC_NEUTRON, ns)};
     std::vector<SparseEntry> cur = gm[L->path[0]];
     for (int m = 1; m < A; ++m) {
         int b = L->path[m];
         auto c = counts_after(L->path, m + 1);
         Space sp;
-        sp.init(dim, nxi, c.kp, c.kn, c.ku, c.kd);
+        sp.init(dim_src, nxi, c.kp, c.kn, c.ku, c.kd);  // L lives on source-side baryon indices
         std::vector<std::atomic<i64>> dense((size_t)sp.size());
         for (auto &d : dense) d.store(0, std::memory_order_relaxed);
         const auto &g = gm[b];
@@ -411,21 +457,36 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
     std::vector<uint8_t> need_hi((size_t)spA.size(), 0);  // needed at stage A
     struct FinEntry {
         i64 zfull;
-        i64 l;
+        double l;
     };
+    // modified list of each output (Sec. 5): L_M(sink set; U, D) = sum over the
+    // output's terms of weight * sign(sink order) * sign(source order) * L(source set; U, D)
     std::vector<std::vector<FinEntry>> fin((size_t)L->n_comp);
-    for (int c = 0; c < L->n_comp; ++c) {
-        u32 sp_ = spin_mask(L->comp_snk.data(), c * A, np), sn_ = spin_mask(L->comp_snk.data(), c * A + np, nn);
-        u32 ap_ = spin_mask(L->comp_src.data(), c * A, np), an_ = spin_mask(L->comp_src.data(), c * A + np, nn);
-        if (sp_ == 0xFFFFFFFFu || sn_ == 0xFFFFFFFFu || ap_ == 0xFFFFFFFFu || an_ == 0xFFFFFFFFu)
-            continue;  // a repeated or out-of-range spin: Pauli zero component
+    for (const Term &tm : terms) {
+        u32 sp_, sn_, ap_, an_;
+        int g1, g2, g3, g4;
+        if (!spin_set(tm.snk, 0, np, dim, sp_, g1) || !spin_set(tm.snk, np, nn, dim, sn_, g2) ||
+            !spin_set(tm.src, 0, np, dim_src, ap_, g3) || !spin_set(tm.src, np, nn, dim_src, an_, g4))
+            continue;  // a repeated or out-of-range spin: Pauli zero term
+        const double w = tm.w * g1 * g2 * g3 * g4;
         for (auto &e : cur) {
             if (e.k.dp != ap_ || e.k.dn != an_) continue;
             Key z{sp_, sn_, e.k.u, e.k.d};
-            i64 zi = spA.index(z);
-            need_hi[(size_t)zi] = 1;
-            fin[(size_t)c].push_back({zi, e.v});
+            fin[(size_t)tm.proj].push_back({spA.index(z), w * (double)e.v});
         }
+    }
+    for (auto &v : fin) {  // add equal keys, drop exact cancellations
+        std::sort(v.begin(), v.end(), [](const FinEntry &a, const FinEntry &b) { return a.zfull < b.zfull; });
+        size_t w = 0;
+        for (size_t i = 0; i < v.size();) {
+            size_t j = i;
+            double sum = 0.0;
+            while (j < v.size() && v[j].zfull == v[i].zfull) sum += v[j++].l;
+            if (sum != 0.0) v[w++] = {v[i].zfull, sum};
+            i = j;
+        }
+        v.resize(w);
+        for (auto &e : v) need_hi[(size_t)e.zfull] = 1;
     }
 
     // ---- backward pruning (Sec. 3): stage m needs every x of every split ----
@@ -517,7 +578,6 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
     const auto &cmA = compact[(size_t)A];
     for (int c = 0; c < L->n_comp; ++c) {
         auto &v = fin[(size_t)c];
-        std::sort(v.begin(), v.end(), [](const FinEntry &a, const FinEntry &b) { return a.zfull < b.zfull; });
         for (auto &e : v) {
             i64 zi = A == 1 ? block_index(spA.key(e.zfull), L->path[0], nxi) : (i64)cmA[(size_t)e.zfull];
             L->fin_z.push_back((uint32_t)zi);
@@ -553,8 +613,18 @@ mbc_status mbc_build_term_list(const mbc_op_spec *spec, mbc_term_list **out) {
     const int A = spec->n_p + spec->n_n;
     if (spec->n_p < 0 || spec->n_n < 0 || A < 1 || A > MBC_MAX_A) return MBC_ERR_INVALID_ARG;
     if (spec->dirac_dim != 2 && spec->dirac_dim != 4) return MBC_ERR_INVALID_ARG;
-    if (spec->n_sources != 1) return MBC_ERR_UNSUPPORTED;
-    if (spec->spin_mode != MBC_SPIN_ALL && spec->spin_mode != MBC_SPIN_LISTED) return MBC_ERR_INVALID_ARG;
+    // quark indices (3 dirac_dim n_sources values) must fit the 24-value index tables
+    if (spec->n_sources < 1 || 3 * spec->dirac_dim * spec->n_sources > 24) return MBC_ERR_UNSUPPORTED;
+    if (spec->n_sinks < 0 || spec->dirac_dim * std::max(1, spec->n_sinks) > 16) return MBC_ERR_UNSUPPORTED;
+    if (spec->spin_mode != MBC_SPIN_ALL && spec->spin_mode != MBC_SPIN_LISTED && spec->spin_mode != MBC_SPIN_PROJECTED)
+        return MBC_ERR_INVALID_ARG;
+    if (spec->spin_mode == MBC_SPIN_PROJECTED) {
+        if (spec->n_proj < 1 || spec->n_spin_sel < 1 || !spec->snk_spins || !spec->src_spins || !spec->term_proj ||
+            !spec->term_coef)
+            return MBC_ERR_INVALID_ARG;
+        for (int t = 0; t < spec->n_spin_sel; ++t)
+            if (spec->term_proj[t] < 0 || spec->term_proj[t] >= spec->n_proj) return MBC_ERR_INVALID_ARG;
+    }
     if (spec->spin_mode == MBC_SPIN_LISTED &&
         (spec->n_spin_sel < 1 || !spec->snk_spins || !spec->src_spins))
         return MBC_ERR_INVALID_ARG;

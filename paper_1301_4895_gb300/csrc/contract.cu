@@ -660,8 +660,10 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     if (opts->n_mom < 1 || opts->n_mom > kMaxMom || !opts->mom) return MBC_ERR_INVALID_ARG;
     const int t0 = opts->t0, t1 = opts->t1 == 0 ? props->nt : opts->t1;
     if (t0 < 0 || t1 > props->nt || t1 <= t0) return MBC_ERR_INVALID_ARG;
-    for (int i = 0; i < n_lists; ++i)
+    for (int i = 0; i < n_lists; ++i) {
         if (!lists[i]) return MBC_ERR_INVALID_ARG;
+        if (lists[i]->n_sources != 1 || lists[i]->n_sinks != 1) return MBC_ERR_UNSUPPORTED;
+    }
     const int64_t v3 = (int64_t)props->lx * props->ly * props->lz;
     if (v3 > (1LL << 30)) return MBC_ERR_INVALID_ARG;
     const int64_t site_elems = 144;
@@ -1032,6 +1034,7 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     // ---- host-only checks: nothing below touches the device before they pass
     if (!props || !list || !opts || !out || !props->s_u || !props->s_d) return MBC_ERR_INVALID_ARG;
     if (props->s_u != props->s_d) return MBC_ERR_UNSUPPORTED;
+    if (list->n_sources != 1 || list->n_sinks != 1) return MBC_ERR_UNSUPPORTED;
     if (props->memory != MBC_MEM_DEVICE || opts->precision != MBC_FP64) return MBC_ERR_UNSUPPORTED;
     if (opts->sink_mode != MBC_SINK_POINT) return MBC_ERR_UNSUPPORTED;
     if (props->dtype != MBC_C128 && props->dtype != MBC_C64) return MBC_ERR_INVALID_ARG;

@@ -135,30 +135,45 @@ __global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__
         const int col = group * 32 + lane;
         const int64_t z_begin = chunk * zchunk;
         const int64_t z_end = min(n_z, z_begin + zchunk);
-        const int64_t o_begin = z_begin * k, o_end = z_end * k;
-        typename Tr::Acc acc;
-        acc.zero();
-        int64_t z = z_begin;
-        int64_t next_flush = o_begin + k;
-        for (int64_t ob = o_begin; ob < o_end; ob += 32) {
-            uint32_t mx = 0;
-            uint32_t my = 0;
-            if (ob + lane < o_end) {
-                mx = __ldg(opx + ob + lane);
-                my = __ldg(opy + ob + lane);
-            }
-            const int nb = (int)min((int64_t)32, o_end - ob);
-            for (int t = 0; t < nb; ++t) {
-                uint32_t x = __shfl_sync(0xffffffffu, mx, t);
-                uint32_t y = __shfl_sync(0xffffffffu, my, t);
-                acc.fma(X[(int64_t)x * W + col], Y[(int64_t)(y & 0x7fffu) * W + col], (y & 0x8000u) << 16);
-                if (ob + t + 1 == next_flush) {
-                    Z[z * W + col] = acc.store();
-                    acc.zero();
-                    ++z;
-                    next_flush += k;
+        const typename Tr::V *Xc = X + col;
+        const typename Tr::V *Yc = Y + col;
+        // output by output: its k terms are contiguous; 32 operand words are
+        // loaded at once and broadcast, the loop body has no branch so the
+        // gathers of several terms are in flight together
+        for (int64_t z = z_begin; z < z_end; ++z) {
+            typename Tr::Acc acc;
+            acc.zero();
+            const uint32_t *ox = opx + z * k;
+            const uint16_t *oy = opy + z * k;
+            for (int64_t b0 = 0; b0 < k; b0 += 32) {
+                const int nb = (int)min((int64_t)32, k - b0);
+                uint32_t mx = 0, my = 0;
+                if (lane < nb) {
+                    mx = __ldg(ox + b0 + lane);
+                    my = __ldg(oy + b0 + lane);
+                }
+                // G terms' gathers are issued before their multiply-adds so that
+                // several L2 round trips overlap (FP32: 4 terms, FP64: 2)
+                constexpr int G = sizeof(typename Tr::V) == 8 ? 4 : 2;
+                for (int t0 = 0; t0 < nb; t0 += G) {
+                    typename Tr::V xv[G], yv[G];
+                    uint32_t sg[G];
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const uint32_t x = __shfl_sync(0xffffffffu, mx, (t0 + g) & 31);
+                        const uint32_t y = __shfl_sync(0xffffffffu, my, (t0 + g) & 31);
+                        if (t0 + g < nb) {
+                            xv[g] = __ldg(Xc + (int64_t)x * W);
+                            yv[g] = __ldg(Yc + (int64_t)(y & 0x7fffu) * W);
+                        }
+                        sg[g] = (y & 0x8000u) << 16;
+                    }
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+                        if (t0 + g < nb) acc.fma(xv[g], yv[g], sg[g]);
                 }
             }
+            Z[z * W + col] = acc.store();
         }
     }
 }

@@ -30,21 +30,23 @@ struct DeviceCache;  // defined by the CUDA side
 }  // namespace mbc
 
 struct mbc_term_list {
-    int A = 0, n_p = 0, n_n = 0, dim = 4, n_sources = 1;
+    int A = 0, n_p = 0, n_n = 0, dim = 4, n_sources = 1, n_sinks = 1;
+    int dim_snk = 4, dim_src = 4;  // baryon index values at the sink / source (Sec. 6 psi / chi)
     int8_t path[MBC_MAX_A] = {0};
     bool pauli_forbidden = false;
-    int nxi = 12;             // source spinor-colour values used (3 * dim)
-    int64_t block_size = 0;   // dim * C(nxi, 2) * nxi
+    int nxi = 12;             // quark index values: 3 * dim * n_sources
+    int64_t block_size = 0;   // dim_snk * C(nxi, 2) * nxi
     bool need_block[2] = {false, false};
     std::vector<mbc::Step> steps;        // A - 1 steps
     int64_t final_size = 0;              // components of F^(A) kept
     int32_t n_comp = 0;
     std::vector<int8_t> comp_snk, comp_src;     // n_comp * A
     // contraction with L (eq. C_final): entries of component c at
-    // [fin_off[c], fin_off[c+1]): F^(A) index and integer L value
+    // [fin_off[c], fin_off[c+1]): F^(A) index and L value (an integer for a
+    // single component, a weighted sum for a projection, Sec. 5)
     std::vector<int64_t> fin_off;
     std::vector<uint32_t> fin_z;
-    std::vector<int64_t> fin_l;
+    std::vector<double> fin_l;
     double norm = 1.0;
     mbc_list_stats stats{};
     // device copies, one per device ordinal, created on first use

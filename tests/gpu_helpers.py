@@ -23,6 +23,15 @@ def oracle_slab(plan, slab, dims_zyx, moms):
     return ref, site_sum.scale_sum(sc)
 
 
+# worst |dC| / sum|terms| seen by the parity tests, per (nucleus, precision)
+WORST = {}
+
+
+def record(label, precision, err):
+    key = (label, "fp64" if precision == 0 else "mixed")
+    WORST[key] = max(WORST.get(key, 0.0), float(err))
+
+
 def max_rel_err(got, ref, scale):
     """max |got - ref| / scale over momenta and components."""
     return float(np.max(np.abs(np.asarray(got) - ref) / scale[None, :]))

@@ -120,7 +120,7 @@ def test_pauli_forbidden_and_invalid_specs():
     with pytest.raises(mbc.MbcError):
         mbc.build_term_list(1, 1, 2, path=[0, 0])
     with pytest.raises(mbc.MbcError):
-        mbc.build_term_list(1, 1, 2, n_sources=2)
+        mbc.build_term_list(1, 1, 2, n_sources=5)  # 30 quark index values > 24
 
 
 def test_contract_rejects_bad_arguments_before_any_device_work():
@@ -130,3 +130,56 @@ def test_contract_rejects_bad_arguments_before_any_device_work():
         mbc.contract(np.zeros((1, 1, 1, 1, 1, 12, 11), dtype=np.complex128), [tl])
     lib = mbc.load()
     assert lib.mbc_contract(None, None, 0, None, None, None) == 1
+
+
+def test_spin_projection_lists():
+    """Sec. 5: a projection is folded into one modified list. A single
+    (delta = alpha) term reproduces the listed component's operation count
+    (Table 5); the deuteron J_z = 0 projection needs no more operations than
+    its four components listed separately."""
+    sp = (0, 1, 0, 1)
+    one = mbc.build_term_list(2, 2, 4, projections=[[(sp, sp, 1.0)]]).stats()
+    assert one["n_ops_total"] == 8541864 and one["n_comp"] == 1
+    # unsorted spins of one species: same list up to a sign, same cost
+    swapped = mbc.build_term_list(2, 2, 4, projections=[[((1, 0, 0, 1), sp, 1.0)]])
+    assert swapped.stats()["n_ops_total"] == 8541864
+    pairs = [((0, 1), (0, 1)), ((0, 1), (1, 0)), ((1, 0), (0, 1)), ((1, 0), (1, 0))]
+    jz0 = mbc.build_term_list(1, 1, 2, projections=[[(a, b, 0.5) for a, b in pairs]])
+    listed = mbc.build_term_list(1, 1, 2, spins=pairs)
+    assert jz0.stats()["n_ops_total"] <= listed.stats()["n_ops_total"]
+    assert jz0.components() == [((-1, -1), (-1, -1))]
+    # a repeated spin within a species is a Pauli zero term
+    zero = mbc.build_term_list(0, 2, 4, projections=[[((1, 1), (0, 1), 1.0)]])
+    assert zero.n_l(0) == 0
+    with pytest.raises(mbc.MbcError):
+        mbc.build_term_list(1, 1, 2, projections=[[]])
+
+
+def test_two_source_single_components_match_table6():
+    """Sec. 6: two quark sources (and two sink functions) with
+    nonrelativistic operators; spinor-source indices 2 alpha + s (Table 6)."""
+    for row in read_golden("table6_nonrel_two_sources_spin.txt"):
+        n_p, n_n, ops = int(row[0]), int(row[1]), int(row[3])
+        if ops > 6e7:
+            continue
+        sp = spins_of(row[2])
+        tl = mbc.build_term_list(n_p, n_n, 2, spins=[(sp, sp)], n_sources=2, n_sinks=2)
+        assert tl.stats()["n_ops_total"] == ops, row
+        assert tl.n_l(0) == int(row[4]), row
+    # contraction kernels are built for one source: refused before device work
+    tl = mbc.build_term_list(1, 1, 2, spins=[((0, 2), (0, 2))], n_sources=2, n_sinks=2)
+    import numpy as np
+    with pytest.raises(mbc.MbcError):
+        mbc.contract(np.zeros((1, 1, 1, 1, 1, 12, 12), dtype=np.complex128), [tl])
+
+
+def test_two_source_lists_agree_with_oracle():
+    """Builder and oracle (O3 fed with its own G~ from the gamma matrices)
+    prune the two-source lists identically."""
+    from oracle import gamma
+    Gt = gamma.g_tensor_sources(2, 2)
+    for n_p, n_n, sp in ((1, 1, (0, 2)), (0, 3, (0, 1, 2)), (1, 2, (2, 0, 2)), (2, 2, (0, 2, 0, 2))):
+        st = mbc.build_term_list(n_p, n_n, 2, spins=[(sp, sp)], n_sources=2, n_sinks=2).stats()
+        plan = recursion.Plan(n_p, n_n, 2, requests=[(sp, sp)], G=Gt)
+        tot, per, stages = plan.ops()
+        assert (st["n_ops_total"], st["n_ops"], st["stage_size"]) == (tot, per, stages)

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_helpers import max_rel_err, oracle_plan, oracle_slab
+from gpu_helpers import WORST, max_rel_err, oracle_plan, oracle_slab, record
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +58,7 @@ def check_slabs(mbc, field, lists, specs, dims, precisions=(0, 1), moms=((0, 0, 
                     got = outs[p][cfg, li, t - t0, :, : len(comps)]
                     e = max_rel_err(got, ref, scale)
                     worst[p] = max(worst[p], e)
+                    record(f"({n_p},{n_n}) D={D}", p, e)
                     assert e <= TOL[p], (n_p, n_n, D, cfg, t, p, e)
     return outs, worst
 
@@ -229,7 +230,9 @@ def _check_sparse(mbc, field, tl, spec, dims, sites, precisions=(0, 1)):
     scale = site_sum.scale_sum(sc)
     for p in precisions:
         got = run(mbc, field, [tl], p)[0, 0, 0, :, : len(tl.components())]
-        assert max_rel_err(got, ref, scale) <= TOL[p], p
+        e = max_rel_err(got, ref, scale)
+        record(f"({spec[0]},{spec[1]}) D={spec[2]} full lattice", p, e)
+        assert e <= TOL[p], p
 
 
 def test_he4_rel_all_components_full_lattice_sampled(mbc):
@@ -306,6 +309,7 @@ def test_momentum_projected_blocks(mbc, n_p, n_n, D, spins):
             C, sc = projection.projected_correlators(plan, field[cfg, t], dims, moms)
             for p in (0, 1):
                 got = outs[p][cfg, 0, t, :, : len(comps)]
+                record(f"({n_p},{n_n}) D={D} projected blocks", p, float(np.max(np.abs(got - C) / sc)))
                 assert np.all(np.abs(got - C) <= TOL[p] * sc), (p, cfg, t, float(np.max(np.abs(got - C) / sc)))
 
 
@@ -323,3 +327,53 @@ def test_momentum_projected_blocks_full_slab(mbc):
     for p in (0, 1):
         got = run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM)[0, 0, 0, :, :1]
         assert np.all(np.abs(got - C) <= TOL[p] * sc), p
+
+
+def _sorted_with_sign(spins, n_p):
+    sign = 1
+    out = []
+    for part in (spins[:n_p], spins[n_p:]):
+        inv = sum(1 for i in range(len(part)) for j in range(i) if part[j] > part[i])
+        sign *= -1 if inv % 2 else 1
+        out += sorted(part)
+    return tuple(out), sign
+
+
+@pytest.mark.parametrize("n_p,n_n,D,projections", [
+    (1, 1, 2, [[((0, 0), (0, 0), 1.0)],
+               [((0, 1), (0, 1), 0.5), ((0, 1), (1, 0), 0.5), ((1, 0), (0, 1), 0.5), ((1, 0), (1, 0), 0.5)]]),
+    (2, 2, 4, [[((1, 0, 0, 1), (0, 1, 0, 1), 1.0), ((0, 1, 2, 3), (0, 1, 0, 1), -0.25)]]),
+])
+def test_spin_projection_outputs(mbc, n_p, n_n, D, projections):
+    """Sec. 5 projections C_M = sum_t w_t C(snk_t; src_t) (spins in any order
+    within a species) against the oracle's components."""
+    dims = (2, 2, 2)
+    field = synth.field(23, 1, 2, dims, 0.4)
+    tl = mbc.build_term_list(n_p, n_n, D, projections=projections)
+    pairs = sorted({(_sorted_with_sign(s, n_p)[0], _sorted_with_sign(a, n_p)[0])
+                    for proj in projections for (s, a, _) in proj})
+    plan = oracle_plan(n_p, n_n, D, pairs)
+    idx = {pr: i for i, pr in enumerate(pairs)}
+    outs = {p: run(mbc, field, [tl], p) for p in (0, 1)}
+    for t in range(2):
+        ref, scale = oracle_slab(plan, field[0, t], dims, [(0, 0, 0)])
+        for k, proj in enumerate(projections):
+            exp, sc = 0j, 0.0
+            for s, a, w in proj:
+                (ss, g1), (aa, g2) = _sorted_with_sign(s, n_p), _sorted_with_sign(a, n_p)
+                exp += w * g1 * g2 * ref[0, idx[(ss, aa)]]
+                sc += abs(w) * scale[idx[(ss, aa)]]
+            for p in (0, 1):
+                e = abs(outs[p][0, 0, t, 0, k] - exp) / sc
+                record(f"({n_p},{n_n}) D={D} projection", p, e)
+                assert e <= TOL[p], (k, t, p, e)
+
+
+def test_zz_accuracy_report(mbc, capsys):
+    """Prints the worst |dC| / sum|terms| of the parity tests above (run with
+    -s to see it); fails if any exceeded its bound."""
+    with capsys.disabled():
+        print("\naccuracy: worst |dC| / sum|terms| against the oracle")
+        for (label, prec), e in sorted(WORST.items()):
+            print(f"  {label:40s} {prec:6s} {e:.3e}")
+    assert all(e <= TOL[0 if prec == "fp64" else 1] for (label, prec), e in WORST.items())

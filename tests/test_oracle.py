@@ -65,7 +65,7 @@ def test_max_components_sec3():
 
 def test_uca_columns_consistent_with_n_l():
     """N_list = n_u! n_d! N_L and N_contr = N_list / 2^A (Sec. 8)."""
-    for name in ("table4_nonrel_spin.txt", "table5_rel_spin.txt"):
+    for name in ("table4_nonrel_spin.txt", "table5_rel_spin.txt", "table6_nonrel_two_sources_spin.txt"):
         for row in read_golden(name):
             n_p, n_n = int(row[0]), int(row[1])
             n_l, n_list, n_contr = int(row[4]), int(row[5]), int(row[6])
