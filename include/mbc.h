@@ -81,7 +81,9 @@ enum { MBC_PROTON = 0, MBC_NEUTRON = 1 };
  *                source baryon indices become spin x source, chi = N_s alpha + s,
  *                quark indices spinor-colour x source, xi = N_s kappa + s, and
  *                G carries the source deltas (eq. G_tilde); 3 dirac_dim N_s
- *                must not exceed 24. Contraction kernels are built for N_s = 1.
+ *                must not exceed 24. Contraction kernels take
+ *                3 dirac_dim N_s <= 12 (one source relativistic, up to two
+ *                nonrelativistic); larger lists are built for their counts.
  *   n_sinks      number of sink functions N_k for the sink baryon indices
  *                psi = N_k alpha + k (Sec. 6); 0 or 1 = one sink. Term lists
  *                with N_k > 1 are built (operation counts, Tables 3 and 6);
@@ -181,7 +183,7 @@ enum { MBC_MEM_DEVICE = 0, MBC_MEM_HOST = 1 };   /* where s_u/s_d/out live */
 enum { MBC_SINK_POINT = 0, MBC_SINK_BLOCK_MOMENTUM = 1 };  /* sink function   */
 
 /*
- * Propagator fields, layout [cfg][t][z][y][x][row 12][col 12] complex,
+ * Propagator fields, layout [cfg][t][z][y][x][(source)][row 12][col 12] complex,
  * row = sink spinor-colour index, col = source index, re/im interleaved.
  *   s_u, s_d     u and d fields (may be the same pointer: u = d).
  *   dtype        MBC_C128 (complex double) or MBC_C64 (complex float).
@@ -191,6 +193,15 @@ enum { MBC_SINK_POINT = 0, MBC_SINK_BLOCK_MOMENTUM = 1 };  /* sink function   */
  *                the given stream and returns after the results are in out.
  *   stride_cfg, stride_t  element strides (in complex numbers) between
  *                configurations and time slices; 0 selects the dense values.
+ *   n_src        quark sources (Sec. 6); 0 means 1. A site then holds n_src
+ *                consecutive 12 x 12 matrices, [source][row][col], one per
+ *                source, and every list must have been built with
+ *                n_sources = n_src (else MBC_ERR_INVALID_ARG). The source
+ *                quark index of the lists is xi = n_src * kappa + s for
+ *                column kappa of source s. Contraction kernels take lists
+ *                with one sink function and 3 * dirac_dim * n_src <= 12
+ *                (MBC_ERR_UNSUPPORTED otherwise); the allocation-free entry
+ *                point takes n_src = 1 only.
  */
 typedef struct {
     const void *s_u;
@@ -199,6 +210,7 @@ typedef struct {
     int32_t memory;
     int32_t n_cfg, nt, lx, ly, lz;
     int64_t stride_cfg, stride_t;
+    int32_t n_src;
 } mbc_props;
 
 /* Launch tuning; zero fields select the library's choice. */

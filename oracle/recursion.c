@@ -60,7 +60,8 @@ typedef struct {
     int64_t n_need[16];
     key_t32 *need[16];
     int64_t ops[16];          /* ops of step m -> m+1 at index m-1 */
-    int8_t G[4 * 12 * 12 * 12];
+    int8_t G[4 * 12 * 12 * 12];   /* source tensor: L (eq. def_L) */
+    int8_t Gs[4 * 12 * 12 * 12];  /* sink tensor: the blocks (eq. def_f) */
     double norm;
 } o3_plan;
 
@@ -230,6 +231,7 @@ int o3_plan_build(int n_p, int n_n, int dim, const int8_t *path, const int8_t *G
     p->A = A; p->n_p = n_p; p->n_n = n_n; p->dim = dim; p->n_req = n_req;
     memcpy(p->path, path, (size_t)A);
     memcpy(p->G, G, sizeof(p->G));
+    memcpy(p->Gs, G, sizeof(p->Gs));
     p->norm = factorial(n_p) * factorial(n_n);
     p->norm *= p->norm;
 
@@ -327,6 +329,11 @@ int o3_plan_build(int n_p, int n_n, int dim, const int8_t *path, const int8_t *G
     return 0;
 }
 
+/* Replace the sink tensor used for the blocks (default: the source tensor).
+ * With several quark sources (Sec. 6) the sink keeps G(alpha; sink spinor-
+ * colour indices) while L is built from G~ over the source indices. */
+void o3_plan_set_sink(o3_plan *p, const int8_t *Gs) { memcpy(p->Gs, Gs, sizeof(p->Gs)); }
+
 int64_t o3_n_ops(const o3_plan *p, int64_t *per_step, int64_t *stage_sizes) {
     int64_t t = 0;
     for (int m = 0; m + 1 < p->A; ++m) { if (per_step) per_step[m] = p->ops[m]; t += p->ops[m]; }
@@ -398,7 +405,7 @@ static void blocks_batch(const o3_plan *p, int nb, const cplx *S, cplx *fm[2], d
             for (int p1 = 0; p1 < 12; ++p1)
                 for (int p2 = 0; p2 < 12; ++p2)
                     for (int p3 = 0; p3 < 12; ++p3) {
-                        int g = p->G[((a * 12 + p1) * 12 + p2) * 12 + p3];
+                        int g = p->Gs[((a * 12 + p1) * 12 + p2) * 12 + p3];
                         if (!g) continue;
                         for (int i = 0; i < 12; ++i)
                             for (int j = 0; j < 12; ++j)

@@ -54,6 +54,8 @@ def _load():
             lib.o3_blocks.restype = ctypes.c_int
             lib.o3_eval_blocks.argtypes = [P, ctypes.c_int64, P, P, P, P, P, P]
             lib.o3_eval_blocks.restype = ctypes.c_int
+            lib.o3_plan_set_sink.argtypes = [P, P]
+            lib.o3_plan_set_sink.restype = None
             _lib = lib
     return _lib
 
@@ -66,11 +68,35 @@ def paper_path(n_p: int, n_n: int) -> list:
     return [1] * n_n + [0] * n_p
 
 
+def _padded(G) -> np.ndarray:
+    Gd = np.asarray(G)
+    Gp = np.zeros((4, 12, 12, 12))
+    Gp[: Gd.shape[0], : Gd.shape[1], : Gd.shape[2], : Gd.shape[3]] = Gd
+    return np.ascontiguousarray(np.rint(Gp).astype(np.int8))
+
+
+def source_columns(S, dirac_dim: int) -> np.ndarray:
+    """Propagators of N_s sources, (..., N_s, 12, 12), as one matrix per site
+    with source quark index xi = N_s * kappa + s (Sec. 6): column xi is column
+    kappa of source s, for kappa < 3 * dirac_dim (the index values G~ uses).
+    Returns (..., 12, 12) complex128, columns beyond 3 dirac_dim N_s zero."""
+    S = np.asarray(S, dtype=np.complex128)
+    ns = S.shape[-3]
+    nk = 3 * dirac_dim
+    if nk * ns > 12:
+        raise ValueError("3 * dirac_dim * n_sources must not exceed 12")
+    out = np.zeros(S.shape[:-3] + (12, 12), dtype=np.complex128)
+    for s in range(ns):
+        for k in range(nk):
+            out[..., :, ns * k + s] = S[..., s, :, k]
+    return out
+
+
 class Plan:
     """Symbolic part of O3 for one nucleus and a list of (sink, source) spin
     assignments (protons first, each species sorted ascending)."""
 
-    def __init__(self, n_p: int, n_n: int, dirac_dim: int, requests=None, path=None, G=None):
+    def __init__(self, n_p: int, n_n: int, dirac_dim: int, requests=None, path=None, G=None, G_sink=None):
         lib = _load()
         self.n_p, self.n_n, self.dim = n_p, n_n, dirac_dim
         self.A = n_p + n_n
@@ -80,11 +106,9 @@ class Plan:
         self.requests = [(tuple(d), tuple(a)) for d, a in requests]
         self.path = list(paper_path(n_p, n_n) if path is None else path)
         # G: optional replacement tensor (e.g. the two-source G~ of Sec. 6),
-        # at most (4, 12, 12, 12), zero-padded to that shape
-        Gd = g_tensor(dirac_dim) if G is None else np.asarray(G)
-        Gp = np.zeros((4, 12, 12, 12))
-        Gp[: Gd.shape[0], : Gd.shape[1], : Gd.shape[2], : Gd.shape[3]] = Gd
-        G = np.ascontiguousarray(np.rint(Gp).astype(np.int8))
+        # at most (4, 12, 12, 12), zero-padded to that shape; G_sink: the
+        # tensor of the blocks when it differs (one sink, several sources)
+        G = _padded(g_tensor(dirac_dim) if G is None else G)
         snk = np.ascontiguousarray(np.array([d for d, _ in self.requests], dtype=np.int8).reshape(-1))
         src = np.ascontiguousarray(np.array([a for _, a in self.requests], dtype=np.int8).reshape(-1))
         pa = np.ascontiguousarray(np.array(self.path, dtype=np.int8))
@@ -96,6 +120,9 @@ class Plan:
             raise ValueError("invalid nucleus / request for O3")
         self._h = h
         self._lib = lib
+        if G_sink is not None:
+            self._gs = _padded(G_sink)
+            lib.o3_plan_set_sink(h, self._gs.ctypes.data)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -21,7 +21,7 @@ import itertools
 
 import numpy as np
 
-from .gamma import SLOT_FLAVOURS, g_nonzeros
+from .gamma import SLOT_FLAVOURS, g_nonzeros, g_tensor_sources
 
 
 def _perms_with_sign(n):
@@ -32,10 +32,13 @@ def _perms_with_sign(n):
     return out
 
 
-def _tuples(baryons, spins, dirac_dim):
+def _tuples(baryons, spins, dirac_dim, gnz=None):
     """All products of nonzero G entries (one per baryon): weights (n,) and the
-    slot index tuples split by flavour: u (n, n_u), d (n, n_d)."""
-    gnz = g_nonzeros(dirac_dim)
+    slot index tuples split by flavour: u (n, n_u), d (n, n_d). gnz: the
+    nonzero entries {index: [((xi1, xi2, xi3), value), ...]} (default: those
+    of G for dirac_dim)."""
+    if gnz is None:
+        gnz = g_nonzeros(dirac_dim)
     flav = [f for b in baryons for f in SLOT_FLAVOURS[b]]
     ws, us, ds = [], [], []
     for combo in itertools.product(*[gnz[int(s)] for s in spins]):
@@ -75,4 +78,35 @@ def correlator(baryons: str, delta, alpha, dirac_dim: int, S_u, S_d) -> complex:
         return 0j
     Wu = _flavour_contraction(S_u, us, ut)
     Wd = _flavour_contraction(S_d, ds, dt)
+    return complex(ws @ (Wu * Wd) @ wt)
+
+
+def correlator_sources(baryons: str, delta, chi, dirac_dim: int, S_list) -> complex:
+    """C(delta; chi) at one site for N_s mutually orthogonal quark sources
+    (Sec. 6), u = d, by explicit Wick enumeration (A <= 3).
+
+    The sink is the single-source operator (G, eq. def_g); the source baryons
+    carry chi = N_s * alpha + s and G~ (eq. G_tilde), whose quark indices are
+    xi = N_s * kappa + s. A quark contracted from sink index xi' to source
+    index xi propagates from source s: the matrix element is S_s[xi', kappa].
+    S_list: (N_s, 12, 12) complex."""
+    S_list = np.asarray(S_list, dtype=complex)
+    ns = S_list.shape[0]
+    nx = 3 * dirac_dim * ns
+    # rectangular propagator: sink rows xi' (12), source columns xi (nx)
+    S = np.zeros((12, nx), dtype=complex)
+    for s in range(ns):
+        for k in range(3 * dirac_dim):
+            S[:, ns * k + s] = S_list[s, :, k]
+    Gt = g_tensor_sources(dirac_dim, ns)
+    src_nz = {}
+    for c in range(Gt.shape[0]):
+        nz = np.argwhere(Gt[c] != 0)
+        src_nz[c] = [((int(i), int(j), int(k)), float(Gt[c, i, j, k])) for i, j, k in nz]
+    ws, us, ds = _tuples(baryons, delta, dirac_dim)
+    wt, ut, dt = _tuples(baryons, chi, dirac_dim, gnz=src_nz)
+    if len(ws) == 0 or len(wt) == 0:
+        return 0j
+    Wu = _flavour_contraction(S, us, ut)
+    Wd = _flavour_contraction(S, ds, dt)
     return complex(ws @ (Wu * Wd) @ wt)

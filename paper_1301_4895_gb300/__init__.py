@@ -62,7 +62,7 @@ class Props(ctypes.Structure):
     _fields_ = [("s_u", ctypes.c_void_p), ("s_d", ctypes.c_void_p), ("dtype", ctypes.c_int32),
                 ("memory", ctypes.c_int32), ("n_cfg", ctypes.c_int32), ("nt", ctypes.c_int32),
                 ("lx", ctypes.c_int32), ("ly", ctypes.c_int32), ("lz", ctypes.c_int32),
-                ("stride_cfg", ctypes.c_int64), ("stride_t", ctypes.c_int64)]
+                ("stride_cfg", ctypes.c_int64), ("stride_t", ctypes.c_int64), ("n_src", ctypes.c_int32)]
 
 
 class Tune(ctypes.Structure):
@@ -252,8 +252,9 @@ def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0
     """``mbc_contract`` on a u = d propagator field.
 
     field: torch tensor (device memory) or numpy array (host memory) of shape
-    (n_cfg, nt, Lz, Ly, Lx, 12, 12), complex128 or complex64, contiguous.
-    Returns out: complex128 (n_cfg, n_lists, t1 - t0, n_mom, n_comp_max) on the
+    (n_cfg, nt, Lz, Ly, Lx, 12, 12), or (n_cfg, nt, Lz, Ly, Lx, n_src, 12, 12)
+    for lists built with n_sources = n_src (Sec. 6), complex128 or complex64,
+    contiguous. Returns out: complex128 (n_cfg, n_lists, t1 - t0, n_mom, n_comp_max) on the
     same side as the field.
     """
     lib = load()
@@ -272,9 +273,10 @@ def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0
         dtype = C128 if field.dtype == torch.complex128 else C64
         ptr = field.data_ptr()
         shape = tuple(field.shape)
-    if len(shape) != 7 or shape[-2:] != (12, 12):
-        raise ValueError("field shape must be (n_cfg, nt, Lz, Ly, Lx, 12, 12)")
+    if len(shape) not in (7, 8) or shape[-2:] != (12, 12):
+        raise ValueError("field shape must be (n_cfg, nt, Lz, Ly, Lx, [n_src,] 12, 12)")
     n_cfg, nt, lz, ly, lx = shape[:5]
+    n_src = shape[5] if len(shape) == 8 else 1
     t1e = nt if t1 == 0 else t1
     moms = np.ascontiguousarray(np.array(moms, dtype=np.int32).reshape(-1, 3))
     comp_max = max(1, max(tl.stats()["n_comp"] for tl in lists))
@@ -286,7 +288,7 @@ def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0
             import torch
             out = torch.empty(oshape, dtype=torch.complex128, device=field.device)  # the library zero-fills
     optr = out.ctypes.data if is_np else out.data_ptr()
-    pr = Props(ptr, ptr, dtype, MEM_HOST if is_np else MEM_DEVICE, n_cfg, nt, lx, ly, lz, 0, 0)
+    pr = Props(ptr, ptr, dtype, MEM_HOST if is_np else MEM_DEVICE, n_cfg, nt, lx, ly, lz, 0, 0, n_src)
     tn = None
     if tune is not None:
         unknown = set(tune) - set(Tune.FIELDS)
@@ -315,7 +317,9 @@ def contract_noalloc(field, term_list, out, moms=((0, 0, 0),), t0: int = 0, t1: 
     n_cfg, nt, lz, ly, lx = shape[:5]
     dtype = C128 if field.dtype == torch.complex128 else C64
     moms = np.ascontiguousarray(np.array(moms, dtype=np.int32).reshape(-1, 3))
-    pr = Props(field.data_ptr(), field.data_ptr(), dtype, MEM_DEVICE, n_cfg, nt, lx, ly, lz, 0, 0)
+    if len(shape) != 7 or shape[-2:] != (12, 12):
+        raise ValueError("field shape must be (n_cfg, nt, Lz, Ly, Lx, 12, 12)")
+    pr = Props(field.data_ptr(), field.data_ptr(), dtype, MEM_DEVICE, n_cfg, nt, lx, ly, lz, 0, 0, 1)
     op = ContractOpts(FP64, moms.shape[0], moms.ctypes.data, t0, t1, None, SINK_POINT)
     _check(lib.mbc_contract_noalloc(ctypes.byref(pr), term_list.handle, ctypes.byref(op), out.data_ptr(),
                                     _stream_ptr(stream)), "mbc_contract_noalloc")

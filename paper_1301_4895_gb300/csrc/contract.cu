@@ -131,15 +131,20 @@ mbc_status upload(T **dst, const T *src, size_t n) {
     return MBC_OK;
 }
 
+// Nonzero entries of Gamma_2 (eq. def_g): 4 relativistic, 2 nonrelativistic.
+inline int n_g2(const mbc_term_list *L) { return L->dim == 4 ? 4 : 2; }
+
 // Build the small-kernel plan (shared-memory layout of one site) on the host.
+// The shared-memory kernels hold square single-source tiles only.
 bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries) {
     std::memset(&P, 0, sizeof(P));
     const int A = L->A;
     if (A > 16 || L->n_comp > kSmallMaxComp || L->n_comp < 1) return false;
+    if (L->n_sources != 1) return false;
     P.A = A;
     P.dim = L->dim;
     P.nxi = L->nxi;
-    P.n_g2 = L->dim == 4 ? 4 : 2;
+    P.n_g2 = n_g2(L);
     P.n_comp = L->n_comp;
     P.n_steps = A - 1;
     P.path0 = L->path[0];
@@ -478,8 +483,8 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
     p += align256(ls.c_bytes);
     int32_t *sexp = reinterpret_cast<int32_t *>(p);
     const int nsm = sm_count(device);
-    const int nxi = L->nxi;
-    const size_t blk_smem = (size_t)16 * 4 * nxi * nxi * sizeof(V);
+    const int nxi = L->nxi, nrow = 3 * L->dim;
+    const size_t blk_smem = (size_t)16 * (nrow * nxi + 3 * nxi * nxi) * sizeof(V);
     {
         int per_sm = 0;
         mbc_status pst = prepare_kernel((const void *)k_large_blocks<Tr>, device, 512, blk_smem, &per_sm);
@@ -492,7 +497,7 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
         wv.v3 = F.lx * F.ly * F.lz;
         wv.v3p = v3p;
         wv.n_items = n_items;
-        k_large_blocks<Tr><<<W / 16, 512, blk_smem, stream>>>(F, wv, nxi, L->dim == 4 ? 4 : 2, (int)L->block_size,
+        k_large_blocks<Tr><<<W / 16, 512, blk_smem, stream>>>(F, wv, nrow, nxi, n_g2(L), (int)L->block_size,
                                                               (int)binom64(nxi, 2), L->need_block[0],
                                                               L->need_block[1], fP, fN, sexp);
         MBC_CUDA_TRY(cudaGetLastError());
@@ -542,7 +547,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
                          const mbc_tune *tune, int device, cudaStream_t stream, char *scratch, const double2 *phase,
                          int li, int n_lists, int comp_max, double2 *out, int64_t n_slabs, const LargeSizes &ls) {
     using V = typename Tr::V;
-    const int nxi = L->nxi, bs = (int)L->block_size;
+    const int nxi = L->nxi, nrow = 3 * L->dim, bs = (int)L->block_size;
     const int v3 = F.lx * F.ly * F.lz;
     const int tps = (v3 + 15) / 16;
     const int64_t n_tiles = n_slabs * tps;
@@ -567,7 +572,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
     int32_t *sexp = reinterpret_cast<int32_t *>(p);
     const int nsm = sm_count(device);
     // 1. blocks of every site, phase-weighted tile sums, reduction over tiles
-    const size_t smem = (size_t)16 * 4 * nxi * nxi * sizeof(double2);
+    const size_t smem = (size_t)16 * (nrow * nxi + 3 * nxi * nxi) * sizeof(double2);
     {
         int per_sm = 0;
         mbc_status pst = prepare_kernel((const void *)k_project_blocks, device, 512, smem, &per_sm);
@@ -575,7 +580,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
     }
     {
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)nsm * 8));
-        k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nxi, L->dim == 4 ? 4 : 2, bs,
+        k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nrow, nxi, n_g2(L), bs,
                                                                 (int)binom64(nxi, 2), L->need_block[0],
                                                                 L->need_block[1], tps, n_tiles, partial);
         MBC_CUDA_TRY(cudaGetLastError());
@@ -660,13 +665,17 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     if (opts->n_mom < 1 || opts->n_mom > kMaxMom || !opts->mom) return MBC_ERR_INVALID_ARG;
     const int t0 = opts->t0, t1 = opts->t1 == 0 ? props->nt : opts->t1;
     if (t0 < 0 || t1 > props->nt || t1 <= t0) return MBC_ERR_INVALID_ARG;
+    const int n_src = props->n_src == 0 ? 1 : props->n_src;
+    if (n_src < 1 || n_src > 4) return MBC_ERR_INVALID_ARG;
     for (int i = 0; i < n_lists; ++i) {
         if (!lists[i]) return MBC_ERR_INVALID_ARG;
-        if (lists[i]->n_sources != 1 || lists[i]->n_sinks != 1) return MBC_ERR_UNSUPPORTED;
+        if (lists[i]->n_sources != n_src) return MBC_ERR_INVALID_ARG;  // list and field disagree
+        // one sink function; source tiles up to 12 columns (c_pair tables)
+        if (lists[i]->n_sinks != 1 || lists[i]->nxi > 12) return MBC_ERR_UNSUPPORTED;
     }
     const int64_t v3 = (int64_t)props->lx * props->ly * props->lz;
     if (v3 > (1LL << 30)) return MBC_ERR_INVALID_ARG;
-    const int64_t site_elems = 144;
+    const int64_t site_elems = 144LL * n_src;
     const int64_t stride_t = props->stride_t ? props->stride_t : v3 * site_elems;
     const int64_t stride_cfg = props->stride_cfg ? props->stride_cfg : stride_t * props->nt;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_v);
@@ -720,6 +729,7 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     F.stride_t = f_stride_t;
     F.t0 = (int)(t0 - f_t_shift);
     F.n_t = n_t;
+    F.n_src = n_src;
     // with staging, slice t0 sits at index 0: shift the base instead
     MomDesc M;
     std::memset(&M, 0, sizeof(M));
@@ -1035,6 +1045,7 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     if (!props || !list || !opts || !out || !props->s_u || !props->s_d) return MBC_ERR_INVALID_ARG;
     if (props->s_u != props->s_d) return MBC_ERR_UNSUPPORTED;
     if (list->n_sources != 1 || list->n_sinks != 1) return MBC_ERR_UNSUPPORTED;
+    if (props->n_src > 1) return MBC_ERR_UNSUPPORTED;
     if (props->memory != MBC_MEM_DEVICE || opts->precision != MBC_FP64) return MBC_ERR_UNSUPPORTED;
     if (opts->sink_mode != MBC_SINK_POINT) return MBC_ERR_UNSUPPORTED;
     if (props->dtype != MBC_C128 && props->dtype != MBC_C64) return MBC_ERR_INVALID_ARG;
@@ -1091,6 +1102,7 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     F.stride_cfg = props->stride_cfg ? props->stride_cfg : stride_t * props->nt;
     F.t0 = t0;
     F.n_t = n_t;
+    F.n_src = 1;
     MomDesc M;
     std::memset(&M, 0, sizeof(M));
     M.n_mom = opts->n_mom;

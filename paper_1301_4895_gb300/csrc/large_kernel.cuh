@@ -33,31 +33,33 @@ __device__ __forceinline__ bool item_site(const FieldDesc &F, const WaveDesc &wv
 }
 
 // Blocks for 16 sites per CTA (512 threads): thread = (site lane, entry slice).
+// The tile of a site has nrow sink rows (3 x Dirac dimension) and nxi source
+// columns (quark index over all sources).
 template <class Tr>
-__global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, int nxi, int n_g2, int block_size,
-                                                      int npair, int need_p, int need_n, typename Tr::V *fP,
-                                                      typename Tr::V *fN, int32_t *sexp_out) {
+__global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, int nrow, int nxi, int n_g2,
+                                                      int block_size, int npair, int need_p, int need_n,
+                                                      typename Tr::V *fP, typename Tr::V *fN, int32_t *sexp_out) {
     using V = typename Tr::V;
     constexpr int NS = 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *S = reinterpret_cast<V *>(smem_raw);  // [NS][nxi*nxi]
-    V *Q = S + NS * nxi * nxi;               // [NS][3*nxi*nxi]
+    V *S = reinterpret_cast<V *>(smem_raw);  // [NS][nrow*nxi]
+    V *Q = S + NS * nrow * nxi;              // [NS][3*nxi*nxi]
     const int sl = threadIdx.x % NS, slice = threadIdx.x / NS, nslice = blockDim.x / NS;
     const int w0 = blockIdx.x * NS;  // first site of this CTA within the wave
-    const int nent = nxi * nxi;
+    const int nent = nrow * nxi, nq = nxi * nxi;
     // load + scale: one warp per site
     for (int s = threadIdx.x >> 5; s < NS; s += blockDim.x >> 5) {
         int lane = threadIdx.x & 31;
         int cfg, t, site;
         bool live = item_site(F, wv, wv.item0 + w0 + s, cfg, t, site);
-        int64_t base = live ? cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * 144 : 0;
+        int64_t base = live ? cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * site_elems(F) : 0;
         double2 sv[5];
         double amax = 0.0;
         for (int q = 0; q < 5; ++q) {
             int e = lane + 32 * q;
             sv[q] = make_double2(0, 0);
             if (live && e < nent) {
-                sv[q] = load_prop(F, base, (e / nxi) * 12 + (e % nxi));
+                sv[q] = load_prop(F, base, tile_index(F, e, nxi));
                 amax = fmax(amax, fmax(fabs(sv[q].x), fabs(sv[q].y)));
             }
         }
@@ -73,13 +75,13 @@ __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, 
         if (lane == 0) sexp_out[w0 + s] = se;
     }
     __syncthreads();
-    for (int e = slice; e < 3 * nent; e += nslice) {
-        int c = e / nent, r = e % nent;
-        Q[sl * 3 * nent + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
+    for (int e = slice; e < 3 * nq; e += nslice) {
+        int c = e / nq, r = e % nq;
+        Q[sl * 3 * nq + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
     }
     __syncthreads();
     const V *Ss = S + sl * nent;
-    const V *Qs = Q + sl * 3 * nent;
+    const V *Qs = Q + sl * 3 * nq;
     const int per_spin = npair * nxi;
     for (int b = 0; b < 2; ++b) {
         if (b == 0 ? !need_p : !need_n) continue;

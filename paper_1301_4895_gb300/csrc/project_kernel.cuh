@@ -17,15 +17,16 @@
 namespace mbc {
 
 __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
-                                                        int nxi, int n_g2, int block_size, int npair, int need_p,
+                                                        int nrow, int nxi, int n_g2, int block_size, int npair,
+                                                        int need_p,
                                                         int need_n, int tiles_per_slab, int64_t n_tiles,
                                                         double2 *__restrict__ partial) {
     constexpr int NS = 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2 *S = reinterpret_cast<double2 *>(smem_raw);  // [NS][nxi*nxi]
-    double2 *Q = S + NS * nxi * nxi;                     // [NS][3*nxi*nxi]
+    double2 *S = reinterpret_cast<double2 *>(smem_raw);  // [NS][nrow*nxi]
+    double2 *Q = S + NS * nrow * nxi;                    // [NS][3*nxi*nxi]
     const int sl = threadIdx.x % NS, slice = threadIdx.x / NS, nslice = blockDim.x / NS;
-    const int nent = nxi * nxi;
+    const int nent = nrow * nxi, nq = nxi * nxi;
     const int v3 = F.lx * F.ly * F.lz;
     const int n_out = 2 * block_size;  // proton block, then neutron block
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -37,20 +38,20 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
             const int lane = threadIdx.x & 31;
             const int site = tin * NS + s;
             const bool live = site < v3;
-            const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * 144;
+            const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * site_elems(F);
             for (int e = lane; e < nent; e += 32)
-                S[s * nent + e] = live ? load_prop(F, base, (e / nxi) * 12 + (e % nxi)) : make_double2(0, 0);
+                S[s * nent + e] = live ? load_prop(F, base, tile_index(F, e, nxi)) : make_double2(0, 0);
         }
         __syncthreads();
-        for (int e = slice; e < 3 * nent; e += nslice) {
-            const int c = e / nent, r = e % nent;
-            Q[sl * 3 * nent + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
+        for (int e = slice; e < 3 * nq; e += nslice) {
+            const int c = e / nq, r = e % nq;
+            Q[sl * 3 * nq + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
         }
         __syncthreads();
         const int site = tin * NS + sl;
         const bool live = site < v3;
         const double2 *Ss = S + sl * nent;
-        const double2 *Qs = Q + sl * 3 * nent;
+        const double2 *Qs = Q + sl * 3 * nq;
         const int per_spin = npair * nxi;
         for (int b = 0; b < 2; ++b) {
             const bool need = b == 0 ? need_p : need_n;

@@ -84,7 +84,19 @@ struct FieldDesc {
     int32_t n_cfg, nt, lx, ly, lz;
     int64_t stride_cfg, stride_t;  // in complex elements
     int32_t t0, n_t;               // evaluated slices [t0, t0 + n_t)
+    int32_t n_src;                 // quark sources per site: a site holds n_src 12 x 12 matrices
 };
+
+// complex elements of one site (all sources)
+__device__ __forceinline__ int64_t site_elems(const FieldDesc &f) { return 144LL * f.n_src; }
+
+// Entry e of a site's propagator tile with nrow x ncol entries: row r = e / ncol
+// is the sink index, column c = e % ncol the source quark index
+// xi = n_src * kappa + s (Sec. 6), read from source s's 12 x 12 matrix.
+__device__ __forceinline__ int tile_index(const FieldDesc &f, int e, int ncol) {
+    const int r = e / ncol, c = e % ncol;
+    return (c % f.n_src) * 144 + r * 12 + c / f.n_src;
+}
 
 struct MomDesc {
     int32_t n_mom;
@@ -217,7 +229,7 @@ __global__ void __launch_bounds__(1024, 1)
         const int site = tin * T + warp;
         const bool live = site < V3;
         if (live) {
-            const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * 144;
+            const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * site_elems(F);
             // 1. propagator tile
             const int nent = nxi * nxi;
             for (int e = lane; e < nent; e += 32) R[P.s_off + e] = Tr::from_d(load_prop(F, base, (e / nxi) * 12 + (e % nxi)));
@@ -333,7 +345,7 @@ __global__ void __launch_bounds__(1024, 1)
         for (int s = warp; s < 32; s += NW) {
             const int site = site0 + s;
             const bool live = site < V3;
-            const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * 144;
+            const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * site_elems(F);
             // two passes over the tile (the second one hits L1): exponent, then values
             int emax = -100000;
             for (int e = lane; e < nent; e += 32) {

@@ -15,6 +15,10 @@ propagators):
 * ``row`` is the sink spinor-colour index, ``col`` the source index, both
   packed as ``3 * spin + colour``;
 * u and d quarks share one field (u = d);
+* with N_s quark sources (Sec. 6) a site holds N_s such matrices, axis
+  ``[..., s, row, col]``; source 0 is the single-source slab above and source
+  s >= 1 draws the same shape from its own stream ``SeedSequence([seed, cfg,
+  t, s])``;
 * complex64 storage is the complex128 value rounded to nearest; every consumer
   (oracle included) promotes the rounded values, so storage rounding is never
   counted as a compute error.
@@ -23,7 +27,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["slab", "field", "site_coords"]
+__all__ = ["slab", "slab_sources", "field", "site_coords"]
 
 
 def slab(seed: int, cfg: int, t: int, dims, lam: float, dtype=np.complex128) -> np.ndarray:
@@ -35,9 +39,23 @@ def slab(seed: int, cfg: int, t: int, dims, lam: float, dtype=np.complex128) -> 
     return s.astype(dtype)
 
 
+def slab_sources(seed: int, cfg: int, t: int, dims, lam: float, n_src: int,
+                 dtype=np.complex128) -> np.ndarray:
+    """Propagators of N_s sources for one slab, shape (Lz, Ly, Lx, n_src, 12, 12)."""
+    lz, ly, lx = (int(d) for d in dims)
+    out = np.empty((lz, ly, lx, int(n_src), 12, 12), dtype=dtype)
+    out[..., 0, :, :] = slab(seed, cfg, t, dims, lam, dtype)
+    for s in range(1, int(n_src)):
+        rng = np.random.default_rng(np.random.SeedSequence([int(seed), int(cfg), int(t), s]))
+        g = rng.standard_normal((lz, ly, lx, 12, 12, 2))
+        out[..., s, :, :] = ((g[..., 0] + 1j * g[..., 1]) * np.exp(-float(lam) * float(t))).astype(dtype)
+    return out
+
+
 def field(seed: int, n_cfg: int, nt: int, dims, lam: float, dtype=np.complex128,
-          cfgs=None, ts=None) -> np.ndarray:
-    """Stack of slabs, shape (n_cfg', nt', Lz, Ly, Lx, 12, 12).
+          cfgs=None, ts=None, n_src: int = 0) -> np.ndarray:
+    """Stack of slabs, shape (n_cfg', nt', Lz, Ly, Lx, 12, 12), or
+    (n_cfg', nt', Lz, Ly, Lx, n_src, 12, 12) when n_src >= 1.
 
     ``cfgs`` / ``ts`` select a subset of configurations / time slices (default:
     all); each slab is generated from its own (seed, cfg, t) stream.
@@ -45,10 +63,12 @@ def field(seed: int, n_cfg: int, nt: int, dims, lam: float, dtype=np.complex128,
     cfgs = list(range(n_cfg)) if cfgs is None else list(cfgs)
     ts = list(range(nt)) if ts is None else list(ts)
     lz, ly, lx = (int(d) for d in dims)
-    out = np.empty((len(cfgs), len(ts), lz, ly, lx, 12, 12), dtype=dtype)
+    site = (12, 12) if n_src < 1 else (int(n_src), 12, 12)
+    out = np.empty((len(cfgs), len(ts), lz, ly, lx) + site, dtype=dtype)
     for i, c in enumerate(cfgs):
         for j, t in enumerate(ts):
-            out[i, j] = slab(seed, c, t, dims, lam, dtype)
+            out[i, j] = (slab(seed, c, t, dims, lam, dtype) if n_src < 1
+                         else slab_sources(seed, c, t, dims, lam, n_src, dtype))
     return out
 
 

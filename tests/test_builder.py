@@ -166,11 +166,20 @@ def test_two_source_single_components_match_table6():
         tl = mbc.build_term_list(n_p, n_n, 2, spins=[(sp, sp)], n_sources=2, n_sinks=2)
         assert tl.stats()["n_ops_total"] == ops, row
         assert tl.n_l(0) == int(row[4]), row
-    # contraction kernels are built for one source: refused before device work
-    tl = mbc.build_term_list(1, 1, 2, spins=[((0, 2), (0, 2))], n_sources=2, n_sinks=2)
+    # contraction kernels take one sink function, at most 12 source quark
+    # index values, and a field with as many sources as the list: every other
+    # case is refused before any device work
     import numpy as np
+    f2 = np.zeros((1, 1, 1, 1, 1, 2, 12, 12), dtype=np.complex128)
+    tl = mbc.build_term_list(1, 1, 2, spins=[((0, 2), (0, 2))], n_sources=2, n_sinks=2)
     with pytest.raises(mbc.MbcError):
-        mbc.contract(np.zeros((1, 1, 1, 1, 1, 12, 12), dtype=np.complex128), [tl])
+        mbc.contract(f2, [tl])
+    one_sink = mbc.build_term_list(1, 1, 2, spins=[((0, 1), (0, 3))], n_sources=2)
+    with pytest.raises(mbc.MbcError):
+        mbc.contract(f2[:, :, :, :, :, 0], [one_sink])  # field without the source axis
+    rel = mbc.build_term_list(1, 0, 4, spins=[((0,), (5,))], n_sources=2)
+    with pytest.raises(mbc.MbcError):
+        mbc.contract(f2, [rel])  # 24 source quark index values
 
 
 def test_two_source_lists_agree_with_oracle():

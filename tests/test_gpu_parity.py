@@ -369,6 +369,76 @@ def test_spin_projection_outputs(mbc, n_p, n_n, D, projections):
                 assert e <= TOL[p], (k, t, p, e)
 
 
+_TWO_SRC_PLANS = {}
+
+
+def two_source_plan(n_p, n_n, comps):
+    """Oracle plan for one nonrelativistic sink and two quark sources (Sec. 6):
+    G~ builds L, the blocks keep the sink's G."""
+    from oracle import gamma, recursion
+    key = (n_p, n_n, tuple(comps))
+    if key not in _TWO_SRC_PLANS:
+        _TWO_SRC_PLANS[key] = recursion.Plan(n_p, n_n, 2, requests=list(comps), G=gamma.g_tensor_sources(2, 2),
+                                             G_sink=gamma.g_tensor(2))
+    return _TWO_SRC_PLANS[key]
+
+
+@pytest.mark.parametrize("n_p,n_n,spins", [
+    (1, 1, None),
+    (2, 1, [((0, 1, 0), (0, 1, 2)), ((0, 1, 1), (1, 3, 0)), ((0, 1, 0), (0, 2, 2))]),
+    (1, 2, [((1, 0, 1), (3, 0, 2))]),
+    (2, 2, [((0, 1, 0, 1), (0, 2, 1, 3)), ((0, 1, 0, 1), (0, 1, 2, 3)), ((0, 1, 0, 1), (1, 3, 1, 3))]),
+])
+def test_two_quark_sources(mbc, n_p, n_n, spins):
+    """Two mutually orthogonal quark sources, one nonrelativistic sink (Sec. 6):
+    field [.., source, 12, 12], source indices chi = 2 alpha + s; point sinks
+    and momentum-projected blocks against the oracle on the combined-column
+    propagator."""
+    from oracle import projection, recursion
+    dims = (3, 2, 5)
+    field = synth.field(24, 2, 2, dims, 0.4, n_src=2)
+    moms = ((0, 0, 0), (1, 0, 2))
+    tl = mbc.build_term_list(n_p, n_n, 2, spins=spins, n_sources=2)
+    comps = tl.components()
+    plan = two_source_plan(n_p, n_n, comps)
+    label = f"({n_p},{n_n}) D=2 two sources"
+    for sink in (mbc.SINK_POINT, mbc.SINK_BLOCK_MOMENTUM):
+        outs = {p: run(mbc, field, [tl], p, moms=moms, sink=sink) for p in (0, 1)}
+        for cfg in range(2):
+            for t in range(2):
+                S = recursion.source_columns(field[cfg, t], 2)
+                if sink == mbc.SINK_POINT:
+                    ref, scale = oracle_slab(plan, S, dims, list(moms))
+                    scale = scale[None, :]
+                else:
+                    ref, scale = projection.projected_correlators(plan, S, dims, moms)
+                for p in (0, 1):
+                    got = outs[p][cfg, 0, t, :, : len(comps)]
+                    e = float(np.max(np.abs(got - ref) / scale))
+                    record(label + (" projected" if sink else ""), p, e)
+                    assert e <= TOL[p], (sink, p, cfg, t, e)
+    # host-memory staging of the source axis
+    host = mbc.contract(field, [tl], precision=0, moms=moms)
+    dev = run(mbc, field, [tl], 0, moms=moms)
+    assert np.array_equal(host, dev)
+
+
+def test_two_quark_sources_larger_slab(mbc):
+    """4He, two sources, one 8^3 slab: several waves of the large-stage path."""
+    dims = (8, 8, 8)
+    field = synth.field(25, 1, 1, dims, 0.4, n_src=2)
+    spins = [((0, 1, 0, 1), (0, 3, 1, 2))]
+    tl = mbc.build_term_list(2, 2, 2, spins=spins, n_sources=2)
+    plan = two_source_plan(2, 2, tl.components())
+    from oracle import recursion
+    ref, scale = oracle_slab(plan, recursion.source_columns(field[0, 0], 2), dims, [(0, 0, 0), (0, 1, 0)])
+    for p in (0, 1):
+        got = run(mbc, field, [tl], p, moms=((0, 0, 0), (0, 1, 0)), tune={"wave_sites": 128})[0, 0, 0, :, :1]
+        e = max_rel_err(got, ref, scale)
+        record("(2,2) D=2 two sources 8^3", p, e)
+        assert e <= TOL[p], (p, e)
+
+
 def test_zz_accuracy_report(mbc, capsys):
     """Prints the worst |dC| / sum|terms| of the parity tests above (run with
     -s to see it); fails if any exceeded its bound."""

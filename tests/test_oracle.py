@@ -335,3 +335,53 @@ def test_projected_blocks_translation_phase(rng):
     C2, _ = projection.projected_correlators(plan, moved, dims, mom)
     expect = C * np.exp(-2j * np.pi * 2 * 1 / 4)
     assert np.all(np.abs(C2 - expect) <= 1e-13 * sc)
+
+
+# ---- several quark sources (Sec. 6) ----------------------------------------------
+
+def _two_source_requests(n_p, n_n, rng, n):
+    """Random (sink spins < 2, source chi < 4) assignments, each species sorted."""
+    out = []
+    while len(out) < n:
+        snk = tuple(sorted(rng.choice(2, n_p, replace=False))) + tuple(sorted(rng.choice(2, n_n, replace=False)))
+        src = tuple(sorted(rng.choice(4, n_p, replace=False))) + tuple(sorted(rng.choice(4, n_n, replace=False)))
+        out.append((tuple(int(v) for v in snk), tuple(int(v) for v in src)))
+    return out
+
+
+@pytest.mark.parametrize("n_p,n_n", [(1, 0), (0, 1), (1, 1), (0, 2),
+                                     pytest.param(2, 1, marks=pytest.mark.slow)])
+def test_two_source_recursion_equals_wick(rng, n_p, n_n):
+    """O3 with G~ at the source and G at the sink equals the explicit Wick
+    sum with one rectangular propagator per flavour whose column xi = 2 kappa
+    + s is column kappa of source s (Sec. 6), nonrelativistic operators."""
+    S2 = np.stack([rand_prop(rng), rand_prop(rng)])
+    reqs = _two_source_requests(n_p, n_n, rng, 6 if n_p + n_n < 3 else 1)
+    plan = recursion.Plan(n_p, n_n, 2, requests=reqs, G=gamma.g_tensor_sources(2, 2), G_sink=gamma.g_tensor(2))
+    C, sc = plan.evaluate(recursion.source_columns(S2, 2)[None])
+    bs = baryons(n_p, n_n)
+    for r, (d, a) in enumerate(plan.requests):
+        c1 = wick.correlator_sources(bs, d, a, 2, S2)
+        assert abs(C[0, r] - c1) <= 1e-13 * sc[0, r], (d, a)
+
+
+def test_two_source_single_source_limits(rng):
+    """Source indices chi = 2 alpha + s all on one source s reduce to the
+    single-source correlator with that source's propagator; one quark source
+    replaced by zero kills every component that uses it."""
+    S2 = np.stack([rand_prop(rng), rand_prop(rng)])
+    Gt, G = gamma.g_tensor_sources(2, 2), gamma.g_tensor(2)
+    snk = (0, 1, 0)
+    reqs = [(snk, (0, 2, 2)), (snk, (1, 3, 3)), (snk, (0, 2, 1)), (snk, (0, 3, 2))]
+    plan = recursion.Plan(2, 1, 2, requests=reqs, G=Gt, G_sink=G)
+    C, sc = plan.evaluate(recursion.source_columns(S2, 2)[None])
+    one = recursion.Plan(2, 1, 2, requests=[(snk, (0, 1, 1))])
+    for r, s in ((0, 0), (1, 1)):
+        ref, _ = one.evaluate(S2[s][None])
+        assert abs(C[0, r] - ref[0, 0]) <= 1e-13 * sc[0, r]
+    assert abs(C[0, 2]) > 1e-8 * sc[0, 2]  # mixed sources: a genuine new component
+    Z = S2.copy()
+    Z[1] = 0.0
+    Cz, _ = plan.evaluate(recursion.source_columns(Z, 2)[None])
+    assert Cz[0, 1] == 0 and Cz[0, 2] == 0 and Cz[0, 3] == 0
+    assert abs(Cz[0, 0] - C[0, 0]) <= 1e-13 * sc[0, 0]
