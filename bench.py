@@ -58,11 +58,29 @@ def parse():
     ap.add_argument("--cfgs", type=int, default=1, help="configurations per rank")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    ap.add_argument("--combined", action="store_true",
+                    help="contract the workload's nuclei with one list on a shared recursion path (Sec. 7)")
     ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner first")
     ap.add_argument("--tune", default="", help='fixed launch shape as JSON, e.g. {"wave_sites": 256}')
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
+
+
+def shared_path(nuclei):
+    """A recursion path on which every nucleus of the workload is the
+    nucleus of a prefix: smaller nuclei first, each adding its extra baryons
+    in the paper's order (more numerous species first, neutrons on a tie)."""
+    path = []
+    cp = cn = 0
+    for n_p, n_n, _, _ in sorted(nuclei, key=lambda n: n[0] + n[1]):
+        dp, dn = n_p - cp, n_n - cn
+        if dp < 0 or dn < 0:
+            raise SystemExit("the workload's nuclei do not lie on one path")
+        first, nf = (0, dp) if dp > dn else (1, dn)
+        path += [first] * nf + [1 - first] * (dp + dn - nf)
+        cp, cn = n_p, n_n
+    return path
 
 
 def site_flops(st, dirac_dim):
@@ -269,13 +287,21 @@ def main():
     nt = args.nt or nt_full
     if args.workload in ("he4rel", "be8") and not args.nt:
         nt = 1  # one time slice: 4096 sinks
-    lists = [mbc.build_term_list(n_p, n_n, D, spins=spins) for (n_p, n_n, D, spins) in nuclei]
+    if args.combined:
+        if len({n[2] for n in nuclei}) != 1:
+            raise SystemExit("--combined needs one operator type")
+        lists = [mbc.build_combined([dict(n_p=a, n_n=b, spins=sp) for a, b, _, sp in nuclei], nuclei[0][2],
+                                    path=shared_path(nuclei))]
+        list_dims = [nuclei[0][2]]
+    else:
+        lists = [mbc.build_term_list(n_p, n_n, D, spins=spins) for (n_p, n_n, D, spins) in nuclei]
+        list_dims = [n[2] for n in nuclei]
     stats = [tl.stats() for tl in lists]
     field_np = make_field(wl, range(rank * args.cfgs, (rank + 1) * args.cfgs), nt)
     v3 = dims[0] * dims[1] * dims[2]
     field = torch.from_numpy(field_np).to(dev)
     stream = torch.cuda.Stream(dev)
-    units_per_step = v3 * nt * len(lists) * args.cfgs
+    units_per_step = v3 * nt * len(nuclei) * args.cfgs
     tunes = {0: None, 1: None}
     if args.tune:
         tunes = {0: json.loads(args.tune), 1: json.loads(args.tune)}
@@ -369,7 +395,7 @@ def main():
     value_mx = units_per_step * world * args.steps / (msmx * 1e-3)
     value = value64 if primary == 0 else value_mx
     # roofline of the dominant kernel (the contraction kernel; FP64 pipe)
-    fl = [site_flops(st, n[2]) for st, n in zip(stats, nuclei)]
+    fl = [site_flops(st, d) for st, d in zip(stats, list_dims)]
     flops_step = sum(f["total"] for f in fl) * v3 * nt * args.cfgs
     peaks = measured_peaks()
     probe64 = mbc.fma_probe(0)
@@ -399,7 +425,7 @@ def main():
     roof_mx = roofline(kmx, msmx, nmx, nominal32, probe32,
                        "FP32 vector, derived: 152 SMs x 128 FFMA/clk x max SM clock", 1)
     roof = roof64 if primary == 0 else roof_mx
-    if roof is not None and args.workload == "nonrel" and primary == 0 and not has_large:
+    if roof is not None and args.workload == "nonrel" and primary == 0 and not has_large and not args.combined:
         roof["traffic"] = profiled_traffic("k_small_fp64_he3_he4_16x16x16x16.md", v3 * nt * args.cfgs)
         roof["traffic_note"] = ("DRAM bytes per launch (one launch per step) from the committed ncu summary, "
                                 "scaled from 65,536 to the step's sites")
@@ -411,6 +437,7 @@ def main():
         "config": {"workload": desc, "nuclei": [f"({n[0]},{n[1]}) D={n[2]}" for n in nuclei],
                    "sites_per_step": v3 * nt * args.cfgs, "units_per_step": units_per_step,
                    "configurations_per_rank": args.cfgs, "graph": bool(args.graph),
+                   "combined_path": stats[0]["path"] if args.combined else None,
                    "tune": {"fp64": tunes[0], "mixed": tunes[1]},
                    "l2": "inputs larger than L2 (field %.0f MB)" % (field_np.nbytes / 2 ** 20),
                    "parallelism": f"configurations sharded over {world} GPU(s)"},

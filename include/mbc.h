@@ -145,7 +145,8 @@ typedef struct {
     int64_t block_size;                  /* antisymmetric block components   */
     int32_t n_comp;                      /* output components per site       */
     int64_t n_l_total;                   /* nonzero L entries, all components */
-    double norm;                         /* (n_P! n_N!)^2                    */
+    double norm;                         /* (n_P! n_N!)^2 of the largest nucleus */
+    int32_t n_parts;                     /* nuclei in the list (mbc_build_combined) */
 } mbc_list_stats;
 
 /*
@@ -157,6 +158,34 @@ typedef struct {
  * On any other status *out is set to NULL.
  */
 mbc_status mbc_build_term_list(const mbc_op_spec *spec, mbc_term_list **out);
+
+/*
+ * Build one term list for n_specs nuclei on one recursion path (Sec. 7: the
+ * stages of the largest nucleus pass through every smaller nucleus whose
+ * baryons are the first ones added, and its components are contracted at
+ * that stage with its own L; only the union of the needed components is
+ * computed). The specs share dirac_dim, n_sources and n_sinks; the largest
+ * nucleus fixes the path (its path field, else the paper's rule); every
+ * other spec must have (n_p, n_n) equal to the counts of the first
+ * n_p + n_n path entries, and a path field, if given, equal to that prefix.
+ * Each spec keeps its own spin_mode and selections. The outputs are the
+ * specs' components in the order given, spec after spec (mbc_term_list_part
+ * gives the ranges); mbc_term_list_components pads the labels of a smaller
+ * nucleus with -1 up to the largest A. With n_specs = 1 this is
+ * mbc_build_term_list. Errors as mbc_build_term_list; a spec off the path,
+ * with other operators, or (n_specs > 1) a Pauli-forbidden largest nucleus
+ * gives MBC_ERR_INVALID_ARG.
+ */
+mbc_status mbc_build_combined(const mbc_op_spec *specs, int32_t n_specs, mbc_term_list **out);
+
+/* One nucleus of a list: its baryon counts and output components [c0, c1). */
+typedef struct {
+    int32_t n_p, n_n;
+    int32_t c0, c1;
+} mbc_list_part;
+
+/* Part j (0 <= j < stats.n_parts) of a list into *part (caller-owned). */
+mbc_status mbc_term_list_part(const mbc_term_list *list, int32_t j, mbc_list_part *part);
 
 /* Fill *st (caller-owned). */
 mbc_status mbc_term_list_stats(const mbc_term_list *list, mbc_list_stats *st);

@@ -341,6 +341,14 @@ int64_t o3_n_ops(const o3_plan *p, int64_t *per_step, int64_t *stage_sizes) {
     return t;
 }
 
+/* Needed keys of stage m (1-based), ascending; returns their number and
+ * copies them to out when out is not NULL. */
+int64_t o3_stage_keys(const o3_plan *p, int m, uint32_t *out) {
+    if (m < 1 || m > p->A) return -1;
+    if (out) memcpy(out, p->need[m - 1], sizeof(key_t32) * (size_t)p->n_need[m - 1]);
+    return p->n_need[m - 1];
+}
+
 int64_t o3_req_nl(const o3_plan *p, int r) { return p->req_off[r + 1] - p->req_off[r]; }
 double o3_norm(const o3_plan *p) { return p->norm; }
 

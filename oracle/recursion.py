@@ -54,6 +54,8 @@ def _load():
             lib.o3_blocks.restype = ctypes.c_int
             lib.o3_eval_blocks.argtypes = [P, ctypes.c_int64, P, P, P, P, P, P]
             lib.o3_eval_blocks.restype = ctypes.c_int
+            lib.o3_stage_keys.argtypes = [P, ctypes.c_int, P]
+            lib.o3_stage_keys.restype = ctypes.c_int64
             lib.o3_plan_set_sink.argtypes = [P, P]
             lib.o3_plan_set_sink.restype = None
             _lib = lib
@@ -136,6 +138,15 @@ class Plan:
         st = np.zeros(16, dtype=np.int64)
         t = self._lib.o3_n_ops(self._h, per.ctypes.data, st.ctypes.data)
         return int(t), per[: self.A - 1].tolist(), st[: self.A].tolist()
+
+    def stage_keys(self, m: int) -> np.ndarray:
+        """Needed components of stage m (1-based) after the backward pruning,
+        as packed keys (proton spins | neutron spins << 4 | u set << 8 |
+        d set << 20), ascending."""
+        n = int(self._lib.o3_stage_keys(self._h, m, None))
+        out = np.zeros(max(n, 1), dtype=np.uint32)
+        self._lib.o3_stage_keys(self._h, m, out.ctypes.data)
+        return out[:n]
 
     def n_l(self):
         """Nonzero L entries per request."""

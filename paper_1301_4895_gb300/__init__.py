@@ -55,7 +55,11 @@ class ListStats(ctypes.Structure):
                 ("ops_per_z", ctypes.c_int64 * MAX_A), ("stage_size", ctypes.c_int64 * MAX_A),
                 ("stage_bound", ctypes.c_int64 * MAX_A), ("q_bound", ctypes.c_int64 * MAX_A),
                 ("block_size", ctypes.c_int64), ("n_comp", ctypes.c_int32), ("n_l_total", ctypes.c_int64),
-                ("norm", ctypes.c_double)]
+                ("norm", ctypes.c_double), ("n_parts", ctypes.c_int32)]
+
+
+class ListPart(ctypes.Structure):
+    _fields_ = [("n_p", ctypes.c_int32), ("n_n", ctypes.c_int32), ("c0", ctypes.c_int32), ("c1", ctypes.c_int32)]
 
 
 class Props(ctypes.Structure):
@@ -98,6 +102,10 @@ def load(path: str | None = None):
         lib.mbc_status_string.restype = ctypes.c_char_p
         lib.mbc_build_term_list.argtypes = [ctypes.POINTER(OpSpec), ctypes.POINTER(V)]
         lib.mbc_build_term_list.restype = ctypes.c_int
+        lib.mbc_build_combined.argtypes = [ctypes.POINTER(OpSpec), ctypes.c_int32, ctypes.POINTER(V)]
+        lib.mbc_build_combined.restype = ctypes.c_int
+        lib.mbc_term_list_part.argtypes = [V, ctypes.c_int32, ctypes.POINTER(ListPart)]
+        lib.mbc_term_list_part.restype = ctypes.c_int
         lib.mbc_term_list_stats.argtypes = [V, ctypes.POINTER(ListStats)]
         lib.mbc_term_list_stats.restype = ctypes.c_int
         lib.mbc_term_list_components.argtypes = [V, V, V]
@@ -159,8 +167,17 @@ class TermList:
             "n_ops": list(st.n_ops[: st.n_steps]), "ops_per_z": list(st.ops_per_z[: st.n_steps]),
             "stage_size": list(st.stage_size[:A]), "stage_bound": list(st.stage_bound[:A]),
             "q_bound": list(st.q_bound[: st.n_steps]), "block_size": st.block_size, "n_comp": st.n_comp,
-            "n_l_total": st.n_l_total, "norm": st.norm,
+            "n_l_total": st.n_l_total, "norm": st.norm, "n_parts": st.n_parts,
         }
+
+    def parts(self):
+        """Nuclei of the list: [{"n_p", "n_n", "c0", "c1"}], outputs [c0, c1) each."""
+        out = []
+        for j in range(self.stats()["n_parts"]):
+            p = ListPart()
+            _check(self._lib.mbc_term_list_part(self._h, j, ctypes.byref(p)), "mbc_term_list_part")
+            out.append({"n_p": p.n_p, "n_n": p.n_n, "c0": p.c0, "c1": p.c1})
+        return out
 
     def components(self):
         st = self.stats()
@@ -187,18 +204,12 @@ class TermList:
             pass
 
 
-def build_term_list(n_p: int, n_n: int, dirac_dim: int = 4, spins=None, path=None, n_sources: int = 1,
-                    projections=None, n_sinks: int = 1) -> TermList:
-    """``mbc_build_term_list``. spins: None for every independent component,
-    or a list of (sink spins, source spins) pairs, protons first.
-    projections: instead of spins, a list of projections, each a list of
-    (sink spins, source spins, real weight) terms (Sec. 5); one output each."""
-    lib = load()
+def _op_spec(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, keep):
+    """Fill an OpSpec; arrays it points to are appended to keep."""
     A = n_p + n_n
     spec = OpSpec()
     spec.n_p, spec.n_n, spec.dirac_dim, spec.n_sources = n_p, n_n, dirac_dim, n_sources
     spec.n_sinks = n_sinks
-    keep = []
     if projections is not None:
         if spins is not None:
             raise ValueError("give spins or projections, not both")
@@ -229,11 +240,45 @@ def build_term_list(n_p: int, n_n: int, dirac_dim: int = 4, spins=None, path=Non
         pa = np.ascontiguousarray(np.array(path, dtype=np.int8))
         spec.path_len, spec.path = len(path), pa.ctypes.data
         keep.append(pa)
+    return spec
+
+
+def build_term_list(n_p: int, n_n: int, dirac_dim: int = 4, spins=None, path=None, n_sources: int = 1,
+                    projections=None, n_sinks: int = 1) -> TermList:
+    """``mbc_build_term_list``. spins: None for every independent component,
+    or a list of (sink spins, source spins) pairs, protons first.
+    projections: instead of spins, a list of projections, each a list of
+    (sink spins, source spins, real weight) terms (Sec. 5); one output each."""
+    lib = load()
+    keep = []
+    spec = _op_spec(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, keep)
     h = ctypes.c_void_p()
     rc = lib.mbc_build_term_list(ctypes.byref(spec), ctypes.byref(h))
     _check(rc, "mbc_build_term_list", ok=(0, 2))
     return TermList(h, rc, {"n_p": n_p, "n_n": n_n, "dirac_dim": dirac_dim, "spins": spins, "path": path,
                             "projections": projections, "n_sources": n_sources, "n_sinks": n_sinks})
+
+
+def build_combined(nuclei, dirac_dim: int = 4, path=None, n_sources: int = 1, n_sinks: int = 1) -> TermList:
+    """``mbc_build_combined``: one list for several nuclei on one recursion
+    path (Sec. 7). nuclei: list of dicts with "n_p", "n_n" and optionally
+    "spins" or "projections" (as for build_term_list); path: the order of the
+    largest nucleus (None: the paper's rule). Outputs follow the nuclei in
+    the order given (``TermList.parts``)."""
+    lib = load()
+    if not nuclei:
+        raise ValueError("no nuclei given")
+    keep = []
+    big = max(range(len(nuclei)), key=lambda j: nuclei[j]["n_p"] + nuclei[j]["n_n"])
+    arr = (OpSpec * len(nuclei))()
+    for j, nu in enumerate(nuclei):
+        arr[j] = _op_spec(nu["n_p"], nu["n_n"], dirac_dim, nu.get("spins"), path if j == big else None, n_sources,
+                          nu.get("projections"), n_sinks, keep)
+    h = ctypes.c_void_p()
+    rc = lib.mbc_build_combined(arr, len(nuclei), ctypes.byref(h))
+    _check(rc, "mbc_build_combined")
+    return TermList(h, rc, {"nuclei": nuclei, "dirac_dim": dirac_dim, "path": path, "n_sources": n_sources,
+                            "n_sinks": n_sinks})
 
 
 def _stream_ptr(stream):

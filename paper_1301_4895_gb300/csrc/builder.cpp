@@ -309,7 +309,90 @@ double factorial(int n) {
     return f;
 }
 
-mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
+// One nucleus of a (possibly combined) list: its requested components and the
+// terms (projection, sink spins, source spins, weight) that define them.
+struct Term {
+    int proj;           // output component within the part
+    const int8_t *snk, *src;
+    double w;
+};
+struct PartReq {
+    int np = 0, nn = 0, A = 0;
+    int n_comp = 0;
+    std::vector<int8_t> snk, src;  // n_comp * A labels (-1 for projections)
+    std::vector<Term> terms;
+    bool forbidden = false;
+};
+
+// Requested components of one nucleus (Sec. 4 all independent components,
+// Sec. 5 / Sec. 8 listed pairs or projections).
+void part_requests(const mbc_op_spec *spec, int dim, int dim_src, int nxi, PartReq &R) {
+    const int np = spec->n_p, nn = spec->n_n, A = np + nn;
+    R.np = np; R.nn = nn; R.A = A;
+    auto sets = [&](int k, int n) {
+        std::vector<std::vector<int8_t>> out;
+        for (i64 r = 0; r < binom(n, k); ++r) {
+            u32 m = colex_unrank(r, k, n);
+            std::vector<int8_t> v;
+            for (int s = 0; s < n; ++s)
+                if (m & (1u << s)) v.push_back((int8_t)s);
+            out.push_back(v);
+        }
+        return out;
+    };
+    R.forbidden = np > std::min(dim, dim_src) || nn > std::min(dim, dim_src) || 2 * np + nn > nxi ||
+                  np + 2 * nn > nxi;
+    if (spec->spin_mode == MBC_SPIN_ALL) {
+        std::vector<std::vector<int8_t>> snk_comps, src_comps;
+        if (!R.forbidden) {
+            for (auto &p : sets(np, dim))
+                for (auto &n : sets(nn, dim)) {
+                    std::vector<int8_t> v = p;
+                    v.insert(v.end(), n.begin(), n.end());
+                    snk_comps.push_back(v);
+                }
+            for (auto &p : sets(np, dim_src))
+                for (auto &n : sets(nn, dim_src)) {
+                    std::vector<int8_t> v = p;
+                    v.insert(v.end(), n.begin(), n.end());
+                    src_comps.push_back(v);
+                }
+        }
+        for (auto &a : snk_comps)
+            for (auto &b : src_comps) {
+                R.snk.insert(R.snk.end(), a.begin(), a.end());
+                R.src.insert(R.src.end(), b.begin(), b.end());
+            }
+        R.n_comp = (int)(snk_comps.size() * src_comps.size());
+    } else if (spec->spin_mode == MBC_SPIN_LISTED) {
+        R.n_comp = spec->n_spin_sel;
+        R.snk.assign(spec->snk_spins, spec->snk_spins + (size_t)A * spec->n_spin_sel);
+        R.src.assign(spec->src_spins, spec->src_spins + (size_t)A * spec->n_spin_sel);
+    } else {  // MBC_SPIN_PROJECTED: one output per projection; labels are not single spin tuples
+        R.n_comp = spec->n_proj;
+        R.snk.assign((size_t)A * spec->n_proj, (int8_t)-1);
+        R.src.assign((size_t)A * spec->n_proj, (int8_t)-1);
+    }
+    if (spec->spin_mode == MBC_SPIN_PROJECTED) {
+        for (int t = 0; t < spec->n_spin_sel; ++t)
+            R.terms.push_back({spec->term_proj[t], spec->snk_spins + (size_t)A * t, spec->src_spins + (size_t)A * t,
+                               spec->term_coef[t]});
+    } else {
+        for (int c = 0; c < R.n_comp; ++c)
+            R.terms.push_back({c, R.snk.data() + (size_t)A * c, R.src.data() + (size_t)A * c, 1.0});
+    }
+}
+
+// Build a term list for n nuclei that lie on one path (Sec. 7: smaller
+// nuclei on the path of the largest one reuse its stages). specs[0..n) share
+// dirac_dim, n_sources and n_sinks; the largest nucleus fixes the path and
+// every other one must be the nucleus of a prefix of it. With n = 1 this is
+// the list of one nucleus.
+mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
+    int big = 0;
+    for (int j = 1; j < n_specs; ++j)
+        if (specs[j].n_p + specs[j].n_n > specs[big].n_p + specs[big].n_n) big = j;
+    const mbc_op_spec *spec = &specs[big];
     const int np = spec->n_p, nn = spec->n_n, A = np + nn, D = spec->dirac_dim;
     const int ns = std::max(1, spec->n_sources), nk = std::max(1, spec->n_sinks);
     const int dim = D * nk;        // sink baryon index: spin x sink function (Sec. 6 psi)
@@ -329,50 +412,42 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
     }
     for (int i = 0; i < A; ++i) L->need_block[L->path[i]] = true;
 
-    // requested components
-    auto sets = [&](int k, int n) {
-        std::vector<std::vector<int8_t>> out;
-        for (i64 r = 0; r < binom(n, k); ++r) {
-            u32 m = colex_unrank(r, k, n);
-            std::vector<int8_t> v;
-            for (int s = 0; s < n; ++s)
-                if (m & (1u << s)) v.push_back((int8_t)s);
-            out.push_back(v);
-        }
-        return out;
-    };
-    bool forbidden = np > std::min(dim, dim_src) || nn > std::min(dim, dim_src) || 2 * np + nn > nxi ||
-                     np + 2 * nn > nxi;
-    if (spec->spin_mode == MBC_SPIN_ALL) {
-        std::vector<std::vector<int8_t>> snk_comps, src_comps;
-        if (!forbidden) {
-            for (auto &p : sets(np, dim))
-                for (auto &n : sets(nn, dim)) {
-                    std::vector<int8_t> v = p;
-                    v.insert(v.end(), n.begin(), n.end());
-                    snk_comps.push_back(v);
+    // every nucleus must be a prefix of the path, with the same operators
+    std::vector<PartReq> parts((size_t)n_specs);
+    for (int j = 0; j < n_specs; ++j) {
+        const mbc_op_spec &s = specs[j];
+        const int Aj = s.n_p + s.n_n;
+        if (s.dirac_dim != D || std::max(1, s.n_sources) != ns || std::max(1, s.n_sinks) != nk)
+            return MBC_ERR_INVALID_ARG;
+        auto c = counts_after(L->path, Aj);
+        if (c.kp != s.n_p || c.kn != s.n_n) return MBC_ERR_INVALID_ARG;  // not on the path
+        if (s.path)
+            for (int i = 0; i < Aj; ++i)
+                if (s.path[i] != L->path[i]) return MBC_ERR_INVALID_ARG;
+        part_requests(&s, dim, dim_src, nxi, parts[(size_t)j]);
+    }
+    bool forbidden = false;
+    int n_comp = 0;
+    for (auto &R : parts) {
+        forbidden = forbidden || R.forbidden;
+        n_comp += R.n_comp;
+    }
+    L->n_comp = n_comp;
+    L->parts.clear();
+    {
+        int c0 = 0;
+        for (auto &R : parts) {
+            double nrm = factorial(R.np) * factorial(R.nn);
+            L->parts.push_back({R.np, R.nn, R.A, c0, c0 + R.n_comp, nrm * nrm});
+            c0 += R.n_comp;
+            // labels padded to A entries per component
+            for (int c = 0; c < R.n_comp; ++c) {
+                for (int i = 0; i < A; ++i) {
+                    L->comp_snk.push_back(i < R.A ? R.snk[(size_t)c * R.A + i] : (int8_t)-1);
+                    L->comp_src.push_back(i < R.A ? R.src[(size_t)c * R.A + i] : (int8_t)-1);
                 }
-            for (auto &p : sets(np, dim_src))
-                for (auto &n : sets(nn, dim_src)) {
-                    std::vector<int8_t> v = p;
-                    v.insert(v.end(), n.begin(), n.end());
-                    src_comps.push_back(v);
-                }
-        }
-        for (auto &a : snk_comps)
-            for (auto &b : src_comps) {
-                L->comp_snk.insert(L->comp_snk.end(), a.begin(), a.end());
-                L->comp_src.insert(L->comp_src.end(), b.begin(), b.end());
             }
-        L->n_comp = (int32_t)(snk_comps.size() * src_comps.size());
-    } else if (spec->spin_mode == MBC_SPIN_LISTED) {
-        L->n_comp = spec->n_spin_sel;
-        L->comp_snk.assign(spec->snk_spins, spec->snk_spins + (size_t)A * spec->n_spin_sel);
-        L->comp_src.assign(spec->src_spins, spec->src_spins + (size_t)A * spec->n_spin_sel);
-    } else {  // MBC_SPIN_PROJECTED: one output per projection; labels are not single spin tuples
-        L->n_comp = spec->n_proj;
-        L->comp_snk.assign((size_t)A * spec->n_proj, (int8_t)-1);
-        L->comp_src.assign((size_t)A * spec->n_proj, (int8_t)-1);
+        }
     }
     L->fin_off.assign((size_t)L->n_comp + 1, 0);
     // a spin tuple of one species -> (set bitmask, sign of the sorting
@@ -389,21 +464,6 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
         sign = (inv & 1) ? -1 : 1;
         return true;
     };
-    // terms: (projection, sink spins, source spins, weight)
-    struct Term {
-        int proj;
-        const int8_t *snk, *src;
-        double w;
-    };
-    std::vector<Term> terms;
-    if (spec->spin_mode == MBC_SPIN_PROJECTED) {
-        for (int t = 0; t < spec->n_spin_sel; ++t)
-            terms.push_back({spec->term_proj[t], spec->snk_spins + (size_t)A * t, spec->src_spins + (size_t)A * t,
-                             spec->term_coef[t]});
-    } else {
-        for (int c = 0; c < L->n_comp; ++c)
-            terms.push_back({c, L->comp_snk.data() + (size_t)A * c, L->comp_src.data() + (size_t)A * c, 1.0});
-    }
 
     mbc_list_stats &st = L->stats;
     std::memset(&st, 0, sizeof(st));
@@ -412,19 +472,25 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
     st.block_size = L->block_size;
     st.n_comp = L->n_comp;
     st.norm = L->norm;
+    st.n_parts = n_specs;
     for (int m = 1; m <= A; ++m) {
         auto c = counts_after(L->path, m);
         st.stage_bound[m - 1] = p_bound(dim, c.kp, c.kn, nxi);
         if (m < A) st.q_bound[m - 1] = q_bound(dim, c.kp, c.kn, L->path[m], nxi);
     }
     if (forbidden) {
+        if (n_specs > 1) return MBC_ERR_INVALID_ARG;  // a combined path through a forbidden nucleus
         L->pauli_forbidden = true;
         return MBC_ERR_PAULI_FORBIDDEN;
     }
+    std::vector<bool> stage_wanted((size_t)A + 1, false);
+    for (auto &R : parts) stage_wanted[(size_t)R.A] = true;
 
-    // ---- L^(A) by the bullet recursion (eq. recr_L) -------------------------
+    // ---- L^(m) by the bullet recursion (eq. recr_L), kept where a nucleus ends
+    std::vector<std::vector<SparseEntry>> Lm((size_t)A + 1);
     std::vector<SparseEntry> gm[2] = {g_minus(D, MBC_PROTON, ns), g_minus(D, MBC_NEUTRON, ns)};
     std::vector<SparseEntry> cur = gm[L->path[0]];
+    if (stage_wanted[1]) Lm[1] = cur;
     for (int m = 1; m < A; ++m) {
         int b = L->path[m];
         auto c = counts_after(L->path, m + 1);
@@ -447,14 +513,19 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
             if (v) nxt.push_back({sp.key(i), v});
         }
         cur.swap(nxt);
+        if (stage_wanted[(size_t)m + 1]) Lm[(size_t)m + 1] = cur;
     }
-    // cur: nonzero L^(A) entries, in dense-index order of the final space
+    // Lm[m]: nonzero L^(m) entries, in dense-index order of the stage-m space
 
-    // ---- components of interest and the final needed set --------------------
-    auto cA = counts_after(L->path, A);
-    Space spA;
-    spA.init(dim, nxi, cA.kp, cA.kn, cA.ku, cA.kd);
-    std::vector<uint8_t> need_hi((size_t)spA.size(), 0);  // needed at stage A
+    // ---- components of interest and the needed set of every stage ----------
+    std::vector<Space> spaces((size_t)A + 1);
+    for (int m = 1; m <= A; ++m) {
+        auto c = counts_after(L->path, m);
+        spaces[(size_t)m].init(dim, nxi, c.kp, c.kn, c.ku, c.kd);
+    }
+    std::vector<std::vector<uint8_t>> need((size_t)A + 1);  // dense marks, allocated when first used
+    for (int m = 1; m <= A; ++m)
+        if (stage_wanted[(size_t)m]) need[(size_t)m].assign((size_t)spaces[(size_t)m].size(), 0);
     struct FinEntry {
         i64 zfull;
         double l;
@@ -462,41 +533,42 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
     // modified list of each output (Sec. 5): L_M(sink set; U, D) = sum over the
     // output's terms of weight * sign(sink order) * sign(source order) * L(source set; U, D)
     std::vector<std::vector<FinEntry>> fin((size_t)L->n_comp);
-    for (const Term &tm : terms) {
-        u32 sp_, sn_, ap_, an_;
-        int g1, g2, g3, g4;
-        if (!spin_set(tm.snk, 0, np, dim, sp_, g1) || !spin_set(tm.snk, np, nn, dim, sn_, g2) ||
-            !spin_set(tm.src, 0, np, dim_src, ap_, g3) || !spin_set(tm.src, np, nn, dim_src, an_, g4))
-            continue;  // a repeated or out-of-range spin: Pauli zero term
-        const double w = tm.w * g1 * g2 * g3 * g4;
-        for (auto &e : cur) {
-            if (e.k.dp != ap_ || e.k.dn != an_) continue;
-            Key z{sp_, sn_, e.k.u, e.k.d};
-            fin[(size_t)tm.proj].push_back({spA.index(z), w * (double)e.v});
+    for (size_t j = 0; j < parts.size(); ++j) {
+        const PartReq &R = parts[j];
+        const int c0 = L->parts[j].c0;
+        const Space &spA = spaces[(size_t)R.A];
+        for (const Term &tm : R.terms) {
+            u32 sp_, sn_, ap_, an_;
+            int g1, g2, g3, g4;
+            if (!spin_set(tm.snk, 0, R.np, dim, sp_, g1) || !spin_set(tm.snk, R.np, R.nn, dim, sn_, g2) ||
+                !spin_set(tm.src, 0, R.np, dim_src, ap_, g3) || !spin_set(tm.src, R.np, R.nn, dim_src, an_, g4))
+                continue;  // a repeated or out-of-range spin: Pauli zero term
+            const double w = tm.w * g1 * g2 * g3 * g4;
+            for (auto &e : Lm[(size_t)R.A]) {
+                if (e.k.dp != ap_ || e.k.dn != an_) continue;
+                Key z{sp_, sn_, e.k.u, e.k.d};
+                fin[(size_t)(c0 + tm.proj)].push_back({spA.index(z), w * (double)e.v});
+            }
+        }
+        for (int c = c0; c < c0 + R.n_comp; ++c) {  // add equal keys, drop exact cancellations
+            auto &v = fin[(size_t)c];
+            std::sort(v.begin(), v.end(), [](const FinEntry &a, const FinEntry &b) { return a.zfull < b.zfull; });
+            size_t w = 0;
+            for (size_t i = 0; i < v.size();) {
+                size_t k = i;
+                double sum = 0.0;
+                while (k < v.size() && v[k].zfull == v[i].zfull) sum += v[k++].l;
+                if (sum != 0.0) v[w++] = {v[i].zfull, sum};
+                i = k;
+            }
+            v.resize(w);
+            for (auto &e : v) need[(size_t)R.A][(size_t)e.zfull] = 1;
         }
     }
-    for (auto &v : fin) {  // add equal keys, drop exact cancellations
-        std::sort(v.begin(), v.end(), [](const FinEntry &a, const FinEntry &b) { return a.zfull < b.zfull; });
-        size_t w = 0;
-        for (size_t i = 0; i < v.size();) {
-            size_t j = i;
-            double sum = 0.0;
-            while (j < v.size() && v[j].zfull == v[i].zfull) sum += v[j++].l;
-            if (sum != 0.0) v[w++] = {v[i].zfull, sum};
-            i = j;
-        }
-        v.resize(w);
-        for (auto &e : v) need_hi[(size_t)e.zfull] = 1;
-    }
+    Lm.clear();
 
-    // ---- backward pruning (Sec. 3): stage m needs every x of every split ----
-    std::vector<Space> spaces((size_t)A + 1);
-    for (int m = 1; m <= A; ++m) {
-        auto c = counts_after(L->path, m);
-        spaces[(size_t)m].init(dim, nxi, c.kp, c.kn, c.ku, c.kd);
-    }
-    std::vector<std::vector<uint8_t>> need((size_t)A + 1);
-    need[(size_t)A].swap(need_hi);
+    // ---- backward pruning (Sec. 3): stage m needs every x of every split of
+    // the needed components of stage m + 1, plus its own nuclei's components
     std::vector<std::vector<i64>> members((size_t)A + 1);  // needed full indices, ascending
     std::vector<std::vector<int32_t>> compact((size_t)A + 1);
     for (int m = A; m >= 1; --m) {
@@ -506,7 +578,8 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
             if (nd[(size_t)i]) mem.push_back(i);
         if (m == 1) break;
         const Space &sz = spaces[(size_t)m], &sx = spaces[(size_t)m - 1];
-        std::vector<uint8_t> nx((size_t)sx.size(), 0);
+        auto &nx = need[(size_t)m - 1];
+        if (nx.empty()) nx.assign((size_t)sx.size(), 0);
         int b = L->path[m - 1];
 #pragma omp parallel for schedule(dynamic, 256)
         for (i64 i = 0; i < (i64)mem.size(); ++i) {
@@ -515,7 +588,7 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
                 __atomic_store_n(&nx[(size_t)sx.index(minus(z, y))], (uint8_t)1, __ATOMIC_RELAXED);
             });
         }
-        need[(size_t)m - 1].swap(nx);
+        std::vector<uint8_t>().swap(nd);
     }
     for (int m = 1; m <= A; ++m) st.stage_size[m - 1] = (i64)members[(size_t)m].size();
 
@@ -569,21 +642,20 @@ mbc_status build(const mbc_op_spec *spec, mbc_term_list *L) {
         if (bad) return MBC_ERR_INVALID_ARG;
     }
 
-    // ---- contraction list (eq. C_final) ------------------------------------
-    if (A == 1) {
-        L->final_size = L->block_size;
-    } else {
-        L->final_size = (i64)members[(size_t)A].size();
-    }
-    const auto &cmA = compact[(size_t)A];
-    for (int c = 0; c < L->n_comp; ++c) {
-        auto &v = fin[(size_t)c];
-        for (auto &e : v) {
-            i64 zi = A == 1 ? block_index(spA.key(e.zfull), L->path[0], nxi) : (i64)cmA[(size_t)e.zfull];
-            L->fin_z.push_back((uint32_t)zi);
-            L->fin_l.push_back(e.l);
+    // ---- contraction lists (eq. C_final), each at its nucleus' stage -------
+    L->final_size = A == 1 ? L->block_size : (i64)members[(size_t)A].size();
+    for (size_t j = 0; j < parts.size(); ++j) {
+        const mbc_term_list::Part &pt = L->parts[j];
+        const int Aj = pt.A;
+        const auto &cmA = compact[(size_t)Aj];
+        for (int c = pt.c0; c < pt.c1; ++c) {
+            for (auto &e : fin[(size_t)c]) {
+                i64 zi = Aj == 1 ? block_index(spaces[1].key(e.zfull), L->path[0], nxi) : (i64)cmA[(size_t)e.zfull];
+                L->fin_z.push_back((uint32_t)zi);
+                L->fin_l.push_back(e.l);
+            }
+            L->fin_off[(size_t)c + 1] = (i64)L->fin_z.size();
         }
-        L->fin_off[(size_t)c + 1] = (i64)L->fin_z.size();
     }
     st.n_l_total = (i64)L->fin_z.size();
     return MBC_OK;
@@ -606,10 +678,12 @@ const char *mbc_status_string(mbc_status s) {
     return "MBC_ERR_UNKNOWN";
 }
 
-mbc_status mbc_build_term_list(const mbc_op_spec *spec, mbc_term_list **out) {
-    if (!out) return MBC_ERR_INVALID_ARG;
-    *out = nullptr;
-    if (!spec) return MBC_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Argument checks of one spec (no allocation).
+mbc_status check_spec(const mbc_op_spec *spec) {
     const int A = spec->n_p + spec->n_n;
     if (spec->n_p < 0 || spec->n_n < 0 || A < 1 || A > MBC_MAX_A) return MBC_ERR_INVALID_ARG;
     if (spec->dirac_dim != 2 && spec->dirac_dim != 4) return MBC_ERR_INVALID_ARG;
@@ -637,11 +711,22 @@ mbc_status mbc_build_term_list(const mbc_op_spec *spec, mbc_term_list **out) {
         }
         if (cp != spec->n_p) return MBC_ERR_INVALID_ARG;
     }
+    return MBC_OK;
+}
+
+mbc_status build_checked(const mbc_op_spec *specs, int32_t n_specs, mbc_term_list **out) {
+    if (!out) return MBC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!specs || n_specs < 1 || n_specs > 64) return MBC_ERR_INVALID_ARG;
+    for (int j = 0; j < n_specs; ++j) {
+        mbc_status cs = check_spec(&specs[j]);
+        if (cs != MBC_OK) return cs;
+    }
     mbc_term_list *L = new (std::nothrow) mbc_term_list();
     if (!L) return MBC_ERR_OOM;
     mbc_status s;
     try {
-        s = build(spec, L);
+        s = build(specs, n_specs, L);
     } catch (const std::bad_alloc &) {
         s = MBC_ERR_OOM;
     } catch (...) {
@@ -653,6 +738,28 @@ mbc_status mbc_build_term_list(const mbc_op_spec *spec, mbc_term_list **out) {
         delete L;
     }
     return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+mbc_status mbc_build_term_list(const mbc_op_spec *spec, mbc_term_list **out) {
+    return build_checked(spec, 1, out);
+}
+
+mbc_status mbc_build_combined(const mbc_op_spec *specs, int32_t n_specs, mbc_term_list **out) {
+    return build_checked(specs, n_specs, out);
+}
+
+mbc_status mbc_term_list_part(const mbc_term_list *list, int32_t j, mbc_list_part *part) {
+    if (!list || !part || j < 0 || j >= (int32_t)list->parts.size()) return MBC_ERR_INVALID_ARG;
+    const auto &p = list->parts[(size_t)j];
+    part->n_p = p.n_p;
+    part->n_n = p.n_n;
+    part->c0 = p.c0;
+    part->c1 = p.c1;
+    return MBC_OK;
 }
 
 mbc_status mbc_term_list_stats(const mbc_term_list *list, mbc_list_stats *st) {

@@ -101,6 +101,9 @@ struct DeviceCache {
     int64_t *d_fin_off = nullptr;
     uint32_t *d_fin_z = nullptr;
     double *d_fin_l = nullptr;
+    uint32_t *d_fin_zs = nullptr;      // small path: region offsets of the contracted entries
+    double *d_comp_inv_norm = nullptr;
+    int32_t *d_comp_deg = nullptr;
     int64_t max_stage = 0;
 };
 
@@ -118,6 +121,9 @@ void free_cache(DeviceCache *c) {
     cudaFree(c->d_fin_off);
     cudaFree(c->d_fin_z);
     cudaFree(c->d_fin_l);
+    cudaFree(c->d_fin_zs);
+    cudaFree(c->d_comp_inv_norm);
+    cudaFree(c->d_comp_deg);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
 }
@@ -136,7 +142,9 @@ inline int n_g2(const mbc_term_list *L) { return L->dim == 4 ? 4 : 2; }
 
 // Build the small-kernel plan (shared-memory layout of one site) on the host.
 // The shared-memory kernels hold square single-source tiles only.
-bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries) {
+// part_off receives, per nucleus of the list, the region offset of the stage
+// its components are contracted from (blocks for a single baryon).
+bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries, std::vector<int> &part_off) {
     std::memset(&P, 0, sizeof(P));
     const int A = L->A;
     if (A > 16 || L->n_comp > kSmallMaxComp || L->n_comp < 1) return false;
@@ -150,7 +158,6 @@ bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries) {
     P.path0 = L->path[0];
     P.block_size = (int)L->block_size;
     P.npair = (int)binom64(L->nxi, 2);
-    P.inv_norm = 1.0 / L->norm;
     if (L->block_size >= 32768) return false;
     for (auto &s : L->steps)
         if (s.n_x >= 65536) return false;
@@ -159,18 +166,23 @@ bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries) {
     Interval blk[2];
     std::vector<Interval> stage((size_t)A + 1);
     std::vector<Interval *> order = {&Sb, &Qb};
+    // a stage where a nucleus of the list ends stays live until the contraction
+    std::vector<bool> contracted((size_t)A + 1, false);
+    for (const auto &pt : L->parts) contracted[(size_t)pt.A] = true;
+    const int last_phase = 2 + A;
     for (int b = 0; b < 2; ++b) {
         P.need_blk[b] = L->need_block[b] ? 1 : 0;
         if (!P.need_blk[b]) continue;
         int last = 2;
         for (int m = 1; m < A; ++m)
             if (L->path[m] == b) last = std::max(last, 3 + m - 1);
-        if (L->path[0] == b) last = std::max(last, A == 1 ? 2 + A : 3);
+        if (L->path[0] == b) last = std::max(last, contracted[1] ? last_phase : 3);
         blk[b] = {2, last, L->block_size, 0};
         order.push_back(&blk[b]);
     }
     for (int m = 1; m < A; ++m) {
-        stage[(size_t)m + 1] = {3 + m - 1, 3 + m, L->steps[(size_t)m - 1].n_z, 0};
+        stage[(size_t)m + 1] = {3 + m - 1, contracted[(size_t)m + 1] ? last_phase : 3 + m,
+                                L->steps[(size_t)m - 1].n_z, 0};
         order.push_back(&stage[(size_t)m + 1]);
     }
     (void)n_ph;
@@ -196,7 +208,9 @@ bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries) {
         d.op_off = op_off;
         op_off += s.n_z * s.k;
     }
-    P.fin_off_buf = A == 1 ? P.blk_off[L->path[0]] : (int)stage[(size_t)A].off;
+    part_off.clear();
+    for (const auto &pt : L->parts)
+        part_off.push_back(pt.A == 1 ? P.blk_off[L->path[0]] : (int)stage[(size_t)pt.A].off);
     int64_t kmax = 1;
     for (int c = 0; c < L->n_comp; ++c) kmax = std::max(kmax, L->fin_off[(size_t)c + 1] - L->fin_off[(size_t)c]);
     P.fin_g = pick_group(L->n_comp, kmax);
@@ -227,8 +241,29 @@ DeviceCache *get_cache(const mbc_term_list *Lc, int device, mbc_status &st) {
         return nullptr;
     }
     // small-kernel plan and packed ops
-    c->small_ok = !L->pauli_forbidden && plan_small(L, c->sp, c->site_entries);
+    std::vector<int> part_off;
+    c->small_ok = !L->pauli_forbidden && plan_small(L, c->sp, c->site_entries, part_off);
     if (c->small_ok) {
+        // contracted entries as offsets in the site region; per-component
+        // normalisation and homogeneity degree of its nucleus
+        std::vector<uint32_t> zs(L->fin_z.size());
+        std::vector<double> inv((size_t)L->n_comp);
+        std::vector<int32_t> deg((size_t)L->n_comp);
+        for (size_t j = 0; j < L->parts.size(); ++j) {
+            const auto &pt = L->parts[j];
+            for (int cc = pt.c0; cc < pt.c1; ++cc) {
+                inv[(size_t)cc] = 1.0 / pt.norm;
+                deg[(size_t)cc] = 3 * pt.A;
+                for (int64_t e = L->fin_off[(size_t)cc]; e < L->fin_off[(size_t)cc + 1]; ++e)
+                    zs[(size_t)e] = L->fin_z[(size_t)e] + (uint32_t)part_off[j];
+            }
+        }
+        if ((st = upload(&c->d_fin_zs, zs.data(), zs.size())) != MBC_OK ||
+            (st = upload(&c->d_comp_inv_norm, inv.data(), inv.size())) != MBC_OK ||
+            (st = upload(&c->d_comp_deg, deg.data(), deg.size())) != MBC_OK) {
+            free_cache(c);
+            return nullptr;
+        }
         // per step: [round j][z][sub], padded to a whole number of rounds
         std::vector<uint32_t> packed;
         for (size_t m = 0; m < L->steps.size(); ++m) {
@@ -264,8 +299,10 @@ DeviceCache *get_cache(const mbc_term_list *Lc, int device, mbc_status &st) {
         c->sp.zops = c->d_small_zops;
         c->sp.ops = c->d_small_ops;
         c->sp.fin_off = c->d_fin_off;
-        c->sp.fin_z = c->d_fin_z;
+        c->sp.fin_z = c->d_fin_zs;
         c->sp.fin_l = c->d_fin_l;
+        c->sp.comp_inv_norm = c->d_comp_inv_norm;
+        c->sp.comp_deg = c->d_comp_deg;
     }
     // large-path op arrays
     c->d_opx.assign(L->steps.size(), nullptr);
@@ -463,6 +500,26 @@ LargeSizes large_sizes(const mbc_term_list *L, const DeviceCache *c, const mbc_t
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
+// Contraction with L (eq. C_final) of every nucleus of the list that ends at
+// stage `stage` of the path, from that stage's buffer X ([component][W]);
+// deg_per_baryon: homogeneity degree of C per baryon in the scaled inputs (3
+// for propagator tiles, 1 for projected blocks).
+template <class Tr>
+mbc_status contract_parts(const mbc_term_list *L, const DeviceCache *c, int stage, const typename Tr::V *X, int W,
+                          const int32_t *sexp, int deg_per_baryon, double2 *Cb, int nsm, cudaStream_t stream) {
+    for (const auto &pt : L->parts) {
+        if (pt.A != stage || pt.c1 <= pt.c0) continue;
+        const int n = pt.c1 - pt.c0;
+        const int64_t items = (int64_t)n * (W / 32);
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
+        k_large_contract<Tr><<<(unsigned)grid, 256, 0, stream>>>(c->d_fin_off + pt.c0, c->d_fin_z, c->d_fin_l, n, W,
+                                                                 X, sexp, deg_per_baryon * pt.A, 1.0 / pt.norm,
+                                                                 Cb + (int64_t)pt.c0 * W);
+        MBC_CUDA_TRY(cudaGetLastError());
+    }
+    return MBC_OK;
+}
+
 template <class Tr>
 mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDesc &F, const MomDesc &M,
                      const mbc_tune *tune, int device, cudaStream_t stream, char *scratch, double2 *partial,
@@ -502,6 +559,8 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
                                                               L->need_block[1], fP, fN, sexp);
         MBC_CUDA_TRY(cudaGetLastError());
         const V *X = L->path[0] == MBC_PROTON ? fP : fN;
+        mbc_status cst = contract_parts<Tr>(L, c, 1, X, W, sexp, 3, Cb, nsm, stream);
+        if (cst != MBC_OK) return cst;
         for (size_t m = 0; m < L->steps.size(); ++m) {
             const Step &s = L->steps[m];
             V *Z = buf[(m + 1) & 1];
@@ -523,13 +582,7 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
             }
             MBC_CUDA_TRY(cudaGetLastError());
             X = Z;
-        }
-        {
-            int64_t items = (int64_t)L->n_comp * (W / 32);
-            int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
-            k_large_contract<Tr><<<(unsigned)grid, 256, 0, stream>>>(c->d_fin_off, c->d_fin_z, c->d_fin_l, L->n_comp,
-                                                                     W, X, sexp, 3 * L->A, 1.0 / L->norm, Cb);
-            MBC_CUDA_TRY(cudaGetLastError());
+            if ((cst = contract_parts<Tr>(L, c, (int)m + 2, X, W, sexp, 3, Cb, nsm, stream)) != MBC_OK) return cst;
         }
         {
             int64_t groups = std::min<int64_t>(W, n_items - item0) / 32;
@@ -596,6 +649,8 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         k_load_proj_blocks<Tr><<<(unsigned)((W + 7) / 8), 256, 0, stream>>>(Pf, n_items, item0, W, bs, fP, fN, sexp);
         MBC_CUDA_TRY(cudaGetLastError());
         const V *X = L->path[0] == MBC_PROTON ? fP : fN;
+        mbc_status cst = contract_parts<Tr>(L, c, 1, X, W, sexp, 1, Cb, nsm, stream);
+        if (cst != MBC_OK) return cst;
         for (size_t m = 0; m < L->steps.size(); ++m) {
             const Step &s = L->steps[m];
             V *Z = buf[(m + 1) & 1];
@@ -616,13 +671,9 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
             }
             MBC_CUDA_TRY(cudaGetLastError());
             X = Z;
+            if ((cst = contract_parts<Tr>(L, c, (int)m + 2, X, W, sexp, 1, Cb, nsm, stream)) != MBC_OK) return cst;
         }
         {
-            const int64_t items = (int64_t)L->n_comp * (W / 32);
-            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
-            k_large_contract<Tr><<<(unsigned)grid, 256, 0, stream>>>(c->d_fin_off, c->d_fin_z, c->d_fin_l, L->n_comp,
-                                                                     W, X, sexp, L->A, 1.0 / L->norm, Cb);
-            MBC_CUDA_TRY(cudaGetLastError());
             const int64_t tot = (int64_t)L->n_comp * W;
             const unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 65535));
             k_write_items<<<g2, 256, 0, stream>>>(Cb, n_items, item0, W, L->n_comp, M.n_mom, F.n_t, li, n_lists,
@@ -1065,7 +1116,8 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     size_t phase_bytes = 0, part_bytes = 0;
     int T = 0;
     if (!zero) {
-        if (!plan_small(list, hp, site_entries)) return MBC_ERR_UNSUPPORTED;  // relativistic lists: no static variant
+        std::vector<int> part_off;
+        if (!plan_small(list, hp, site_entries, part_off)) return MBC_ERR_UNSUPPORTED;  // relativistic lists: no static variant
         const int64_t per_site = site_entries * 16LL + 16LL * hp.n_comp;
         T = (int)std::min<int64_t>(32, kSmemLimit / per_site);
         if (opts->tune && opts->tune->sites_per_cta > 0) T = std::min(T, opts->tune->sites_per_cta);

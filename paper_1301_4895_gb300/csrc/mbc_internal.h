@@ -48,6 +48,15 @@ struct mbc_term_list {
     std::vector<uint32_t> fin_z;
     std::vector<double> fin_l;
     double norm = 1.0;
+    // nuclei of the list (one, or several on one path, Sec. 7): components
+    // [c0, c1) belong to the nucleus of the first A baryons of the path and
+    // are contracted at stage A with normalisation (n_P! n_N!)^2
+    struct Part {
+        int32_t n_p, n_n, A;
+        int32_t c0, c1;
+        double norm;
+    };
+    std::vector<Part> parts;
     mbc_list_stats stats{};
     // device copies, one per device ordinal, created on first use
     std::mutex dev_mu;

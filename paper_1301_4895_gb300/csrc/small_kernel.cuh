@@ -34,7 +34,7 @@ struct SmallPlan {
     int32_t A, dim, nxi, n_g2, n_comp, n_steps;
     int32_t path0;
     int32_t need_blk[2], blk_off[2];
-    int32_t s_off, q_off, fin_off_buf;  // entry offsets in the per-site region
+    int32_t s_off, q_off;               // entry offsets in the per-site region
     int32_t site_entries;               // per-site region size (entries)
     int32_t block_size, npair;
     int32_t fin_g;                      // lanes per component in the contraction
@@ -43,9 +43,10 @@ struct SmallPlan {
     const uint32_t *zops;               // the same ops, z-major
     int32_t part_off;                   // lanes-are-sites: split partials (64 entries)
     const int64_t *fin_off;             // n_comp + 1
-    const uint32_t *fin_z;
+    const uint32_t *fin_z;              // entry offsets in the per-site region
     const double *fin_l;                // integer L values
-    double inv_norm;
+    const double *comp_inv_norm;        // per component: 1 / (n_P! n_N!)^2 of its nucleus
+    const int32_t *comp_deg;            // per component: 3 A of its nucleus (homogeneity degree)
 };
 
 // A batch of term lists contracted by one persistent launch: the work items
@@ -239,14 +240,13 @@ __global__ void __launch_bounds__(1024, 1)
             // 3. recursion
             for (int m = 0; m < P.n_steps; ++m) small_step<Tr>(P, P.step[m], R, lane);
             // 4. contraction with L, FP64
-            const V *FA = R + P.fin_off_buf;
             const int g = P.fin_g, per = 32 / g, sub = lane & (g - 1);
             for (int c0 = 0; c0 < P.n_comp; c0 += per) {
                 int c = c0 + lane / g;
                 double re = 0.0, im = 0.0;
                 if (c < P.n_comp) {
                     for (int64_t e = P.fin_off[c] + sub; e < P.fin_off[c + 1]; e += g) {
-                        double2 f = Tr::to_d(FA[__ldg(P.fin_z + e)]);
+                        double2 f = Tr::to_d(R[__ldg(P.fin_z + e)]);
                         double l = __ldg(P.fin_l + e);
                         re = __fma_rn(l, f.x, re);
                         im = __fma_rn(l, f.y, im);
@@ -272,7 +272,8 @@ __global__ void __launch_bounds__(1024, 1)
                 re = __fma_rn(ph.x, cv.x, __fma_rn(-ph.y, cv.y, re));
                 im = __fma_rn(ph.x, cv.y, __fma_rn(ph.y, cv.x, im));
             }
-            partial[tile * (int64_t)(M.n_mom * P.n_comp) + o] = make_double2(re * P.inv_norm, im * P.inv_norm);
+            const double inv_norm = __ldg(P.comp_inv_norm + c);
+            partial[tile * (int64_t)(M.n_mom * P.n_comp) + o] = make_double2(re * inv_norm, im * inv_norm);
         }
     }
 }
@@ -488,17 +489,18 @@ __global__ void __launch_bounds__(1024, 1)
         //    32 sites of the tile by a fixed xor tree
         const int site = site0 + lane;
         const bool live = site < V3;
-        const int ue = -3 * P.A * sexp_s[lane];
         for (int c = warp; c < P.n_comp; c += NW) {
+            const int ue = -__ldg(P.comp_deg + c) * sexp_s[lane];
+            const double inv_norm = __ldg(P.comp_inv_norm + c);
             double re = 0.0, im = 0.0;
             for (int64_t e = P.fin_off[c]; e < P.fin_off[c + 1]; ++e) {
-                const double2 f = Tr::to_d(ROW(P.fin_off_buf + __ldg(P.fin_z + e)));
+                const double2 f = Tr::to_d(ROW(__ldg(P.fin_z + e)));
                 const double l = __ldg(P.fin_l + e);
                 re = __fma_rn(l, f.x, re);
                 im = __fma_rn(l, f.y, im);
             }
-            re = live ? scalbn(re * P.inv_norm, ue) : 0.0;
-            im = live ? scalbn(im * P.inv_norm, ue) : 0.0;
+            re = live ? scalbn(re * inv_norm, ue) : 0.0;
+            im = live ? scalbn(im * inv_norm, ue) : 0.0;
             for (int q = 0; q < M.n_mom; ++q) {
                 const double2 ph = live ? __ldg(phase + (int64_t)site * M.n_mom + q) : make_double2(0, 0);
                 double pr = __fma_rn(ph.x, re, -ph.y * im), pi = __fma_rn(ph.x, im, ph.y * re);

@@ -192,3 +192,73 @@ def test_two_source_lists_agree_with_oracle():
         plan = recursion.Plan(n_p, n_n, 2, requests=[(sp, sp)], G=Gt)
         tot, per, stages = plan.ops()
         assert (st["n_ops_total"], st["n_ops"], st["stage_size"]) == (tot, per, stages)
+
+
+def _prefix(path, A):
+    return list(path[:A])
+
+
+@pytest.mark.parametrize("D,path,nuclei", [
+    (2, [0, 0, 1, 1], [(2, 1, None), (2, 2, None)]),
+    (2, [0, 1, 0, 1], [(1, 0, None), (1, 1, None), (2, 1, None), (2, 2, None)]),
+    (4, [1, 1, 0, 0], [(0, 1, None), (0, 2, None), (2, 2, [((0, 1, 0, 1), (0, 1, 0, 1))])]),
+    (4, [1, 0, 1], [(1, 1, [((0, 1), (2, 3)), ((1, 1), (1, 1))]), (1, 2, [((2, 0, 1), (0, 1, 2)), ((0, 1, 3), (1, 0, 2))])]),
+])
+def test_combined_path_lists_agree_with_oracle_pruning(D, path, nuclei):
+    """Sec. 7: nuclei on one path share its stages. Every stage of the
+    combined list holds exactly the union of the components each nucleus
+    needs on its own (the oracle's independent pruning along the same path
+    prefix), each step costs splits x stage size, and the outputs are the
+    nuclei's components in order, labels padded with -1."""
+    specs = [dict(n_p=a, n_n=b, spins=sp) for a, b, sp in nuclei]
+    tl = mbc.build_combined(specs, D, path=path)
+    st = tl.stats()
+    A = len(path)
+    assert st["path"] == path and st["n_parts"] == len(nuclei)
+    plans = []
+    c0 = 0
+    comps = tl.components()
+    for j, (a, b, sp) in enumerate(nuclei):
+        Aj = a + b
+        plan = recursion.Plan(a, b, D, requests=sp, path=_prefix(path, Aj))
+        plans.append((Aj, plan))
+        part = tl.parts()[j]
+        assert (part["n_p"], part["n_n"], part["c0"]) == (a, b, c0)
+        assert part["c1"] - part["c0"] == len(plan.requests)
+        nl = dict(zip(plan.requests, plan.n_l()))
+        pad = (-1,) * (A - Aj)
+        mine = comps[part["c0"]:part["c1"]]
+        assert all(snk[Aj:] == pad and src[Aj:] == pad for snk, src in mine)
+        assert sorted((snk[:Aj], src[:Aj]) for snk, src in mine) == sorted(plan.requests)
+        for c, (snk, src) in zip(range(part["c0"], part["c1"]), mine):
+            assert tl.n_l(c) == nl[(snk[:Aj], src[:Aj])]
+        c0 = part["c1"]
+    for m in range(2, A + 1):
+        union = set()
+        for Aj, plan in plans:
+            if Aj >= m:
+                union |= set(plan.stage_keys(m).tolist())
+        assert st["stage_size"][m - 1] == len(union), m
+        assert st["n_ops"][m - 2] == st["ops_per_z"][m - 2] * st["stage_size"][m - 1]
+    separate = sum(plan.ops()[0] for _, plan in plans)
+    assert max(plan.ops()[0] for _, plan in plans) <= st["n_ops_total"] <= separate
+
+
+def test_combined_free_rider():
+    """Nonrelativistic 4He on the path P, P, N, N needs every stage-3
+    component, so 3He (all components) costs nothing extra."""
+    he4 = mbc.build_term_list(2, 2, 2, path=[0, 0, 1, 1]).stats()["n_ops_total"]
+    both = mbc.build_combined([dict(n_p=2, n_n=1), dict(n_p=2, n_n=2)], 2, path=[0, 0, 1, 1])
+    assert both.stats()["n_ops_total"] == he4 == 10980
+    assert both.stats()["n_comp"] == 4 + 1
+
+
+def test_combined_rejects_nuclei_off_the_path():
+    with pytest.raises(mbc.MbcError):
+        mbc.build_combined([dict(n_p=0, n_n=2), dict(n_p=2, n_n=2)], 2, path=[0, 0, 1, 1])
+    with pytest.raises(mbc.MbcError):  # Pauli-forbidden largest nucleus
+        mbc.build_combined([dict(n_p=1, n_n=0), dict(n_p=3, n_n=0)], 2)
+    with pytest.raises(ValueError):
+        mbc.build_combined([], 2)
+    h = ctypes.c_void_p()
+    assert mbc.load().mbc_build_combined(None, 0, ctypes.byref(h)) == 1 and not h.value

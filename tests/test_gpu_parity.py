@@ -439,6 +439,42 @@ def test_two_quark_sources_larger_slab(mbc):
         assert e <= TOL[p], (p, e)
 
 
+@pytest.mark.parametrize("D,path,nuclei,regime,sink", [
+    (2, [0, 0, 1, 1], [(2, 1, None), (2, 2, None)], 0, 0),
+    (2, [0, 0, 1, 1], [(2, 1, None), (2, 2, None)], 2, 0),
+    (2, [0, 1, 0, 1], [(1, 0, None), (1, 1, None), (2, 1, None), (2, 2, None)], 0, 0),
+    (2, [0, 1, 0, 1], [(1, 0, None), (1, 1, None), (2, 1, None), (2, 2, None)], 0, 1),
+    (4, [1, 1, 0, 0], [(0, 1, None), (0, 2, None), (2, 2, [((0, 1, 0, 1), (0, 1, 0, 1))])], 0, 0),
+])
+def test_combined_path_lists(mbc, D, path, nuclei, regime, sink):
+    """Several nuclei on one recursion path in one list (Sec. 7): each
+    nucleus is contracted at its own stage; every output equals the oracle's
+    correlator of that nucleus alone (both regimes, point sinks and
+    momentum-projected blocks)."""
+    from oracle import projection
+    dims = (2, 3, 5)
+    field = synth.field(26, 1, 2, dims, 0.4)
+    moms = ((0, 0, 0), (0, 2, 1))
+    tl = mbc.build_combined([dict(n_p=a, n_n=b, spins=sp) for a, b, sp in nuclei], D, path=path)
+    comps = tl.components()
+    outs = {p: run(mbc, field, [tl], p, moms=moms, sink=sink, tune={"regime": regime}) for p in (0, 1)}
+    for part in tl.parts():
+        a, b = part["n_p"], part["n_n"]
+        mine = [(snk[:a + b], src[:a + b]) for snk, src in comps[part["c0"]:part["c1"]]]
+        plan = oracle_plan(a, b, D, mine)
+        for t in range(2):
+            if sink == 0:
+                ref, scale = oracle_slab(plan, field[0, t], dims, list(moms))
+                scale = scale[None, :]
+            else:
+                ref, scale = projection.projected_correlators(plan, field[0, t], dims, moms)
+            for p in (0, 1):
+                got = outs[p][0, 0, t, :, part["c0"]:part["c1"]]
+                e = float(np.max(np.abs(got - ref) / scale))
+                record(f"({a},{b}) D={D} on a combined path", p, e)
+                assert e <= TOL[p], (a, b, t, p, e)
+
+
 def test_zz_accuracy_report(mbc, capsys):
     """Prints the worst |dC| / sum|terms| of the parity tests above (run with
     -s to see it); fails if any exceeded its bound."""
