@@ -85,9 +85,9 @@ enum { MBC_PROTON = 0, MBC_NEUTRON = 1 };
  *                3 dirac_dim N_s <= 12 (one source relativistic, up to two
  *                nonrelativistic); larger lists are built for their counts.
  *   n_sinks      number of sink functions N_k for the sink baryon indices
- *                psi = N_k alpha + k (Sec. 6); 0 or 1 = one sink. Term lists
- *                with N_k > 1 are built (operation counts, Tables 3 and 6);
- *                contraction kernels are built for N_k = 1.
+ *                psi = N_k alpha + k (Sec. 6); 0 or 1 = one sink. N_k > 1
+ *                lists contract with momentum-projected blocks, one momentum
+ *                per sink function (mbc_contract_opts.sink_mode).
  *   spin_mode    MBC_SPIN_ALL: every independent component, i.e. every pair
  *                (sink spin set, source spin set) (Sec. 4); the output
  *                component index is snk_index * n_sets + src_index with the
@@ -271,7 +271,15 @@ typedef struct {
  *                the momentum first, f_B = sum_x exp(-2 pi i n.x / L) f_B(x)
  *                (Sec. 2 sink function s(x)), and the recursion runs once
  *                per (configuration, time slice, momentum) on those blocks.
- *                The block sums are FP64 in both precisions.
+ *                The block sums are FP64 in both precisions. Lists built
+ *                with n_sinks = N_k > 1 (Sec. 6 sink functions s_1 .. s_N_k)
+ *                take the momenta in groups of N_k (n_mom a multiple of N_k,
+ *                all lists of the call with the same N_k): sink function k
+ *                of group g is momentum g N_k + k, the block of sink index
+ *                psi = N_k alpha + k is the spin-alpha block projected with
+ *                it, and the recursion runs once per (configuration, time
+ *                slice, group). MBC_SINK_POINT takes N_k = 1 only
+ *                (MBC_ERR_UNSUPPORTED).
  */
 typedef struct {
     int32_t precision;
@@ -284,7 +292,7 @@ typedef struct {
 
 /*
  * Evaluate the correlators of n_lists nuclei.
- * out: complex128 [n_cfg][n_lists][t1 - t0][n_mom][n_comp_max], where
+ * out: complex128 [n_cfg][n_lists][t1 - t0][n_mom / N_k][n_comp_max], where
  * n_comp_max is the largest n_comp of the lists; unused tail entries are
  * zero. With memory == MBC_MEM_DEVICE the call is asynchronous on stream
  * (a cudaStream_t; NULL = legacy default stream) and out is written in a

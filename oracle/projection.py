@@ -11,6 +11,11 @@ O3, the phase-weighted sum over sites is a plain numpy sum, and O3 runs the
 recursion and contraction on the summed blocks. The error scale sums the
 per-site block magnitudes (|s(x)| = 1) and runs the magnitude recursion on
 them.
+
+Several sink functions (Sec. 6): with N_k of them the sink baryon index is
+psi = N_k alpha + k, and the block of sink index psi is the block of spin alpha
+summed with sink function k. Here sink function k of a group is the k-th of
+N_k consecutive momenta, so a group of momenta gives one set of blocks.
 """
 from __future__ import annotations
 
@@ -19,9 +24,12 @@ import numpy as np
 from .site_sum import phases
 
 
-def projected_correlators(plan, slab, dims_zyx, moms, chunk: int = 256):
+def projected_correlators(plan, slab, dims_zyx, moms, chunk: int = 256, n_sinks: int = 1, dirac_dim: int = 0):
     """C(t, n) of one slab with momentum-projected blocks.
-    slab: (Lz, Ly, Lx, 12, 12); returns (C (n_mom, n_req), scale (n_mom, n_req))."""
+    slab: (Lz, Ly, Lx, 12, 12); returns (C (n_groups, n_req), scale (n_groups,
+    n_req)) with n_groups = n_mom / n_sinks (one group = n_sinks momenta, one
+    per sink function; dirac_dim, needed when n_sinks > 1, is the number of
+    spin values alpha of the single-sink blocks)."""
     import synth
     S = np.asarray(slab, dtype=np.complex128).reshape(-1, 12, 12)
     coords = synth.site_coords(dims_zyx)
@@ -39,4 +47,17 @@ def projected_correlators(plan, slab, dims_zyx, moms, chunk: int = 256):
         Pn += np.tensordot(w, fn, axes=(1, 0))
         Mp += mp.sum(axis=0)[None]
         Mn += mn.sum(axis=0)[None]
+    if n_sinks > 1:
+        if len(moms) % n_sinks or dirac_dim * n_sinks > 4:
+            raise ValueError("momenta must come in whole groups; dirac_dim * n_sinks <= 4")
+        n_groups = len(moms) // n_sinks
+        grouped = []
+        for X in (Pp, Pn, Mp, Mn):
+            Y = np.zeros((n_groups,) + X.shape[1:], dtype=X.dtype)
+            for g in range(n_groups):
+                for k in range(n_sinks):
+                    for a in range(dirac_dim):
+                        Y[g, n_sinks * a + k] = X[g * n_sinks + k, a]
+            grouped.append(Y)
+        Pp, Pn, Mp, Mn = grouped
     return plan.evaluate_blocks(Pp, Pn, Mp, Mn)

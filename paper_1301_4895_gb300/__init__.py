@@ -299,8 +299,9 @@ def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0
     field: torch tensor (device memory) or numpy array (host memory) of shape
     (n_cfg, nt, Lz, Ly, Lx, 12, 12), or (n_cfg, nt, Lz, Ly, Lx, n_src, 12, 12)
     for lists built with n_sources = n_src (Sec. 6), complex128 or complex64,
-    contiguous. Returns out: complex128 (n_cfg, n_lists, t1 - t0, n_mom, n_comp_max) on the
-    same side as the field.
+    contiguous. Returns out: complex128 (n_cfg, n_lists, t1 - t0, n_mom / n_sinks,
+    n_comp_max) on the same side as the field; lists with n_sinks > 1 need
+    sink=SINK_BLOCK_MOMENTUM and take the momenta in groups of n_sinks.
     """
     lib = load()
     lists = list(lists)
@@ -325,7 +326,8 @@ def contract(field, lists, precision: int = FP64, moms=((0, 0, 0),), t0: int = 0
     t1e = nt if t1 == 0 else t1
     moms = np.ascontiguousarray(np.array(moms, dtype=np.int32).reshape(-1, 3))
     comp_max = max(1, max(tl.stats()["n_comp"] for tl in lists))
-    oshape = (n_cfg, len(lists), t1e - t0, moms.shape[0], comp_max)
+    n_k = max(1, int(lists[0].spec.get("n_sinks", 1) or 1)) if lists else 1
+    oshape = (n_cfg, len(lists), t1e - t0, moms.shape[0] // n_k, comp_max)
     if out is None:
         if is_np:
             out = np.zeros(oshape, dtype=np.complex128)

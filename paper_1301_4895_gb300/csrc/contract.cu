@@ -594,13 +594,16 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
 }
 
 // Momentum-projected blocks: per-site blocks summed over sites with the phase
-// (FP64), then the recursion once per (slab, momentum) item on the wave kernels.
+// (FP64), then the recursion once per (slab, momentum group) item on the wave
+// kernels; a group holds the n_sinks momenta of the list's sink functions.
 template <class Tr>
 mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const FieldDesc &F, const MomDesc &M,
                          const mbc_tune *tune, int device, cudaStream_t stream, char *scratch, const double2 *phase,
                          int li, int n_lists, int comp_max, double2 *out, int64_t n_slabs, const LargeSizes &ls) {
     using V = typename Tr::V;
-    const int nxi = L->nxi, nrow = 3 * L->dim, bs = (int)L->block_size;
+    const int nxi = L->nxi, nrow = 3 * L->dim, n_k = L->n_sinks;
+    const int bs = (int)(L->block_size / n_k);  // one sink function: dirac_dim * C(nxi, 2) * nxi
+    const int n_groups = M.n_mom / n_k;
     const int v3 = F.lx * F.ly * F.lz;
     const int tps = (v3 + 15) / 16;
     const int64_t n_tiles = n_slabs * tps;
@@ -644,9 +647,11 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         MBC_CUDA_TRY(cudaGetLastError());
     }
     // 2. recursion and contraction per item, a wave of W items at a time
-    const int64_t n_items = n_slabs * M.n_mom;
+    const int64_t n_items = n_slabs * n_groups;
+    const int per_spin = (int)(binom64(nxi, 2) * nxi);
     for (int64_t item0 = 0; item0 < n_items; item0 += W) {
-        k_load_proj_blocks<Tr><<<(unsigned)((W + 7) / 8), 256, 0, stream>>>(Pf, n_items, item0, W, bs, fP, fN, sexp);
+        k_load_proj_blocks<Tr><<<(unsigned)((W + 7) / 8), 256, 0, stream>>>(Pf, n_items, item0, W, bs, per_spin, n_k,
+                                                                            M.n_mom, fP, fN, sexp);
         MBC_CUDA_TRY(cudaGetLastError());
         const V *X = L->path[0] == MBC_PROTON ? fP : fN;
         mbc_status cst = contract_parts<Tr>(L, c, 1, X, W, sexp, 1, Cb, nsm, stream);
@@ -676,7 +681,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         {
             const int64_t tot = (int64_t)L->n_comp * W;
             const unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 65535));
-            k_write_items<<<g2, 256, 0, stream>>>(Cb, n_items, item0, W, L->n_comp, M.n_mom, F.n_t, li, n_lists,
+            k_write_items<<<g2, 256, 0, stream>>>(Cb, n_items, item0, W, L->n_comp, n_groups, F.n_t, li, n_lists,
                                                   comp_max, out);
             MBC_CUDA_TRY(cudaGetLastError());
         }
@@ -686,7 +691,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
 
 size_t projected_bytes(const mbc_term_list *L, const MomDesc &M, int v3, int64_t n_slabs, const LargeSizes &ls) {
     const int tps = (v3 + 15) / 16;
-    const int64_t n_out = 2 * L->block_size;
+    const int64_t n_out = 2 * (L->block_size / L->n_sinks);
     return align256((size_t)n_slabs * tps * M.n_mom * n_out * sizeof(double2)) +
            align256((size_t)n_slabs * M.n_mom * n_out * sizeof(double2)) + 2 * align256(ls.blk_bytes) +
            2 * align256(ls.stage_bytes) + align256(ls.c_bytes) + align256(ls.sexp_bytes);
@@ -718,12 +723,19 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     if (t0 < 0 || t1 > props->nt || t1 <= t0) return MBC_ERR_INVALID_ARG;
     const int n_src = props->n_src == 0 ? 1 : props->n_src;
     if (n_src < 1 || n_src > 4) return MBC_ERR_INVALID_ARG;
+    if (opts->sink_mode != MBC_SINK_POINT && opts->sink_mode != MBC_SINK_BLOCK_MOMENTUM) return MBC_ERR_INVALID_ARG;
+    // sink functions per list: 1 for point sinks; with projected blocks every
+    // list has the same n_k and the momenta come in groups of n_k (Sec. 6)
+    const int n_k = lists[0] ? std::max(1, (int)lists[0]->n_sinks) : 1;
     for (int i = 0; i < n_lists; ++i) {
         if (!lists[i]) return MBC_ERR_INVALID_ARG;
         if (lists[i]->n_sources != n_src) return MBC_ERR_INVALID_ARG;  // list and field disagree
-        // one sink function; source tiles up to 12 columns (c_pair tables)
-        if (lists[i]->n_sinks != 1 || lists[i]->nxi > 12) return MBC_ERR_UNSUPPORTED;
+        if (lists[i]->nxi > 12) return MBC_ERR_UNSUPPORTED;  // source tiles up to 12 columns (c_pair tables)
+        if (lists[i]->n_sinks != n_k) return MBC_ERR_INVALID_ARG;
     }
+    if (n_k > 1 && opts->sink_mode == MBC_SINK_POINT) return MBC_ERR_UNSUPPORTED;  // one sink point per site
+    if (opts->n_mom % n_k != 0) return MBC_ERR_INVALID_ARG;
+    const int n_out_mom = opts->n_mom / n_k;  // output momentum (group) index
     const int64_t v3 = (int64_t)props->lx * props->ly * props->lz;
     if (v3 > (1LL << 30)) return MBC_ERR_INVALID_ARG;
     const int64_t site_elems = 144LL * n_src;
@@ -738,7 +750,7 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     int comp_max = 1;
     for (int i = 0; i < n_lists; ++i) comp_max = std::max(comp_max, (int)lists[i]->n_comp);
     const int n_t = t1 - t0;
-    const size_t out_bytes = (size_t)props->n_cfg * n_lists * n_t * opts->n_mom * comp_max * sizeof(double2);
+    const size_t out_bytes = (size_t)props->n_cfg * n_lists * n_t * n_out_mom * comp_max * sizeof(double2);
 
     // host-memory mode: stage the evaluated slices on the device
     const void *field = props->s_u;
@@ -793,10 +805,9 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     const int64_t n_slabs = (int64_t)props->n_cfg * n_t;
     const bool mixed = opts->precision == MBC_MIXED;
 
-    if (opts->sink_mode != MBC_SINK_POINT && opts->sink_mode != MBC_SINK_BLOCK_MOMENTUM) return MBC_ERR_INVALID_ARG;
     if (opts->sink_mode == MBC_SINK_BLOCK_MOMENTUM) {
         // every baryon's block projected to the momentum, one recursion per item
-        const int64_t n_items_p = n_slabs * M.n_mom;
+        const int64_t n_items_p = n_slabs * n_out_mom;
         std::vector<DeviceCache *> cs((size_t)n_lists, nullptr);
         std::vector<LargeSizes> lsz((size_t)n_lists);
         size_t need = 0;

@@ -91,18 +91,28 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
     }
 }
 
-// One warp per item (slab, momentum) of the wave: summed blocks -> wave layout.
+// One warp per item of the wave: summed blocks -> wave layout. An item is
+// (slab, group of n_k momenta); with n_k sink functions (Sec. 6) the sink
+// index of the item's block is psi = n_k * alpha + k, and block entry
+// (psi; pair, single) is entry (alpha; pair, single) of the block projected
+// with momentum k of the group. Pf: [slab][momentum][P block, N block] with
+// bs_site entries per block (one sink function).
 template <class Tr>
 __global__ void __launch_bounds__(256) k_load_proj_blocks(const double2 *__restrict__ Pf, int64_t n_items,
-                                                          int64_t item0, int W, int block_size,
-                                                          typename Tr::V *__restrict__ fP,
+                                                          int64_t item0, int W, int bs_site, int per_spin, int n_k,
+                                                          int n_mom, typename Tr::V *__restrict__ fP,
                                                           typename Tr::V *__restrict__ fN, int32_t *__restrict__ sexp) {
     const int lane = threadIdx.x & 31;
     const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (col >= W) return;
     const int64_t item = item0 + col;
     const bool live = item < n_items;
-    const double2 *src = Pf + (live ? item : 0) * 2 * (int64_t)block_size;
+    const int n_groups = n_mom / n_k;
+    const int64_t it = live ? item : 0;
+    const int64_t slab = it / n_groups;
+    const int q0 = (int)(it % n_groups) * n_k;
+    const double2 *src = Pf + (slab * n_mom + q0) * 2 * (int64_t)bs_site;  // n_k consecutive momenta
+    const int block_size = bs_site * n_k;
     int se = 0;
     if (sizeof(typename Tr::V) == sizeof(float2)) {
         double amax = 0.0;
@@ -114,8 +124,11 @@ __global__ void __launch_bounds__(256) k_load_proj_blocks(const double2 *__restr
         se = amax > 0.0 ? -ilogb(amax) : 0;
     }
     for (int e = lane; e < block_size; e += 32) {
-        const double2 p = live ? src[e] : make_double2(0, 0);
-        const double2 n = live ? src[block_size + e] : make_double2(0, 0);
+        const int psi = e / per_spin, r = e % per_spin;
+        const int k = psi % n_k, alpha = psi / n_k;
+        const double2 *s_k = src + (int64_t)k * 2 * bs_site + alpha * per_spin + r;
+        const double2 p = live ? s_k[0] : make_double2(0, 0);
+        const double2 n = live ? s_k[bs_site] : make_double2(0, 0);
         fP[(int64_t)e * W + col] = Tr::from_d(make_double2(scalbn(p.x, se), scalbn(p.y, se)));
         fN[(int64_t)e * W + col] = Tr::from_d(make_double2(scalbn(n.x, se), scalbn(n.y, se)));
     }
@@ -123,6 +136,7 @@ __global__ void __launch_bounds__(256) k_load_proj_blocks(const double2 *__restr
 }
 
 // out[cfg][list][t - t0][mom][comp_stride] = C[comp][item] for the wave's items
+// (n_mom: items per slab)
 __global__ void k_write_items(const double2 *__restrict__ C, int64_t n_items, int64_t item0, int W, int n_comp,
                               int n_mom, int n_t, int list_idx, int n_lists, int comp_stride, double2 *out) {
     const int64_t total = (int64_t)n_comp * W;

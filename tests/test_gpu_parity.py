@@ -439,6 +439,38 @@ def test_two_quark_sources_larger_slab(mbc):
         assert e <= TOL[p], (p, e)
 
 
+@pytest.mark.parametrize("n_p,n_n,n_src,spins", [
+    (1, 1, 1, [((0, 3), (0, 1)), ((1, 2), (1, 0)), ((0, 1), (1, 1))]),
+    (2, 1, 1, [((0, 3, 1), (0, 1, 0)), ((0, 1, 2), (0, 1, 1))]),
+    (1, 1, 2, [((0, 3), (0, 3)), ((1, 2), (2, 1))]),
+    (2, 2, 2, [((0, 2, 0, 2), (0, 2, 0, 2)), ((0, 1, 2, 3), (0, 1, 2, 3)), ((1, 3, 0, 2), (0, 3, 1, 2))]),
+])
+def test_two_sink_functions(mbc, n_p, n_n, n_src, spins):
+    """N_k = 2 sink functions (Sec. 6), one per momentum of a group, sink
+    index psi = 2 alpha + k, with one or two quark sources (the setting of
+    Table 6), against the oracle's grouped projected blocks."""
+    from oracle import gamma, projection, recursion
+    dims = (2, 3, 4)
+    field = synth.field(27, 1, 2, dims, 0.4, n_src=n_src if n_src > 1 else 0)
+    moms = ((0, 0, 0), (1, 0, 0), (0, 1, 2), (0, 0, 1))
+    tl = mbc.build_term_list(n_p, n_n, 2, spins=spins, n_sources=n_src, n_sinks=2)
+    comps = tl.components()
+    if n_src == 1:
+        plan = recursion.Plan(n_p, n_n, 2, requests=comps)
+    else:
+        plan = recursion.Plan(n_p, n_n, 2, requests=comps, G=gamma.g_tensor_sources(2, 2), G_sink=gamma.g_tensor(2))
+    outs = {p: run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM) for p in (0, 1)}
+    for t in range(2):
+        S = field[0, t] if n_src == 1 else recursion.source_columns(field[0, t], 2)
+        ref, scale = projection.projected_correlators(plan, S, dims, moms, n_sinks=2, dirac_dim=2)
+        for p in (0, 1):
+            got = outs[p][0, 0, t, :, : len(comps)]
+            assert got.shape == ref.shape
+            e = float(np.max(np.abs(got - ref) / scale))
+            record(f"({n_p},{n_n}) D=2 {n_src} source(s), 2 sinks", p, e)
+            assert e <= TOL[p], (t, p, e)
+
+
 @pytest.mark.parametrize("D,path,nuclei,regime,sink", [
     (2, [0, 0, 1, 1], [(2, 1, None), (2, 2, None)], 0, 0),
     (2, [0, 0, 1, 1], [(2, 1, None), (2, 2, None)], 2, 0),

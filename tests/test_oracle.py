@@ -385,3 +385,43 @@ def test_two_source_single_source_limits(rng):
     Cz, _ = plan.evaluate(recursion.source_columns(Z, 2)[None])
     assert Cz[0, 1] == 0 and Cz[0, 2] == 0 and Cz[0, 3] == 0
     assert abs(Cz[0, 0] - C[0, 0]) <= 1e-13 * sc[0, 0]
+
+
+# ---- several sink functions (Sec. 6), momentum-projected blocks -------------------
+
+def test_two_sink_functions_pins(rng):
+    """N_k = 2 sink functions, one per momentum of a group: sink index
+    psi = 2 alpha + k. (a) One baryon: C(psi; alpha') is the single-sink
+    correlator at momentum k. (b) Equal momenta in a group make the two
+    sink functions identical, so two protons in the same spin with
+    different k vanish (Pauli). (c) Shifting the field by one site along x
+    multiplies a component by exp(-2 pi i sum_b n_{k(b)} / L_x)."""
+    from oracle import projection
+    dims = (1, 2, 4)  # (Lz, Ly, Lx)
+    field = rand_prop(rng, 8).reshape(dims + (12, 12))
+    moms = [(1, 0, 0), (0, 1, 0), (2, 0, 0), (1, 1, 0)]
+    # (a)
+    reqs2 = [((psi,), (a,)) for psi in range(4) for a in range(2)]
+    p2 = recursion.Plan(1, 0, 2, requests=reqs2)
+    C2, _ = projection.projected_correlators(p2, field, dims, moms, n_sinks=2, dirac_dim=2)
+    p1 = recursion.Plan(1, 0, 2, requests=[((al,), (a,)) for al in range(2) for a in range(2)])
+    C1, _ = projection.projected_correlators(p1, field, dims, moms)
+    for g in range(2):
+        for r, ((psi,), (a,)) in enumerate(reqs2):
+            al, k = divmod(psi, 2)
+            assert abs(C2[g, r] - C1[2 * g + k, 2 * al + a]) <= 1e-13 * abs(C1[2 * g + k]).max()
+    # (b)
+    reqs = [((0, 1, 0), (0, 1, 0)), ((0, 2, 1), (0, 1, 1))]
+    pl = recursion.Plan(2, 1, 2, requests=reqs)
+    same = [(1, 0, 0), (1, 0, 0)]
+    C, sc = projection.projected_correlators(pl, field, dims, same, n_sinks=2, dirac_dim=2)
+    assert abs(C[0, 0]) <= 1e-13 * sc[0, 0]
+    assert abs(C[0, 1]) > 1e-6 * sc[0, 1]
+    # (c): psi = (0, 3 | 1): momenta of k = 0, 1, 1 -> n_x total 1 + 0 + 0
+    pair = [(1, 0, 0), (0, 1, 0)]
+    C, sc = projection.projected_correlators(pl, field, dims, pair, n_sinks=2, dirac_dim=2)
+    moved = np.roll(field, 1, axis=2)
+    Cm, _ = projection.projected_correlators(pl, moved, dims, pair, n_sinks=2, dirac_dim=2)
+    nx = [sum(pair[psi % 2][0] for psi in snk) for snk, _ in reqs]
+    for r in range(2):
+        assert abs(Cm[0, r] - C[0, r] * np.exp(-2j * np.pi * nx[r] / 4)) <= 1e-13 * sc[0, r]
