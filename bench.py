@@ -44,7 +44,16 @@ WORKLOADS = {
     "batched": ("batched: pn, 3He, 4He nonrel + 4He rel (0,1,0,1), 24^3x48 per configuration, complex64, seed 3",
                 [(1, 1, 2, None), (2, 1, 2, None), (2, 2, 2, None), (2, 2, 4, [((0, 1, 0, 1), (0, 1, 0, 1))])],
                 (24, 24, 24), 48, 3, 0.4, "c64"),
+    "he4two": ("4He nonrelativistic, two quark sources, two sink functions (momenta (0,0,0) and (1,0,0)), "
+               "36 sink components x source spins (0,2,0,2), 16^3x32, complex128, seed 5",
+               [(2, 2, 2, [(p + q, (0, 2, 0, 2)) for p in ((0, 1), (0, 2), (1, 2), (0, 3), (1, 3), (2, 3))
+                           for q in ((0, 1), (0, 2), (1, 2), (0, 3), (1, 3), (2, 3))])],
+               (16, 16, 16), 32, 5, 0.4, "c128"),
 }
+# workloads beyond one source and point sinks: quark sources, sink functions,
+# sink mode and the number of momenta per (configuration, time slice)
+WORKLOAD_OPTS = {"he4two": {"n_src": 2, "n_sinks": 2, "sink": "block", "moms": 2}}
+MOMENTA = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
 
 
 def parse():
@@ -58,6 +67,11 @@ def parse():
     ap.add_argument("--cfgs", type=int, default=1, help="configurations per rank")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    ap.add_argument("--sink", default="", choices=["", "point", "block"],
+                    help="point sinks (site correlators summed with the phase) or momentum-projected blocks")
+    ap.add_argument("--moms", type=int, default=0, help="momenta per (configuration, time slice)")
+    ap.add_argument("--list-free", action="store_true",
+                    help="term lists without operation arrays (splits regenerated on the GPU)")
     ap.add_argument("--combined", action="store_true",
                     help="contract the workload's nuclei with one list on a shared recursion path (Sec. 7)")
     ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner first")
@@ -181,11 +195,11 @@ def measured_peaks():
     return {}
 
 
-def make_field(wl, cfgs, nt):
+def make_field(wl, cfgs, nt, n_src=1):
     import synth
     _, _, dims, _, seed, lam, dt = wl
     return synth.field(seed, max(cfgs) + 1, nt, dims, lam, dtype=np.complex64 if dt == "c64" else np.complex128,
-                       cfgs=list(cfgs))
+                       cfgs=list(cfgs), n_src=n_src if n_src > 1 else 0)
 
 
 def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0):
@@ -227,41 +241,104 @@ def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0):
                       f"recursion in C with OpenMP, {t_tot:.1f} s"}
 
 
+def oracle_plans(lists_spec, n_src):
+    """O3 plans of the workload's nuclei; several quark sources take G~ at
+    the source and G for the blocks (Sec. 6)."""
+    from oracle import gamma, recursion
+    plans = []
+    for (n_p, n_n, D, _), comps in lists_spec:
+        if n_src > 1:
+            plans.append(recursion.Plan(n_p, n_n, D, requests=comps, G=gamma.g_tensor_sources(D, n_src),
+                                        G_sink=gamma.g_tensor(D)))
+        else:
+            plans.append(recursion.Plan(n_p, n_n, D, requests=comps))
+    return plans
+
+
+def cpu_baseline_projected(wl, lists_spec, nt_used, moms, n_src, n_sinks, budget_s=15.0):
+    """The oracle with momentum-projected blocks (oracle/projection.py) on
+    whole slabs of the workload until the budget is spent."""
+    from oracle import projection, recursion
+    import synth
+    _, nuclei, dims, nt, seed, lam, dt = wl
+    plans = oracle_plans(lists_spec, n_src)
+    done, t_tot, slabs = 0, 0.0, 0
+    for t in range(nt_used):
+        if n_src > 1:
+            S = recursion.source_columns(synth.slab_sources(seed, 0, t, dims, lam, n_src), nuclei[0][2])
+        else:
+            S = synth.slab(seed, 0, t, dims, lam, np.complex64 if dt == "c64" else np.complex128)
+        t0 = time.perf_counter()
+        for pl, (nu, _) in zip(plans, lists_spec):
+            projection.projected_correlators(pl, S.astype(np.complex128), dims, moms, n_sinks=n_sinks,
+                                             dirac_dim=nu[2])
+            done += len(moms) // n_sinks
+        t_tot += time.perf_counter() - t0
+        slabs += 1
+        if t_tot > budget_s:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    omp = os.environ.get("OMP_NUM_THREADS")
+    return {"value": done / t_tot, "unit": "momentum-projected correlators/s", "cores": int(omp) if omp else cores,
+            "kind": "oracle",
+            "sample": f"{slabs} slab(s) of the workload, {done} correlators over all nuclei, O3 blocks per site, "
+                      f"numpy phase sums, O3 recursion on the summed blocks, {t_tot:.1f} s"}
+
+
 def run_reference(args, wl):
     """--impl reference: the CPU oracle as it stands, on the machine's host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from oracle import recursion
+    from oracle import projection, recursion
     import synth
     _, nuclei, dims, nt, seed, lam, dt = wl
-    plans = []
-    for (n_p, n_n, D, spins) in nuclei:
-        plans.append(recursion.Plan(n_p, n_n, D, requests=spins))
+    wopt = WORKLOAD_OPTS.get(args.workload, {})
+    n_src, n_sinks = wopt.get("n_src", 1), wopt.get("n_sinks", 1)
+    block = (args.sink or wopt.get("sink", "point")) == "block"
+    moms = tuple(MOMENTA[:args.moms or wopt.get("moms", 1)])
+    plans = oracle_plans([(n, n[3]) for n in nuclei], n_src)
     v3 = dims[0] * dims[1] * dims[2]
-    per_step_sites = 1024 if all(p.dim == 2 for p in plans) else 4
-    slab = synth.slab(seed, 0, 0, dims, lam, np.complex64 if dt == "c64" else np.complex128)
-    S = slab.reshape(-1, 12, 12).astype(np.complex128)[: min(v3, per_step_sites)]
-    def step():
-        for pl in plans:
-            pl.evaluate(S, batch=16)
+    if n_src > 1:
+        S = recursion.source_columns(synth.slab_sources(seed, 0, 0, dims, lam, n_src), nuclei[0][2]).reshape(-1, 12, 12)
+    else:
+        slab = synth.slab(seed, 0, 0, dims, lam, np.complex64 if dt == "c64" else np.complex128)
+        S = slab.reshape(-1, 12, 12).astype(np.complex128)
+    if block:  # one step: every nucleus' projected correlators of one whole slab
+        metric = "momentum-projected correlators/s"
+        unit_per_step = (len(moms) // n_sinks) * len(plans)
+        sample = f"slab t=0 ({v3} sites) per step, momentum-projected blocks, every nucleus of the workload"
+
+        def step():
+            for pl, nu in zip(plans, nuclei):
+                projection.projected_correlators(pl, S.reshape(dims + (12, 12)), dims, moms, n_sinks=n_sinks,
+                                                 dirac_dim=nu[2])
+    else:
+        metric = "sink-site correlators/s"
+        per_step_sites = 1024 if all(p.dim == 2 for p in plans) else 4
+        S = S[: min(v3, per_step_sites)]
+        unit_per_step = S.shape[0] * len(plans)
+        sample = f"{S.shape[0]} sites of slab t=0 per step, every nucleus of the workload"
+
+        def step():
+            for pl in plans:
+                pl.evaluate(S, batch=16)
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
     dt_s = time.perf_counter() - t0
-    units = S.shape[0] * len(plans) * args.steps
+    units = unit_per_step * args.steps
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     val = units / dt_s
-    line = {"impl": "reference", "metric": "sink-site correlators/s", "value": val,
-            "unit": "sink-site correlators/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+    line = {"impl": "reference", "metric": metric, "value": val,
+            "unit": metric, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt_s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl[0], "sample_sites_per_step": int(S.shape[0])},
-            "cpu_baseline": {"value": val, "unit": "sink-site correlators/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{S.shape[0]} sites of slab t=0 per step, every nucleus of the workload"},
-            "e2e": {"value": val, "unit": "sink-site correlators/s", "h2d_bytes_per_step": 0,
+            "config": {"workload": wl[0], "units_per_step": int(unit_per_step)},
+            "cpu_baseline": {"value": val, "unit": metric, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": metric, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -287,6 +364,14 @@ def main():
     nt = args.nt or nt_full
     if args.workload in ("he4rel", "be8") and not args.nt:
         nt = 1  # one time slice: 4096 sinks
+    wopt = WORKLOAD_OPTS.get(args.workload, {})
+    n_src, n_sinks = wopt.get("n_src", 1), wopt.get("n_sinks", 1)
+    sink = args.sink or wopt.get("sink", "point")
+    n_mom = args.moms or wopt.get("moms", 1)
+    if n_mom % n_sinks or n_mom > len(MOMENTA):
+        raise SystemExit("momenta must fill whole groups of sink functions")
+    moms = tuple(MOMENTA[:n_mom])
+    sink_mode = mbc.SINK_BLOCK_MOMENTUM if sink == "block" else mbc.SINK_POINT
     if args.combined:
         if len({n[2] for n in nuclei}) != 1:
             raise SystemExit("--combined needs one operator type")
@@ -294,14 +379,20 @@ def main():
                                     path=shared_path(nuclei))]
         list_dims = [nuclei[0][2]]
     else:
-        lists = [mbc.build_term_list(n_p, n_n, D, spins=spins) for (n_p, n_n, D, spins) in nuclei]
+        lists = [mbc.build_term_list(n_p, n_n, D, spins=spins, list_free=args.list_free, n_sources=n_src,
+                                     n_sinks=n_sinks) for (n_p, n_n, D, spins) in nuclei]
         list_dims = [n[2] for n in nuclei]
     stats = [tl.stats() for tl in lists]
-    field_np = make_field(wl, range(rank * args.cfgs, (rank + 1) * args.cfgs), nt)
+    field_np = make_field(wl, range(rank * args.cfgs, (rank + 1) * args.cfgs), nt, n_src)
     v3 = dims[0] * dims[1] * dims[2]
     field = torch.from_numpy(field_np).to(dev)
     stream = torch.cuda.Stream(dev)
-    units_per_step = v3 * nt * len(nuclei) * args.cfgs
+    if sink == "block":  # one unit: a nucleus' correlator tensor at one (cfg, t, momentum group)
+        units_per_step = nt * (n_mom // n_sinks) * len(nuclei) * args.cfgs
+        metric = "momentum-projected correlators/s"
+    else:  # one unit: a nucleus' correlator tensor at one (cfg, t, sink site)
+        units_per_step = v3 * nt * len(nuclei) * args.cfgs
+        metric = "sink-site correlators/s"
     tunes = {0: None, 1: None}
     if args.tune:
         tunes = {0: json.loads(args.tune), 1: json.loads(args.tune)}
@@ -313,14 +404,17 @@ def main():
 
     def step(precision):
         if not args.graph:
-            return mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision])
+            return mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision], moms=moms,
+                                sink=sink_mode)
         if precision not in graphs:
             with torch.cuda.stream(stream):
-                out = mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision])
+                out = mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision], moms=moms,
+                                   sink=sink_mode)
             stream.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
-                mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision], out=out)
+                mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision], out=out,
+                             moms=moms, sink=sink_mode)
             graphs[precision] = (g, out)
         g, out = graphs[precision]
         with torch.cuda.stream(stream):
@@ -373,11 +467,11 @@ def main():
         pinned.copy_(torch.from_numpy(field_np))
         host = pinned.numpy()
         for _ in range(max(1, args.warmup)):
-            mbc.contract(host, lists, precision=primary)
+            mbc.contract(host, lists, precision=primary, moms=moms, sink=sink_mode)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            res = mbc.contract(host, lists, precision=primary)
+            res = mbc.contract(host, lists, precision=primary, moms=moms, sink=sink_mode)
             _ = complex(res.reshape(-1)[0])  # the step's result read on the host
         dt_s = time.perf_counter() - t0
         tt = torch.tensor([dt_s], dtype=torch.float64, device=dev)
@@ -385,7 +479,7 @@ def main():
             import torch.distributed as dist
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         dt_s = float(tt.item())
-        e2e = {"value": units_per_step * world * args.steps / dt_s, "unit": "sink-site correlators/s",
+        e2e = {"value": units_per_step * world * args.steps / dt_s, "unit": metric,
                "h2d_bytes_per_step": int(field_np.nbytes), "d2h_bytes_per_step": int(res.nbytes)}
 
     if rank != 0:
@@ -396,7 +490,19 @@ def main():
     value = value64 if primary == 0 else value_mx
     # roofline of the dominant kernel (the contraction kernel; FP64 pipe)
     fl = [site_flops(st, d) for st, d in zip(stats, list_dims)]
-    flops_step = sum(f["total"] for f in fl) * v3 * nt * args.cfgs
+    if sink == "block":
+        # per site: blocks of one sink function and their phase-weighted sums
+        # over the momenta; per (cfg, t, group): recursion and contraction
+        per_site = per_item = 0
+        for st, d in zip(stats, list_dims):
+            bs_site = st["block_size"] // n_sinks
+            nxi = 3 * d * n_src
+            n_blocks = len(set(st["path"]))
+            per_site += 3 * nxi * nxi * (2 * (4 if d == 4 else 2)) * 8 + n_blocks * bs_site * (6 * 8 + n_mom * 8)
+            per_item += 8 * st["n_ops_total"] + 4 * st["n_l_total"]
+        flops_step = (per_site * v3 + per_item * (n_mom // n_sinks)) * nt * args.cfgs
+    else:
+        flops_step = sum(f["total"] for f in fl) * v3 * nt * args.cfgs
     peaks = measured_peaks()
     probe64 = mbc.fma_probe(0)
     probe32 = mbc.fma_probe(1)
@@ -430,7 +536,7 @@ def main():
         roof["traffic_note"] = ("DRAM bytes per launch (one launch per step) from the committed ncu summary, "
                                 "scaled from 65,536 to the step's sites")
     line = {
-        "metric": "sink-site correlators/s", "value": value, "unit": "sink-site correlators/s", "n_gpus": world,
+        "metric": metric, "value": value, "unit": metric, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": (ms64 if primary == 0 else msmx) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if primary == 0 else "f32+f64", "data": "synthetic",
@@ -438,6 +544,7 @@ def main():
                    "sites_per_step": v3 * nt * args.cfgs, "units_per_step": units_per_step,
                    "configurations_per_rank": args.cfgs, "graph": bool(args.graph),
                    "combined_path": stats[0]["path"] if args.combined else None,
+                   "list_free": bool(args.list_free), "list_bytes": [st["op_bytes"] for st in stats],
                    "tune": {"fp64": tunes[0], "mixed": tunes[1]},
                    "l2": "inputs larger than L2 (field %.0f MB)" % (field_np.nbytes / 2 ** 20),
                    "parallelism": f"configurations sharded over {world} GPU(s)"},
@@ -451,7 +558,11 @@ def main():
         "n_ops": [st["n_ops_total"] for st in stats],
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, [(n, tl.components()) for n, tl in zip(nuclei, lists)], nt)
+        if sink == "block":
+            line["cpu_baseline"] = cpu_baseline_projected(wl, [(n, tl.components()) for n, tl in zip(nuclei, lists)],
+                                                          nt, moms, n_src, n_sinks)
+        else:
+            line["cpu_baseline"] = cpu_baseline(wl, [(n, tl.components()) for n, tl in zip(nuclei, lists)], nt)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -108,6 +108,17 @@ enum { MBC_PROTON = 0, MBC_NEUTRON = 1 };
  *                order in which baryons are added (Sec. 7). NULL selects the
  *                paper's rule: the more numerous species first, neutrons
  *                first on a tie.
+ *   list_free    0: every step keeps its operation arrays. 1: no step
+ *                stores operation arrays; the contraction kernels regenerate
+ *                every split of an output component from its key (Sec. 3
+ *                tuples, the split order of the stored lists). A step whose
+ *                stages are dense (every component of the index space is
+ *                needed, e.g. all stages of 8Be and of nonrelativistic 4He)
+ *                needs nothing else; otherwise two index tables stand in for
+ *                the arrays (dense rank of each output, compact index of each
+ *                dense input rank), e.g. 4He relativistic, all components:
+ *                3.19 GB of arrays become about 100 MB of tables. Such lists
+ *                run on the wave kernels only.
  * The spec is read during the call only; the caller keeps ownership.
  */
 typedef struct {
@@ -124,6 +135,7 @@ typedef struct {
     const int32_t *term_proj;
     const double *term_coef;
     int32_t n_sinks;
+    int32_t list_free;
 } mbc_op_spec;
 
 typedef struct mbc_term_list mbc_term_list; /* opaque, library-owned */
@@ -147,6 +159,9 @@ typedef struct {
     int64_t n_l_total;                   /* nonzero L entries, all components */
     double norm;                         /* (n_P! n_N!)^2 of the largest nucleus */
     int32_t n_parts;                     /* nuclei in the list (mbc_build_combined) */
+    uint32_t dense_mask;                 /* bit m-1: step m -> m+1 has dense stages */
+    int64_t op_bytes;                    /* host bytes of the operation arrays (or of
+                                            the index tables of a list-free list) */
 } mbc_list_stats;
 
 /*
@@ -252,6 +267,10 @@ typedef struct {
     int32_t wave_order;         /* large-stage step kernel: 0 site groups of a chunk
                                    side by side, 1 a CTA's warps on consecutive chunks
                                    of one site group                              */
+    int32_t list_free;          /* large-stage step kernel: 0 regenerate the splits of
+                                   list-free lists, read the arrays of the others;
+                                   1 also regenerate the dense steps of lists with
+                                   arrays                                           */
 } mbc_tune;
 
 /*

@@ -46,7 +46,7 @@ class OpSpec(ctypes.Structure):
                 ("n_sources", ctypes.c_int32), ("spin_mode", ctypes.c_int32), ("n_spin_sel", ctypes.c_int32),
                 ("snk_spins", ctypes.c_void_p), ("src_spins", ctypes.c_void_p), ("path_len", ctypes.c_int32),
                 ("path", ctypes.c_void_p), ("n_proj", ctypes.c_int32), ("term_proj", ctypes.c_void_p),
-                ("term_coef", ctypes.c_void_p), ("n_sinks", ctypes.c_int32)]
+                ("term_coef", ctypes.c_void_p), ("n_sinks", ctypes.c_int32), ("list_free", ctypes.c_int32)]
 
 
 class ListStats(ctypes.Structure):
@@ -55,7 +55,8 @@ class ListStats(ctypes.Structure):
                 ("ops_per_z", ctypes.c_int64 * MAX_A), ("stage_size", ctypes.c_int64 * MAX_A),
                 ("stage_bound", ctypes.c_int64 * MAX_A), ("q_bound", ctypes.c_int64 * MAX_A),
                 ("block_size", ctypes.c_int64), ("n_comp", ctypes.c_int32), ("n_l_total", ctypes.c_int64),
-                ("norm", ctypes.c_double), ("n_parts", ctypes.c_int32)]
+                ("norm", ctypes.c_double), ("n_parts", ctypes.c_int32), ("dense_mask", ctypes.c_uint32),
+                ("op_bytes", ctypes.c_int64)]
 
 
 class ListPart(ctypes.Structure):
@@ -72,9 +73,9 @@ class Props(ctypes.Structure):
 class Tune(ctypes.Structure):
     _fields_ = [("sites_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
                 ("wave_sites", ctypes.c_int32), ("regime", ctypes.c_int32), ("zchunk", ctypes.c_int32),
-                ("wave_order", ctypes.c_int32)]
+                ("wave_order", ctypes.c_int32), ("list_free", ctypes.c_int32)]
 
-    FIELDS = ("sites_per_cta", "threads_per_cta", "wave_sites", "regime", "zchunk", "wave_order")
+    FIELDS = ("sites_per_cta", "threads_per_cta", "wave_sites", "regime", "zchunk", "wave_order", "list_free")
 
 
 class ContractOpts(ctypes.Structure):
@@ -168,6 +169,7 @@ class TermList:
             "stage_size": list(st.stage_size[:A]), "stage_bound": list(st.stage_bound[:A]),
             "q_bound": list(st.q_bound[: st.n_steps]), "block_size": st.block_size, "n_comp": st.n_comp,
             "n_l_total": st.n_l_total, "norm": st.norm, "n_parts": st.n_parts,
+            "dense_steps": [m + 1 for m in range(st.n_steps) if st.dense_mask >> m & 1], "op_bytes": st.op_bytes,
         }
 
     def parts(self):
@@ -204,12 +206,13 @@ class TermList:
             pass
 
 
-def _op_spec(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, keep):
+def _op_spec(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, keep, list_free=False):
     """Fill an OpSpec; arrays it points to are appended to keep."""
     A = n_p + n_n
     spec = OpSpec()
     spec.n_p, spec.n_n, spec.dirac_dim, spec.n_sources = n_p, n_n, dirac_dim, n_sources
     spec.n_sinks = n_sinks
+    spec.list_free = 1 if list_free else 0
     if projections is not None:
         if spins is not None:
             raise ValueError("give spins or projections, not both")
@@ -244,19 +247,22 @@ def _op_spec(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, 
 
 
 def build_term_list(n_p: int, n_n: int, dirac_dim: int = 4, spins=None, path=None, n_sources: int = 1,
-                    projections=None, n_sinks: int = 1) -> TermList:
+                    projections=None, n_sinks: int = 1, list_free: bool = False) -> TermList:
     """``mbc_build_term_list``. spins: None for every independent component,
     or a list of (sink spins, source spins) pairs, protons first.
     projections: instead of spins, a list of projections, each a list of
-    (sink spins, source spins, real weight) terms (Sec. 5); one output each."""
+    (sink spins, source spins, real weight) terms (Sec. 5); one output each.
+    list_free: store no operation arrays for dense steps (regenerated on
+    the GPU)."""
     lib = load()
     keep = []
-    spec = _op_spec(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, keep)
+    spec = _op_spec(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, keep, list_free)
     h = ctypes.c_void_p()
     rc = lib.mbc_build_term_list(ctypes.byref(spec), ctypes.byref(h))
     _check(rc, "mbc_build_term_list", ok=(0, 2))
     return TermList(h, rc, {"n_p": n_p, "n_n": n_n, "dirac_dim": dirac_dim, "spins": spins, "path": path,
-                            "projections": projections, "n_sources": n_sources, "n_sinks": n_sinks})
+                            "projections": projections, "n_sources": n_sources, "n_sinks": n_sinks,
+                            "list_free": list_free})
 
 
 def build_combined(nuclei, dirac_dim: int = 4, path=None, n_sources: int = 1, n_sinks: int = 1) -> TermList:

@@ -394,6 +394,8 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
         if (specs[j].n_p + specs[j].n_n > specs[big].n_p + specs[big].n_n) big = j;
     const mbc_op_spec *spec = &specs[big];
     const int np = spec->n_p, nn = spec->n_n, A = np + nn, D = spec->dirac_dim;
+    bool list_free = false;
+    for (int j = 0; j < n_specs; ++j) list_free = list_free || specs[j].list_free != 0;
     const int ns = std::max(1, spec->n_sources), nk = std::max(1, spec->n_sinks);
     const int dim = D * nk;        // sink baryon index: spin x sink function (Sec. 6 psi)
     const int dim_src = D * ns;    // source baryon index: spin x source (Sec. 6 chi)
@@ -616,6 +618,20 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
         st.ops_per_z[m - 1] = k;
         st.n_ops[m - 1] = k * s.n_z;
         st.n_ops_total += k * s.n_z;
+        s.dense = s.n_z == sz.size() && (m == 1 || (i64)members[(size_t)m].size() == sx.size());
+        if (s.dense) st.dense_mask |= 1u << (m - 1);
+        s.zk[0] = sz.kp; s.zk[1] = sz.kn; s.zk[2] = sz.ku; s.zk[3] = sz.kd;
+        s.xk[0] = sx.kp; s.xk[1] = sx.kn; s.xk[2] = sx.ku; s.xk[3] = sx.kd;
+        if (list_free) {
+            // splits regenerated from the output key on the device; two index
+            // tables stand in for the op arrays where a stage is not dense
+            s.generated = true;
+            if (s.n_z != sz.size()) s.zrank.assign(mem.begin(), mem.end());
+            if (m > 1 && (i64)members[(size_t)m].size() != sx.size()) s.xmap = compact[(size_t)m];
+            st.op_bytes += (i64)(s.zrank.size() * sizeof(int64_t) + s.xmap.size() * sizeof(int32_t));
+            continue;
+        }
+        st.op_bytes += k * s.n_z * (i64)(sizeof(uint32_t) + sizeof(uint16_t));
         s.x.resize((size_t)(k * s.n_z));
         s.ys.resize((size_t)(k * s.n_z));
         const auto &cmx = compact[(size_t)m];

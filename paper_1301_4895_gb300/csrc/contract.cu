@@ -101,6 +101,8 @@ struct DeviceCache {
     int64_t *d_fin_off = nullptr;
     uint32_t *d_fin_z = nullptr;
     double *d_fin_l = nullptr;
+    std::vector<int64_t *> d_zrank;    // list-free steps: index tables
+    std::vector<int32_t *> d_xmap;
     uint32_t *d_fin_zs = nullptr;      // small path: region offsets of the contracted entries
     double *d_comp_inv_norm = nullptr;
     int32_t *d_comp_deg = nullptr;
@@ -118,6 +120,8 @@ void free_cache(DeviceCache *c) {
     cudaFree(c->d_small_zops);
     for (auto p : c->d_opx) cudaFree(p);
     for (auto p : c->d_opy) cudaFree(p);
+    for (auto p : c->d_zrank) cudaFree(p);
+    for (auto p : c->d_xmap) cudaFree(p);
     cudaFree(c->d_fin_off);
     cudaFree(c->d_fin_z);
     cudaFree(c->d_fin_l);
@@ -149,6 +153,8 @@ bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries, std
     const int A = L->A;
     if (A > 16 || L->n_comp > kSmallMaxComp || L->n_comp < 1) return false;
     if (L->n_sources != 1) return false;
+    for (const auto &s : L->steps)
+        if (s.generated) return false;  // list-free lists run on the wave kernels
     P.A = A;
     P.dim = L->dim;
     P.nxi = L->nxi;
@@ -307,11 +313,15 @@ DeviceCache *get_cache(const mbc_term_list *Lc, int device, mbc_status &st) {
     // large-path op arrays
     c->d_opx.assign(L->steps.size(), nullptr);
     c->d_opy.assign(L->steps.size(), nullptr);
+    c->d_zrank.assign(L->steps.size(), nullptr);
+    c->d_xmap.assign(L->steps.size(), nullptr);
     for (size_t m = 0; m < L->steps.size(); ++m) {
         const Step &s = L->steps[m];
         c->max_stage = std::max(c->max_stage, s.n_z);
         if ((st = upload(&c->d_opx[m], s.x.data(), s.x.size())) != MBC_OK ||
-            (st = upload(&c->d_opy[m], s.ys.data(), s.ys.size())) != MBC_OK) {
+            (st = upload(&c->d_opy[m], s.ys.data(), s.ys.size())) != MBC_OK ||
+            (st = upload(&c->d_zrank[m], s.zrank.data(), s.zrank.size())) != MBC_OK ||
+            (st = upload(&c->d_xmap[m], s.xmap.data(), s.xmap.size())) != MBC_OK) {
             free_cache(c);
             return nullptr;
         }
@@ -362,6 +372,10 @@ mbc_status ensure_constants(int device) {
         }
     MBC_CUDA_TRY(cudaMemcpyToSymbol(c_pair_i, pi, sizeof(pi)));
     MBC_CUDA_TRY(cudaMemcpyToSymbol(c_pair_j, pj, sizeof(pj)));
+    uint32_t bn[25][25];
+    for (int n = 0; n < 25; ++n)
+        for (int k = 0; k < 25; ++k) bn[n][k] = (uint32_t)binom64(n, k);
+    MBC_CUDA_TRY(cudaMemcpyToSymbol(c_binom, bn, sizeof(bn)));
     if (device < 31) g_const_dev_mask |= 1 << device;
     return MBC_OK;
 }
@@ -500,6 +514,83 @@ LargeSizes large_sizes(const mbc_term_list *L, const DeviceCache *c, const mbc_t
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
+// Device description of step m (0-based) for regenerating its operations.
+GenStep gen_step(const mbc_term_list *L, const DeviceCache *c, size_t m) {
+    const Step &s = L->steps[m];
+    GenStep g;
+    std::memset(&g, 0, sizeof(g));
+    g.b = s.baryon;
+    g.bprev = L->path[0];
+    g.x_block = m == 0;
+    g.nxi = L->nxi;
+    g.npair = (int)binom64(L->nxi, 2);
+    g.dim = L->dim_snk;
+    for (int i = 0; i < 4; ++i) {
+        g.zk[i] = s.zk[i];
+        g.xk[i] = s.xk[i];
+        const int n = i < 2 ? L->dim_snk : L->nxi;
+        g.zr[i] = binom64(n, s.zk[i]);
+        g.xr[i] = binom64(n, s.xk[i]);
+    }
+    g.zrank = c->d_zrank[m];
+    g.xmap = c->d_xmap[m];
+    return g;
+}
+
+// One recursion step of a wave (k_large_step), reading the stored operations
+// or regenerating them (list-free lists; dense steps on request).
+template <class Tr>
+mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, const mbc_tune *tune, int W, int nsm,
+                       const typename Tr::V *X, const typename Tr::V *Y, typename Tr::V *Z, cudaStream_t stream) {
+    const Step &s = L->steps[m];
+    const bool gen = s.generated || (tune && tune->list_free == 1 && s.dense);
+    // FP32 arithmetic is too cheap to hide per-warp regeneration: the mixed
+    // path regenerates once per CTA into shared memory
+    if (gen && sizeof(typename Tr::V) == sizeof(float2)) {
+        // CTA-shared regeneration: zb outputs' operations per round in shared memory
+        const size_t per_z = (size_t)s.k * (sizeof(uint32_t) + sizeof(uint16_t));
+        const int64_t nblk = (W / 32 + 7) / 8;
+        const int64_t target = (int64_t)nsm * 3 * 8;
+        int64_t nchunks = std::max<int64_t>(1, std::min<int64_t>(s.n_z, (target + nblk - 1) / nblk));
+        int64_t zchunk = (s.n_z + nchunks - 1) / nchunks;
+        if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
+        nchunks = (s.n_z + zchunk - 1) / zchunk;
+        const int zb = (int)std::max<int64_t>(1, std::min<int64_t>(zchunk, (int64_t)((64u << 10) / per_z)));
+        const size_t smem = (size_t)zb * per_z + 16;
+        int per_sm = 0;
+        mbc_status pst = prepare_kernel((const void *)k_large_step_gen<Tr>, c->device, 256, smem, &per_sm);
+        if (pst != MBC_OK) return pst;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nchunks * nblk, (int64_t)nsm * std::max(per_sm, 1) * 4));
+        {
+            TimedLaunch tl(stream);
+            k_large_step_gen<Tr><<<(unsigned)grid, 256, smem, stream>>>(gen_step(L, c, m), s.n_z, s.k, zchunk, zb, W,
+                                                                        X, Y, Z);
+        }
+        MBC_CUDA_TRY(cudaGetLastError());
+        return MBC_OK;
+    }
+    const int threads = 256;
+    const int64_t total_warps = (int64_t)nsm * 8 * (threads / 32);
+    const int64_t ngroups = W / 32;
+    int64_t zchunk = (s.n_z * ngroups + 8 * total_warps - 1) / (8 * total_warps);
+    zchunk = std::max<int64_t>(1, std::min<int64_t>(zchunk, 256));
+    if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
+    const int64_t items = ((s.n_z + zchunk - 1) / zchunk) * ngroups;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
+    const int order = tune ? tune->wave_order : 0;
+    {
+        TimedLaunch tl(stream);
+        if (gen)
+            k_large_step<Tr, true><<<(unsigned)grid, threads, 0, stream>>>(nullptr, nullptr, gen_step(L, c, m), s.n_z,
+                                                                           s.k, zchunk, W, order, X, Y, Z);
+        else
+            k_large_step<Tr, false><<<(unsigned)grid, threads, 0, stream>>>(c->d_opx[m], c->d_opy[m], GenStep{}, s.n_z,
+                                                                            s.k, zchunk, W, order, X, Y, Z);
+    }
+    MBC_CUDA_TRY(cudaGetLastError());
+    return MBC_OK;
+}
+
 // Contraction with L (eq. C_final) of every nucleus of the list that ends at
 // stage `stage` of the path, from that stage's buffer X ([component][W]);
 // deg_per_baryon: homogeneity degree of C per baryon in the scaled inputs (3
@@ -565,22 +656,7 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
             const Step &s = L->steps[m];
             V *Z = buf[(m + 1) & 1];
             const V *Y = s.baryon == MBC_PROTON ? fP : fN;
-            const int threads = 256;
-            const int64_t total_warps = (int64_t)nsm * 8 * (threads / 32);
-            int64_t ngroups = W / 32;
-            int64_t zchunk = (s.n_z * ngroups + 8 * total_warps - 1) / (8 * total_warps);
-            zchunk = std::max<int64_t>(1, std::min<int64_t>(zchunk, 256));
-            if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
-            int64_t items = ((s.n_z + zchunk - 1) / zchunk) * ngroups;
-            int64_t grid = std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8);
-            grid = std::max<int64_t>(grid, 1);
-            {
-                TimedLaunch tl(stream);
-                k_large_step<Tr><<<(unsigned)grid, threads, 0, stream>>>(c->d_opx[m], c->d_opy[m], s.n_z, s.k,
-                                                                         zchunk, W, tune ? tune->wave_order : 0, X,
-                                                                         Y, Z);
-            }
-            MBC_CUDA_TRY(cudaGetLastError());
+            if ((cst = launch_step<Tr>(L, c, m, tune, W, nsm, X, Y, Z, stream)) != MBC_OK) return cst;
             X = Z;
             if ((cst = contract_parts<Tr>(L, c, (int)m + 2, X, W, sexp, 3, Cb, nsm, stream)) != MBC_OK) return cst;
         }
@@ -636,9 +712,12 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
     }
     {
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)nsm * 8));
-        k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nrow, nxi, n_g2(L), bs,
-                                                                (int)binom64(nxi, 2), L->need_block[0],
-                                                                L->need_block[1], tps, n_tiles, partial);
+        {
+            TimedLaunch tl(stream);
+            k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nrow, nxi, n_g2(L), bs,
+                                                                    (int)binom64(nxi, 2), L->need_block[0],
+                                                                    L->need_block[1], tps, n_tiles, partial);
+        }
         MBC_CUDA_TRY(cudaGetLastError());
         const int64_t outs = n_slabs * M.n_mom * n_out;
         const unsigned rg = (unsigned)std::min<int64_t>((outs + 7) / 8, 65535);
@@ -660,21 +739,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
             const Step &s = L->steps[m];
             V *Z = buf[(m + 1) & 1];
             const V *Y = s.baryon == MBC_PROTON ? fP : fN;
-            const int threads = 256;
-            const int64_t total_warps = (int64_t)nsm * 8 * (threads / 32);
-            const int64_t ngroups = W / 32;
-            int64_t zchunk = (s.n_z * ngroups + 8 * total_warps - 1) / (8 * total_warps);
-            zchunk = std::max<int64_t>(1, std::min<int64_t>(zchunk, 256));
-            if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
-            const int64_t items = ((s.n_z + zchunk - 1) / zchunk) * ngroups;
-            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
-            {
-                TimedLaunch tl(stream);
-                k_large_step<Tr><<<(unsigned)grid, threads, 0, stream>>>(c->d_opx[m], c->d_opy[m], s.n_z, s.k,
-                                                                         zchunk, W, tune ? tune->wave_order : 0, X,
-                                                                         Y, Z);
-            }
-            MBC_CUDA_TRY(cudaGetLastError());
+            if ((cst = launch_step<Tr>(L, c, m, tune, W, nsm, X, Y, Z, stream)) != MBC_OK) return cst;
             X = Z;
             if ((cst = contract_parts<Tr>(L, c, (int)m + 2, X, W, sexp, 1, Cb, nsm, stream)) != MBC_OK) return cst;
         }
@@ -708,6 +773,95 @@ void free_device_cache(mbc_term_list *list) {
 }  // namespace mbc
 
 using namespace mbc;
+
+namespace {
+
+// Host-memory mode with the copies overlapped: the evaluated time slices go
+// to the device in chunks through two staging buffers; a second stream copies
+// chunk i + 1 while the caller's stream contracts chunk i (a device-memory
+// call with the same lists and options), and each chunk's results are copied
+// back into their rows of out.
+mbc_status contract_host_pipelined(const mbc_props *props, const mbc_term_list *const *lists, int32_t n_lists,
+                                   const mbc_contract_opts *opts, void *out, cudaStream_t stream, int t0, int n_t,
+                                   int64_t stride_cfg, int64_t stride_t, int64_t site_elems, int n_out_mom,
+                                   int comp_max) {
+    const size_t elem = props->dtype == MBC_C128 ? 16 : 8;
+    const int64_t v3 = (int64_t)props->lx * props->ly * props->lz;
+    const size_t slab_bytes = (size_t)v3 * site_elems * elem;
+    const size_t total = (size_t)props->n_cfg * n_t * slab_bytes;
+    int n_chunks = (int)std::min<size_t>(8, std::max<size_t>(2, total / ((size_t)64 << 20)));
+    n_chunks = std::min(n_chunks, n_t);
+    const int ct = (n_t + n_chunks - 1) / n_chunks;
+    n_chunks = (n_t + ct - 1) / ct;
+    const size_t buf_bytes = (size_t)props->n_cfg * ct * slab_bytes;
+    const size_t row_out = (size_t)n_out_mom * comp_max * sizeof(double2);  // one (cfg, list, t)
+    const size_t chunk_out = (size_t)props->n_cfg * n_lists * ct * row_out;
+    char *stage = nullptr;
+    MBC_CUDA_TRY(cudaMallocAsync((void **)&stage, 2 * buf_bytes + chunk_out, stream));
+    char *buf[2] = {stage, stage + buf_bytes};
+    char *cout = stage + 2 * buf_bytes;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr}, start = nullptr;
+    mbc_status st = MBC_OK;
+    auto cuda_ok = [&](cudaError_t e) {
+        if (e != cudaSuccess && st == MBC_OK) st = MBC_ERR_CUDA;
+        return st == MBC_OK;
+    };
+    if (cuda_ok(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) &&
+        cuda_ok(cudaEventCreateWithFlags(&start, cudaEventDisableTiming))) {
+        for (int b = 0; b < 2 && st == MBC_OK; ++b) {
+            cuda_ok(cudaEventCreateWithFlags(&ready[b], cudaEventDisableTiming));
+            cuda_ok(cudaEventCreateWithFlags(&used[b], cudaEventDisableTiming));
+        }
+    }
+    // the copy stream starts after the staging allocation (stream order)
+    if (st == MBC_OK && cuda_ok(cudaEventRecord(start, stream))) cuda_ok(cudaStreamWaitEvent(cs, start, 0));
+    const char *host = reinterpret_cast<const char *>(props->s_u);
+    char *hout = reinterpret_cast<char *>(out);
+    for (int i = 0; i < n_chunks && st == MBC_OK; ++i) {
+        const int b = i & 1;
+        const int ta = t0 + i * ct, nc = std::min(ct, t0 + n_t - ta);
+        if (i >= 2 && !cuda_ok(cudaStreamWaitEvent(cs, used[b], 0))) break;  // chunk i - 2 done with buf[b]
+        for (int cfg = 0; cfg < props->n_cfg && st == MBC_OK; ++cfg) {
+            const char *src = host + ((size_t)cfg * stride_cfg + (size_t)ta * stride_t) * elem;
+            char *dst = buf[b] + (size_t)cfg * nc * slab_bytes;
+            if (stride_t * (int64_t)elem == (int64_t)slab_bytes) {
+                cuda_ok(cudaMemcpyAsync(dst, src, nc * slab_bytes, cudaMemcpyHostToDevice, cs));
+            } else {
+                for (int t = 0; t < nc && st == MBC_OK; ++t)
+                    cuda_ok(cudaMemcpyAsync(dst + t * slab_bytes, src + (size_t)t * stride_t * elem, slab_bytes,
+                                            cudaMemcpyHostToDevice, cs));
+            }
+        }
+        if (st != MBC_OK || !cuda_ok(cudaEventRecord(ready[b], cs)) || !cuda_ok(cudaStreamWaitEvent(stream, ready[b], 0)))
+            break;
+        mbc_props sub = *props;
+        sub.s_u = sub.s_d = buf[b];
+        sub.memory = MBC_MEM_DEVICE;
+        sub.nt = nc;
+        sub.stride_t = v3 * site_elems;
+        sub.stride_cfg = (int64_t)nc * v3 * site_elems;
+        mbc_contract_opts so = *opts;
+        so.t0 = 0;
+        so.t1 = nc;
+        st = mbc_contract(&sub, lists, n_lists, &so, cout, stream);
+        if (st != MBC_OK || !cuda_ok(cudaEventRecord(used[b], stream))) break;
+        cuda_ok(cudaMemcpy2DAsync(hout + (size_t)(ta - t0) * row_out, (size_t)n_t * row_out, cout, (size_t)nc * row_out,
+                                  (size_t)nc * row_out, (size_t)props->n_cfg * n_lists, cudaMemcpyDeviceToHost, stream));
+    }
+    cudaStreamSynchronize(cs);
+    cudaFreeAsync(stage, stream);
+    if (cudaStreamSynchronize(stream) != cudaSuccess && st == MBC_OK) st = MBC_ERR_CUDA;
+    for (int b = 0; b < 2; ++b) {
+        if (ready[b]) cudaEventDestroy(ready[b]);
+        if (used[b]) cudaEventDestroy(used[b]);
+    }
+    if (start) cudaEventDestroy(start);
+    if (cs) cudaStreamDestroy(cs);
+    return st;
+}
+
+}  // namespace
 
 extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *const *lists, int32_t n_lists,
                                    const mbc_contract_opts *opts, void *out, void *stream_v) {
@@ -751,6 +905,9 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     for (int i = 0; i < n_lists; ++i) comp_max = std::max(comp_max, (int)lists[i]->n_comp);
     const int n_t = t1 - t0;
     const size_t out_bytes = (size_t)props->n_cfg * n_lists * n_t * n_out_mom * comp_max * sizeof(double2);
+    if (props->memory == MBC_MEM_HOST && n_t >= 2)
+        return contract_host_pipelined(props, lists, n_lists, opts, out, stream, t0, n_t, stride_cfg, stride_t,
+                                       site_elems, n_out_mom, comp_max);
 
     // host-memory mode: stage the evaluated slices on the device
     const void *field = props->s_u;

@@ -10,6 +10,7 @@
 #pragma once
 
 #include "device_common.cuh"
+#include "gen_ops.cuh"
 #include "small_kernel.cuh"
 
 namespace mbc {
@@ -108,11 +109,14 @@ __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, 
 
 // One recursion step (eq. recr_F) for a whole wave. Work item = (z chunk,
 // 32-site group), site group fastest so that concurrent warps share list
-// entries and nearby rows of X.
-template <class Tr>
+// entries and nearby rows of X. LF: every warp regenerates the operations of
+// its outputs (gen_ops.cuh), one per lane per 32, instead of reading opx /
+// opy; on the FP64 pipe the integer work of one warp hides under the other
+// warps' DFMAs (the mixed path shares it per CTA instead, k_large_step_gen).
+template <class Tr, bool LF>
 __global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__ opx, const uint16_t *__restrict__ opy,
-                                                    int64_t n_z, int64_t k, int64_t zchunk, int W, int order,
-                                                    const typename Tr::V *__restrict__ X,
+                                                    GenStep gs, int64_t n_z, int64_t k, int64_t zchunk, int W,
+                                                    int order, const typename Tr::V *__restrict__ X,
                                                     const typename Tr::V *__restrict__ Y, typename Tr::V *__restrict__ Z) {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -145,14 +149,20 @@ __global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__
         for (int64_t z = z_begin; z < z_end; ++z) {
             typename Tr::Acc acc;
             acc.zero();
-            const uint32_t *ox = opx + z * k;
-            const uint16_t *oy = opy + z * k;
+            const uint32_t *ox = LF ? nullptr : opx + z * k;
+            const uint16_t *oy = LF ? nullptr : opy + z * k;
+            uint32_t zkey[4];
+            if (LF) g_key(gs, z, zkey);
             for (int64_t b0 = 0; b0 < k; b0 += 32) {
                 const int nb = (int)min((int64_t)32, k - b0);
                 uint32_t mx = 0, my = 0;
                 if (lane < nb) {
-                    mx = __ldg(ox + b0 + lane);
-                    my = __ldg(oy + b0 + lane);
+                    if (LF) {
+                        g_op(gs, zkey, b0 + lane, mx, my);
+                    } else {
+                        mx = __ldg(ox + b0 + lane);
+                        my = __ldg(oy + b0 + lane);
+                    }
                 }
                 // G terms' gathers are issued before their multiply-adds so that
                 // several L2 round trips overlap (FP32: 4 terms, FP64: 2)
@@ -176,6 +186,76 @@ __global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__
                 }
             }
             Z[z * W + col] = acc.store();
+        }
+    }
+}
+
+// The same step with the operations regenerated once per CTA (the mixed
+// path's choice for list-free lists). A CTA of 8 warps takes a z chunk and 8 consecutive
+// 32-site groups; for zb outputs at a time its 256 threads regenerate the
+// outputs' operations once into shared memory, then every warp runs them on
+// its site group exactly as k_large_step runs the stored words (same order,
+// same arithmetic), so the integer work is shared by the CTA's 256 sites.
+template <class Tr>
+__global__ void __launch_bounds__(256, 3) k_large_step_gen(GenStep gs, int64_t n_z, int64_t k, int64_t zchunk, int zb,
+                                                        int W, const typename Tr::V *__restrict__ X,
+                                                        const typename Tr::V *__restrict__ Y,
+                                                        typename Tr::V *__restrict__ Z) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sx = reinterpret_cast<uint32_t *>(smem_raw);  // [zb][k]
+    uint16_t *sy = reinterpret_cast<uint16_t *>(sx + (int64_t)zb * k);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ngroups = W >> 5;
+    const int nblk = (ngroups + 7) / 8;
+    const int64_t nchunks = (n_z + zchunk - 1) / zchunk;
+    for (int64_t item = blockIdx.x; item < nchunks * nblk; item += gridDim.x) {
+        const int64_t chunk = item / nblk;
+        const int group = (int)(item % nblk) * 8 + warp;
+        const bool active = group < ngroups;
+        const int col = group * 32 + lane;
+        const typename Tr::V *Xc = X + (active ? col : 0);
+        const typename Tr::V *Yc = Y + (active ? col : 0);
+        const int64_t z_begin = chunk * zchunk;
+        const int64_t z_end = min(n_z, z_begin + zchunk);
+        for (int64_t zr = z_begin; zr < z_end; zr += zb) {
+            const int nzr = (int)min((int64_t)zb, z_end - zr);
+            __syncthreads();  // the previous round's operations are consumed
+            for (int q = 0; q < nzr; ++q) {
+                uint32_t zkey[4];
+                g_key(gs, zr + q, zkey);
+                for (int64_t j = threadIdx.x; j < k; j += blockDim.x) {
+                    uint32_t ox, oy;
+                    g_op(gs, zkey, j, ox, oy);
+                    sx[q * k + j] = ox;
+                    sy[q * k + j] = (uint16_t)oy;
+                }
+            }
+            __syncthreads();
+            if (!active) continue;
+            for (int q = 0; q < nzr; ++q) {
+                typename Tr::Acc acc;
+                acc.zero();
+                const uint32_t *ox = sx + q * k;
+                const uint16_t *oy = sy + q * k;
+                constexpr int G = sizeof(typename Tr::V) == 8 ? 4 : 2;
+                for (int64_t t0 = 0; t0 < k; t0 += G) {
+                    typename Tr::V xv[G], yv[G];
+                    uint32_t sg[G];
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        if (t0 + g < k) {
+                            const uint32_t x = ox[t0 + g], y = oy[t0 + g];
+                            xv[g] = __ldg(Xc + (int64_t)x * W);
+                            yv[g] = __ldg(Yc + (int64_t)(y & 0x7fffu) * W);
+                            sg[g] = (y & 0x8000u) << 16;
+                        }
+                    }
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+                        if (t0 + g < k) acc.fma(xv[g], yv[g], sg[g]);
+                }
+                Z[(zr + q) * W + col] = acc.store();
+            }
         }
     }
 }

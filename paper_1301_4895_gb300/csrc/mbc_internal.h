@@ -21,8 +21,18 @@ struct Step {
     int64_t n_x = 0;         // size of the input stage (block size for m = 1)
     int64_t n_z = 0;         // size of the output stage
     int64_t k = 0;           // operations per output component
-    std::vector<uint32_t> x; // n_z * k
+    bool dense = false;      // both stages hold their whole index space: the
+                             // compact index is the dense rank (Sec. 3 tuples)
+    bool generated = false;  // list-free: no op arrays, the kernels regenerate
+                             // every split of an output from its key
+    std::vector<uint32_t> x; // n_z * k (empty when generated)
     std::vector<uint16_t> ys;
+    // generated steps: dense rank of each output (empty when the output stage
+    // is dense) and compact index of each dense rank of the input stage
+    // (empty when the input stage is dense or is the first baryon's block)
+    std::vector<int64_t> zrank;
+    std::vector<int32_t> xmap;
+    int32_t zk[4] = {0, 0, 0, 0}, xk[4] = {0, 0, 0, 0};  // set sizes (dp, dn, u, d)
 };
 
 struct DeviceCache;  // defined by the CUDA side

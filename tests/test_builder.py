@@ -262,3 +262,41 @@ def test_combined_rejects_nuclei_off_the_path():
         mbc.build_combined([], 2)
     h = ctypes.c_void_p()
     assert mbc.load().mbc_build_combined(None, 0, ctypes.byref(h)) == 1 and not h.value
+
+
+def test_list_free_lists():
+    """list_free stores no operation arrays: dense steps need nothing, the
+    others two index tables; counts and stage sizes are unchanged."""
+    for n_p, n_n, D, sp in ((2, 2, 2, None), (2, 1, 2, None), (2, 2, 4, [((0, 1, 0, 1), (0, 1, 0, 1))])):
+        spins = sp
+        a = mbc.build_term_list(n_p, n_n, D, spins=spins).stats()
+        b = mbc.build_term_list(n_p, n_n, D, spins=spins, list_free=True).stats()
+        for key in ("n_ops_total", "n_ops", "stage_size", "dense_steps", "n_l_total"):
+            assert a[key] == b[key], key
+        assert a["op_bytes"] == 6 * a["n_ops_total"]
+        assert b["op_bytes"] < a["op_bytes"]
+    st = mbc.build_term_list(2, 2, 2, list_free=True).stats()
+    assert st["dense_steps"] == [1, 2, 3] and st["op_bytes"] == 0
+
+
+def _fill_source_sets(n):
+    """Source spin-source sets of n baryons of one species that fill source 0
+    (chi = 0, 2) first and take source 1 (chi = 1, 3) beyond two baryons."""
+    import itertools
+    if n <= 2:
+        return [tuple(c) for c in itertools.combinations((0, 2), n)]
+    return [tuple(sorted((0, 2) + c)) for c in itertools.combinations((1, 3), n - 2)]
+
+
+def test_two_source_all_component_counts_match_table3():
+    """Table 3 (two sources, nonrelativistic, all components) under the
+    reading in its golden file: two sink functions with every sink
+    component, source components filling source 0 first."""
+    import itertools
+    for row in read_golden("table3_nonrel_two_sources_all.txt"):
+        n_p, n_n, ops = int(row[0]), int(row[1]), int(row[2])
+        snk = [p + q for p in itertools.combinations(range(4), n_p) for q in itertools.combinations(range(4), n_n)]
+        src = [p + q for p in _fill_source_sets(n_p) for q in _fill_source_sets(n_n)]
+        tl = mbc.build_term_list(n_p, n_n, 2, spins=[(a, b) for a in snk for b in src], n_sources=2, n_sinks=2)
+        assert tl.stats()["n_ops_total"] == ops, row
+        tl.free()

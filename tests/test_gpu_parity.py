@@ -111,15 +111,22 @@ def test_complex64_storage(mbc):
 
 
 def test_host_memory_mode_and_determinism(mbc):
+    """Device calls repeat bitwise; host-memory calls (time slices staged in
+    chunks, copies overlapping the contraction) repeat bitwise and agree with
+    the device call up to the summation order of the site sums (the chunks
+    change the launch shape), also on a sub-range of time slices."""
     dims = (4, 4, 4)
-    field = synth.field(5, 2, 3, dims, 0.4)
-    lists = [mbc.build_term_list(1, 1, 2), mbc.build_term_list(2, 2, 2)]
+    field = synth.field(5, 2, 5, dims, 0.4)
+    lists = [mbc.build_term_list(1, 1, 2), mbc.build_term_list(2, 2, 2), mbc.build_term_list(2, 1, 2)]
     for p in (0, 1):
-        a = run(mbc, field, lists, p)
-        b = run(mbc, field, lists, p)
-        h = mbc.contract(field, lists, precision=p)
-        assert np.array_equal(a, b)
-        assert np.array_equal(a, h)
+        for t0, t1 in ((0, 0), (1, 4)):
+            a = run(mbc, field, lists, p, t0=t0, t1=t1)
+            b = run(mbc, field, lists, p, t0=t0, t1=t1)
+            h = mbc.contract(field, lists, precision=p, t0=t0, t1=t1)
+            h2 = mbc.contract(field, lists, precision=p, t0=t0, t1=t1)
+            assert np.array_equal(a, b) and np.array_equal(h, h2)
+            scale = np.max(np.abs(a), axis=(2, 3, 4), keepdims=True) + 1e-300
+            assert float(np.max(np.abs(h - a) / scale)) <= 1e-12, (p, t0, t1)
 
 
 def test_pauli_forbidden_list_is_zero(mbc):
@@ -437,6 +444,46 @@ def test_two_quark_sources_larger_slab(mbc):
         e = max_rel_err(got, ref, scale)
         record("(2,2) D=2 two sources 8^3", p, e)
         assert e <= TOL[p], (p, e)
+
+
+@pytest.mark.parametrize("n_p,n_n,D,spins", [
+    (2, 2, 2, None), (2, 1, 2, None), (1, 1, 2, None),
+    (2, 2, 4, [((0, 1, 0, 1), (0, 1, 0, 1)), ((0, 2, 1, 3), (0, 1, 0, 1))]),
+    (0, 3, 4, [((0, 1, 2), (1, 2, 3))]),
+])
+def test_list_free_steps_match_stored_lists(mbc, n_p, n_n, D, spins):
+    """List-free lists (splits regenerated on the device from the output key,
+    with index tables where a stage is not dense) perform the stored lists'
+    operations in the same order: bitwise equal results on the wave kernels,
+    and within the bound of the oracle. Regenerating the dense steps of a
+    list with arrays (tune list_free = 1) is bitwise equal too."""
+    dims = (3, 2, 5)
+    field = synth.field(28, 1, 2, dims, 0.4)
+    stored = mbc.build_term_list(n_p, n_n, D, spins=spins)
+    free = mbc.build_term_list(n_p, n_n, D, spins=spins, list_free=True)
+    st, sf = stored.stats(), free.stats()
+    assert st["n_ops_total"] == sf["n_ops_total"] and sf["op_bytes"] < st["op_bytes"]
+    moms = ((0, 0, 0), (1, 0, 1))
+    for p in (0, 1):
+        a = run(mbc, field, [stored], p, moms=moms, tune={"regime": 2})
+        b = run(mbc, field, [free], p, moms=moms)
+        assert np.array_equal(a, b), p
+        if st["dense_steps"]:
+            c = run(mbc, field, [stored], p, moms=moms, tune={"regime": 2, "list_free": 1})
+            assert np.array_equal(a, c), p
+    check_slabs(mbc, field, [free], [(n_p, n_n, D)], dims, moms=moms)
+
+
+def test_list_free_be8(mbc):
+    """8Be (0,1,2,3,0,1,2,3): every stage is dense, so the list-free list
+    stores no operations at all (against 2.7 GB of arrays)."""
+    dims = (2, 2, 2)
+    field = synth.field(4, 1, 1, dims, 0.4, dtype=np.complex64)
+    sp = (0, 1, 2, 3, 0, 1, 2, 3)
+    tl = mbc.build_term_list(4, 4, 4, spins=[(sp, sp)], list_free=True)
+    st = tl.stats()
+    assert st["op_bytes"] == 0 and st["dense_steps"] == list(range(1, 8))
+    check_slabs(mbc, field, [tl], [(4, 4, 4)], dims)
 
 
 @pytest.mark.parametrize("n_p,n_n,n_src,spins", [

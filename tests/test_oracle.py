@@ -47,9 +47,14 @@ def test_gamma_conventions():
 # ---- printed counts ------------------------------------------------------------
 
 def test_naive_counts_match_tables():
-    for name, D in (("table1_rel_all.txt", 4), ("table2_nonrel_all.txt", 2)):
+    # Table 3 (two sources) prints the one-source naive count of the same
+    # nucleus, except (3,3): printed 1.3e24, the formula gives 1.17e24 (the
+    # row does not follow n_u! n_d! 12^(2A) to its two digits)
+    for name, D in (("table1_rel_all.txt", 4), ("table2_nonrel_all.txt", 2), ("table3_nonrel_two_sources_all.txt", 2)):
         for row in read_golden(name):
             n_p, n_n = int(row[0]), int(row[1])
+            if name.startswith("table3") and (n_p, n_n) == (3, 3):
+                continue
             naive = counts.naive_ops(n_p, n_n, D)
             printed = float(row[3])
             if "e" in row[3]:
