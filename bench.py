@@ -202,6 +202,20 @@ def make_field(wl, cfgs, nt, n_src=1):
                        cfgs=list(cfgs), n_src=n_src if n_src > 1 else 0)
 
 
+def cpu_model() -> str:
+    """The host CPU as the OS reports it (model name or implementer/part)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model", "CPU part"):
+        for line in info.splitlines():
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    return "unknown"
+
+
 def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0):
     """The oracle (O3, plain C with OpenMP) on a bounded sample: whole slabs
     of the same workload until the budget is spent."""
@@ -236,7 +250,7 @@ def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0):
         pass
     omp = os.environ.get("OMP_NUM_THREADS")
     return {"value": done / t_tot, "unit": "sink-site correlators/s", "cores": int(omp) if omp else cores,
-            "kind": "oracle",
+            "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"{slabs} slab(s) of the workload, {done} site-correlators over all nuclei, O3 plain "
                       f"recursion in C with OpenMP, {t_tot:.1f} s"}
 
@@ -280,7 +294,7 @@ def cpu_baseline_projected(wl, lists_spec, nt_used, moms, n_src, n_sinks, budget
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     omp = os.environ.get("OMP_NUM_THREADS")
     return {"value": done / t_tot, "unit": "momentum-projected correlators/s", "cores": int(omp) if omp else cores,
-            "kind": "oracle",
+            "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"{slabs} slab(s) of the workload, {done} correlators over all nuclei, O3 blocks per site, "
                       f"numpy phase sums, O3 recursion on the summed blocks, {t_tot:.1f} s"}
 
@@ -337,7 +351,8 @@ def run_reference(args, wl):
             "ms_per_step": 1e3 * dt_s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl[0], "units_per_step": int(unit_per_step)},
-            "cpu_baseline": {"value": val, "unit": metric, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": metric, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": val, "unit": metric, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -514,6 +529,10 @@ def main():
     kname = {0: " + ".join(k for k, on in (("k_small<FP64>", has_small), ("k_large_step<FP64>", has_large)) if on),
              1: " + ".join(k for k, on in (("k_small_ls<Mixed>", has_small), ("k_large_step<Mixed>", has_large))
                            if on)}
+    if sink == "block" or n_src > 1 or args.list_free:  # wave kernels only
+        kname = {0: "k_large_step<FP64>", 1: "k_large_step<Mixed>"}
+        if sink == "block":
+            kname = {p: "k_project_blocks + " + k for p, k in kname.items()}
 
     def roofline(kms, ms, launches, peak, probe, kind, prec):
         # kernel time from the library's CUDA events; with graph replay those

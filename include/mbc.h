@@ -202,6 +202,19 @@ typedef struct {
 /* Part j (0 <= j < stats.n_parts) of a list into *part (caller-owned). */
 mbc_status mbc_term_list_part(const mbc_term_list *list, int32_t j, mbc_list_part *part);
 
+/*
+ * Term lists on disk (no counterpart in the paper: a cache so that ranks and
+ * runs load a large list instead of rebuilding it). mbc_save_term_list
+ * writes every field of the list to path (overwritten); mbc_load_term_list
+ * reads such a file into a new list the caller frees with
+ * mbc_free_term_list. A file from another format version or build layout,
+ * a truncated or inconsistent file, or an I/O error gives
+ * MBC_ERR_INVALID_ARG (nothing is returned); a Pauli-forbidden list loads
+ * with MBC_ERR_PAULI_FORBIDDEN, as it was built. Host only.
+ */
+mbc_status mbc_save_term_list(const mbc_term_list *list, const char *path);
+mbc_status mbc_load_term_list(const char *path, mbc_term_list **out);
+
 /* Fill *st (caller-owned). */
 mbc_status mbc_term_list_stats(const mbc_term_list *list, mbc_list_stats *st);
 

@@ -103,6 +103,10 @@ def load(path: str | None = None):
         lib.mbc_status_string.restype = ctypes.c_char_p
         lib.mbc_build_term_list.argtypes = [ctypes.POINTER(OpSpec), ctypes.POINTER(V)]
         lib.mbc_build_term_list.restype = ctypes.c_int
+        lib.mbc_save_term_list.argtypes = [V, ctypes.c_char_p]
+        lib.mbc_save_term_list.restype = ctypes.c_int
+        lib.mbc_load_term_list.argtypes = [ctypes.c_char_p, ctypes.POINTER(V)]
+        lib.mbc_load_term_list.restype = ctypes.c_int
         lib.mbc_build_combined.argtypes = [ctypes.POINTER(OpSpec), ctypes.c_int32, ctypes.POINTER(V)]
         lib.mbc_build_combined.restype = ctypes.c_int
         lib.mbc_term_list_part.argtypes = [V, ctypes.c_int32, ctypes.POINTER(ListPart)]
@@ -191,6 +195,10 @@ class TermList:
                    "mbc_term_list_components")
         return [(tuple(snk[i * A:(i + 1) * A].tolist()), tuple(src[i * A:(i + 1) * A].tolist())) for i in range(n)]
 
+    def save(self, path: str):
+        """``mbc_save_term_list``: write the list to a file."""
+        _check(self._lib.mbc_save_term_list(self._h, os.fsencode(path)), "mbc_save_term_list")
+
     def n_l(self, c: int) -> int:
         return int(self._lib.mbc_term_list_n_l(self._h, c))
 
@@ -246,14 +254,46 @@ def _op_spec(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, 
     return spec
 
 
+def load_term_list(path: str, spec=None) -> TermList:
+    """``mbc_load_term_list``: a list written by ``TermList.save``."""
+    lib = load()
+    h = ctypes.c_void_p()
+    rc = lib.mbc_load_term_list(os.fsencode(path), ctypes.byref(h))
+    _check(rc, "mbc_load_term_list", ok=(0, 2))
+    return TermList(h, rc, spec or {"file": path})
+
+
+def _cache_path(cache_dir: str, spec: dict) -> str:
+    import hashlib
+    key = repr(sorted(spec.items())) + load().mbc_version().decode()
+    return os.path.join(cache_dir, "mbc_list_" + hashlib.sha256(key.encode()).hexdigest()[:24] + ".bin")
+
+
 def build_term_list(n_p: int, n_n: int, dirac_dim: int = 4, spins=None, path=None, n_sources: int = 1,
-                    projections=None, n_sinks: int = 1, list_free: bool = False) -> TermList:
+                    projections=None, n_sinks: int = 1, list_free: bool = False, cache_dir=None) -> TermList:
     """``mbc_build_term_list``. spins: None for every independent component,
     or a list of (sink spins, source spins) pairs, protons first.
     projections: instead of spins, a list of projections, each a list of
     (sink spins, source spins, real weight) terms (Sec. 5); one output each.
-    list_free: store no operation arrays for dense steps (regenerated on
-    the GPU)."""
+    list_free: store no operation arrays (splits regenerated on the GPU).
+    cache_dir: a directory of saved lists keyed by a hash of these
+    arguments; the list is loaded from there when present, else built and
+    saved there."""
+    spec_d = {"n_p": n_p, "n_n": n_n, "dirac_dim": dirac_dim, "spins": spins, "path": path,
+              "projections": projections, "n_sources": n_sources, "n_sinks": n_sinks, "list_free": list_free}
+    if cache_dir is not None:
+        fn = _cache_path(cache_dir, spec_d)
+        if os.path.exists(fn):
+            try:
+                return load_term_list(fn, spec_d)
+            except MbcError:
+                pass  # unreadable or from another build: rebuild and overwrite
+        tl = build_term_list(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, list_free)
+        os.makedirs(cache_dir, exist_ok=True)
+        tmp = f"{fn}.{os.getpid()}.tmp"
+        tl.save(tmp)
+        os.replace(tmp, fn)
+        return tl
     lib = load()
     keep = []
     spec = _op_spec(n_p, n_n, dirac_dim, spins, path, n_sources, projections, n_sinks, keep, list_free)

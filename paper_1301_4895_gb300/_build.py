@@ -1,6 +1,6 @@
 """In-tree build of libmbc.so (nvcc for sm_103a + g++ for the host builder).
 
-Two translation units compiled in parallel, then linked with nvcc; no cmake.
+Three translation units compiled in parallel, then linked with nvcc; no cmake.
 The result lands next to this file and is git-ignored.
 """
 from __future__ import annotations
@@ -44,11 +44,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     inc = ["-I", os.path.join(HERE, "..", "include")]
     cu_obj = os.path.join(OUT, "contract.o")
     cpp_obj = os.path.join(OUT, "builder.o")
+    io_obj = os.path.join(OUT, "list_io.o")
     jobs = [
         [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", *inc, "-c",
          os.path.join(CSRC, "contract.cu"), "-o", cu_obj],
         ["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", *inc, "-c", os.path.join(CSRC, "builder.cpp"), "-o",
          cpp_obj],
+        ["g++", "-O2", "-std=c++17", "-fPIC", *inc, "-c", os.path.join(CSRC, "list_io.cpp"), "-o", io_obj],
     ]
 
     def run(cmd):
@@ -56,11 +58,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)
 
-    with ThreadPoolExecutor(max_workers=2) as ex:
+    with ThreadPoolExecutor(max_workers=3) as ex:
         for f in [ex.submit(run, j) for j in jobs]:
             f.result()
     tmp = LIB + f".{os.getpid()}.tmp"
-    run([nvcc, "-shared", *ARCH, "-o", tmp, cu_obj, cpp_obj, "-Xcompiler", "-fopenmp", "-lgomp"])
+    run([nvcc, "-shared", *ARCH, "-o", tmp, cu_obj, cpp_obj, io_obj, "-Xcompiler", "-fopenmp", "-lgomp"])
     os.replace(tmp, LIB)
     return LIB
 

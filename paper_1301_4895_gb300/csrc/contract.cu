@@ -704,7 +704,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
     int32_t *sexp = reinterpret_cast<int32_t *>(p);
     const int nsm = sm_count(device);
     // 1. blocks of every site, phase-weighted tile sums, reduction over tiles
-    const size_t smem = (size_t)16 * (nrow * nxi + 3 * nxi * nxi) * sizeof(double2);
+    const size_t smem = project_smem_bytes(nrow, nxi, M.n_mom);
     {
         int per_sm = 0;
         mbc_status pst = prepare_kernel((const void *)k_project_blocks, device, 512, smem, &per_sm);

@@ -2,10 +2,12 @@
 // every baryon uses s(x) = exp(-2 pi i n.x / L)), then one recursion per
 // (configuration, time slice, momentum) on the summed blocks.
 //
-//   k_project_blocks   per-site antisymmetric blocks in FP64, multiplied by
-//                      the phase and summed over the 16 sites of a tile by a
-//                      fixed half-warp tree -> tile partials, reduced over
-//                      tiles by k_reduce_tiles (compensated, fixed order);
+//   k_project_blocks   per-site antisymmetric blocks in FP64, a chunk of
+//                      entries at a time through shared memory, multiplied
+//                      by the phase and summed over the 16 sites of a tile
+//                      in a fixed order by one thread per (block, momentum,
+//                      entry) -> tile partials, reduced over tiles by
+//                      k_reduce_tiles (compensated, fixed order);
 //   k_load_proj_blocks copies the summed blocks of a wave of items into the
 //                      [component][item] layout of the wave kernels (MIXED:
 //                      exact power-of-two scaling per item);
@@ -16,6 +18,18 @@
 
 namespace mbc {
 
+// Entries of a block chunk held in shared memory between the block pass and
+// the phase-sum pass; the site index is padded to 17 so that the threads of
+// the phase sum (consecutive entries) read distinct banks.
+constexpr int kProjChunk = 128;
+constexpr int kProjPad = 17;
+
+// Shared memory of k_project_blocks for tiles of 16 sites.
+inline size_t project_smem_bytes(int nrow, int nxi, int n_mom) {
+    return sizeof(double2) * (16 * (size_t)nrow * nxi + 16 * 3 * (size_t)nxi * nxi + 2 * (size_t)kProjChunk * kProjPad +
+                              16 * (size_t)n_mom);
+}
+
 __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
                                                         int nrow, int nxi, int n_g2, int block_size, int npair,
                                                         int need_p,
@@ -25,6 +39,8 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *S = reinterpret_cast<double2 *>(smem_raw);  // [NS][nrow*nxi]
     double2 *Q = S + NS * nrow * nxi;                    // [NS][3*nxi*nxi]
+    double2 *Fb = Q + NS * 3 * nxi * nxi;                // [2][kProjChunk][kProjPad]: block values of the chunk
+    double2 *Ph = Fb + 2 * kProjChunk * kProjPad;        // [NS][n_mom]: the tile's phases
     const int sl = threadIdx.x % NS, slice = threadIdx.x / NS, nslice = blockDim.x / NS;
     const int nent = nrow * nxi, nq = nxi * nxi;
     const int v3 = F.lx * F.ly * F.lz;
@@ -42,6 +58,10 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
             for (int e = lane; e < nent; e += 32)
                 S[s * nent + e] = live ? load_prop(F, base, tile_index(F, e, nxi)) : make_double2(0, 0);
         }
+        for (int o = threadIdx.x; o < NS * M.n_mom; o += blockDim.x) {
+            const int site = tin * NS + o / M.n_mom;
+            Ph[o] = site < v3 ? __ldg(phase + (int64_t)site * M.n_mom + o % M.n_mom) : make_double2(0, 0);
+        }
         __syncthreads();
         for (int e = slice; e < 3 * nq; e += nslice) {
             const int c = e / nq, r = e % nq;
@@ -53,40 +73,48 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
         const double2 *Ss = S + sl * nent;
         const double2 *Qs = Q + sl * 3 * nq;
         const int per_spin = npair * nxi;
-        for (int b = 0; b < 2; ++b) {
-            const bool need = b == 0 ? need_p : need_n;
-            // warp w takes entries (e0, e0 + 1) with e0 = 2w, 2w + nslice, ...: the
-            // trip count is uniform over the warp, so every shuffle has all lanes
-            for (int e0 = (threadIdx.x >> 5) * 2; e0 < block_size; e0 += nslice) {
-                const int e = e0 + ((threadIdx.x >> 4) & 1);
-                const bool ok = e < block_size;
-                double2 f = make_double2(0, 0);
-                if (need && live && ok) {
-                    const int dl = e / per_spin, r = e % per_spin;
-                    const int pr = r / nxi, single = r % nxi;
-                    const int i = c_pair_i[pr], j = c_pair_j[pr];
-                    for (int c = 0; c < 3; ++c) {
-                        const double2 *Sr = Ss + (3 * dl + c) * nxi;
-                        if (b == 0) {
-                            f = cfma(Sr[i], Qs[(c * nxi + j) * nxi + single], f);
-                            f = cfms(Sr[j], Qs[(c * nxi + i) * nxi + single], f);
-                        } else {
-                            f = cfma(Sr[i], Qs[(c * nxi + single) * nxi + j], f);
-                            f = cfms(Sr[j], Qs[(c * nxi + single) * nxi + i], f);
+        for (int e0 = 0; e0 < block_size; e0 += kProjChunk) {
+            // 1. block values of the chunk's entries for the tile's sites
+            for (int el = slice; el < kProjChunk; el += nslice) {
+                const int e = e0 + el;
+                const bool ok = live && e < block_size;
+                const int dl = e / per_spin, r = e % per_spin;
+                const int pr = r / nxi, single = r % nxi;
+                const int i = ok ? c_pair_i[pr] : 0, j = ok ? c_pair_j[pr] : 0;
+                for (int b = 0; b < 2; ++b) {
+                    double2 f = make_double2(0, 0);
+                    if (ok && (b == 0 ? need_p : need_n)) {
+                        for (int c = 0; c < 3; ++c) {
+                            const double2 *Sr = Ss + (3 * dl + c) * nxi;
+                            if (b == 0) {
+                                f = cfma(Sr[i], Qs[(c * nxi + j) * nxi + single], f);
+                                f = cfms(Sr[j], Qs[(c * nxi + i) * nxi + single], f);
+                            } else {
+                                f = cfma(Sr[i], Qs[(c * nxi + single) * nxi + j], f);
+                                f = cfms(Sr[j], Qs[(c * nxi + single) * nxi + i], f);
+                            }
                         }
                     }
-                }
-                for (int q = 0; q < M.n_mom; ++q) {
-                    const double2 ph = live ? __ldg(phase + (int64_t)site * M.n_mom + q) : make_double2(0, 0);
-                    double re = __fma_rn(ph.x, f.x, -ph.y * f.y), im = __fma_rn(ph.x, f.y, ph.y * f.x);
-                    for (int off = NS >> 1; off > 0; off >>= 1) {  // fixed tree over the tile's 16 sites
-                        re += __shfl_xor_sync(0xffffffffu, re, off);
-                        im += __shfl_xor_sync(0xffffffffu, im, off);
-                    }
-                    if (sl == 0 && ok)
-                        partial[(tile * M.n_mom + q) * (int64_t)n_out + b * block_size + e] = make_double2(re, im);
+                    Fb[(b * kProjChunk + el) * kProjPad + sl] = f;
                 }
             }
+            __syncthreads();
+            // 2. phase-weighted sums over the tile's 16 sites in a fixed order,
+            //    one (block, momentum, entry) per thread
+            for (int o = threadIdx.x; o < 2 * M.n_mom * kProjChunk; o += blockDim.x) {
+                const int el = o % kProjChunk, q = (o / kProjChunk) % M.n_mom, b = o / (kProjChunk * M.n_mom);
+                const int e = e0 + el;
+                if (e >= block_size) continue;
+                const double2 *fv = Fb + (b * kProjChunk + el) * kProjPad;
+                double re = 0.0, im = 0.0;
+                for (int w = 0; w < NS; ++w) {
+                    const double2 ph = Ph[w * M.n_mom + q], f = fv[w];
+                    re = __fma_rn(ph.x, f.x, __fma_rn(-ph.y, f.y, re));
+                    im = __fma_rn(ph.x, f.y, __fma_rn(ph.y, f.x, im));
+                }
+                partial[(tile * M.n_mom + q) * (int64_t)n_out + b * block_size + e] = make_double2(re, im);
+            }
+            __syncthreads();  // the chunk's values are consumed
         }
     }
 }

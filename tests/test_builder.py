@@ -300,3 +300,42 @@ def test_two_source_all_component_counts_match_table3():
         tl = mbc.build_term_list(n_p, n_n, 2, spins=[(a, b) for a in snk for b in src], n_sources=2, n_sinks=2)
         assert tl.stats()["n_ops_total"] == ops, row
         tl.free()
+
+
+def test_term_list_files_roundtrip(tmp_path):
+    """A saved list loads with the same statistics, labels and contents (its
+    own save is byte-identical); damaged or foreign files are refused."""
+    kinds = [dict(n_p=2, n_n=2, dirac_dim=2), dict(n_p=2, n_n=1, dirac_dim=2, list_free=True),
+             dict(n_p=1, n_n=1, dirac_dim=2, projections=[[((0, 1), (0, 1), 0.5), ((1, 0), (1, 0), 0.5)]]),
+             dict(n_p=2, n_n=2, dirac_dim=2, spins=[((0, 1, 2, 3), (0, 2, 0, 2))], n_sources=2, n_sinks=2),
+             dict(n_p=0, n_n=3, dirac_dim=2)]
+    for j, kw in enumerate(kinds):
+        a = mbc.build_term_list(**kw)
+        p1, p2 = tmp_path / f"a{j}.bin", tmp_path / f"b{j}.bin"
+        a.save(str(p1))
+        b = mbc.load_term_list(str(p1))
+        b.save(str(p2))
+        assert a.stats() == b.stats() and a.components() == b.components(), kw
+        assert [a.n_l(c) for c in range(a.stats()["n_comp"])] == [b.n_l(c) for c in range(b.stats()["n_comp"])]
+        assert p1.read_bytes() == p2.read_bytes(), kw
+        assert b.pauli_forbidden == a.pauli_forbidden
+    comb = mbc.build_combined([dict(n_p=2, n_n=1), dict(n_p=2, n_n=2)], 2, path=[0, 0, 1, 1])
+    comb.save(str(tmp_path / "c.bin"))
+    assert mbc.load_term_list(str(tmp_path / "c.bin")).parts() == comb.parts()
+    raw = (tmp_path / "a0.bin").read_bytes()
+    (tmp_path / "cut.bin").write_bytes(raw[: len(raw) // 2])
+    (tmp_path / "magic.bin").write_bytes(b"XBCL" + raw[4:])
+    for bad in ("cut.bin", "magic.bin", "missing.bin"):
+        with pytest.raises(mbc.MbcError):
+            mbc.load_term_list(str(tmp_path / bad))
+
+
+def test_term_list_cache(tmp_path):
+    kw = dict(n_p=2, n_n=1, dirac_dim=2, spins=[((0, 1, 0), (0, 1, 1))])
+    a = mbc.build_term_list(**kw, cache_dir=str(tmp_path))
+    files = list(tmp_path.iterdir())
+    assert len(files) == 1
+    b = mbc.build_term_list(**kw, cache_dir=str(tmp_path))  # loaded from the file
+    assert b.stats() == a.stats() and b.components() == a.components()
+    c = mbc.build_term_list(**dict(kw, spins=[((0, 1, 1), (0, 1, 1))]), cache_dir=str(tmp_path))
+    assert len(list(tmp_path.iterdir())) == 2 and c.components() != a.components()

@@ -446,6 +446,21 @@ def test_two_quark_sources_larger_slab(mbc):
         assert e <= TOL[p], (p, e)
 
 
+def test_loaded_term_lists_contract_identically(mbc, tmp_path):
+    """A list written to a file and loaded back contracts bitwise like the
+    list that was built (both regimes, a list-free list included)."""
+    dims = (3, 2, 4)
+    field = synth.field(29, 1, 2, dims, 0.4)
+    built = [mbc.build_term_list(2, 1, 2), mbc.build_term_list(2, 2, 4, spins=[((0, 1, 0, 1), (0, 1, 0, 1))]),
+             mbc.build_term_list(2, 2, 2, list_free=True)]
+    loaded = []
+    for j, tl in enumerate(built):
+        tl.save(str(tmp_path / f"l{j}.bin"))
+        loaded.append(mbc.load_term_list(str(tmp_path / f"l{j}.bin")))
+    for p in (0, 1):
+        assert np.array_equal(run(mbc, field, built, p), run(mbc, field, loaded, p)), p
+
+
 @pytest.mark.parametrize("n_p,n_n,D,spins", [
     (2, 2, 2, None), (2, 1, 2, None), (1, 1, 2, None),
     (2, 2, 4, [((0, 1, 0, 1), (0, 1, 0, 1)), ((0, 2, 1, 3), (0, 1, 0, 1))]),
