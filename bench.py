@@ -427,11 +427,12 @@ def main():
                                    sink=sink_mode)
             stream.synchronize()
             g = torch.cuda.CUDAGraph()
+            n0 = mbc.kernel_launches()
             with torch.cuda.graph(g, stream=stream):
                 mbc.contract(field, lists, precision=precision, stream=stream, tune=tunes[precision], out=out,
                              moms=moms, sink=sink_mode)
-            graphs[precision] = (g, out)
-        g, out = graphs[precision]
+            graphs[precision] = (g, out, mbc.kernel_launches() - n0)
+        g, out, _ = graphs[precision]
         with torch.cuda.stream(stream):
             g.replay()
         return out
@@ -451,10 +452,14 @@ def main():
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        n0 = mbc.kernel_launches()
         e0.record(stream)
         for _ in range(steps):
             out = step(precision)
         e1.record(stream)
+        launch_count[precision] = mbc.kernel_launches() - n0
+        if args.graph:  # each replay runs the kernels captured from one call
+            launch_count[precision] = graphs[precision][2] * steps
         torch.cuda.synchronize(dev)
         barrier()
         ms = e0.elapsed_time(e1)
@@ -467,6 +472,7 @@ def main():
         return float(t.item()), kms, launches, out
 
     nan = float("nan")
+    launch_count = {0: 0, 1: 0}
     with ClockSampler(local) as clk:
         ms64, k64, n64 = (timed(0, args.steps, args.warmup)[:3] if args.precision in ("both", "fp64")
                           else (nan, 0.0, 0))
@@ -573,7 +579,10 @@ def main():
                   "dtype": "f32 products, Kahan-compensated f32 accumulation, f64 contraction and site sums", "roofline": roof_mx},
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": int((1 + 2 * len(lists)) * args.steps),
+        # kernels the library launched in the timed region(s) (graph replays
+        # launch the captured kernels without passing through the library)
+        "gpu_launches": int(launch_count[0] + launch_count[1]),
+        "gpu_launches_per_step": {"fp64": launch_count[0] / args.steps, "mixed": launch_count[1] / args.steps},
         "n_ops": [st["n_ops_total"] for st in stats],
     }
     if not args.no_cpu_baseline:

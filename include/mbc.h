@@ -395,6 +395,11 @@ void mbc_release_scratch(void);
 void mbc_timing_enable(int32_t on);
 mbc_status mbc_timing_read(double *ms, int64_t *launches);
 
+/* Kernels launched by the library's contraction entry points since it was
+ * loaded (cumulative, all devices and streams; the FMA probe excluded), for
+ * counting the launches of a timed region. No counterpart in the paper. */
+int64_t mbc_kernel_launches(void);
+
 /*
  * Arithmetic peak probe: runs independent FMA chains on every SM of the
  * current device (precision MBC_FP64: DFMA, MBC_MIXED: FFMA) and writes the

@@ -134,6 +134,8 @@ def load(path: str | None = None):
         lib.mbc_timing_read.restype = ctypes.c_int
         lib.mbc_fma_probe.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         lib.mbc_fma_probe.restype = ctypes.c_int
+        lib.mbc_kernel_launches.argtypes = []
+        lib.mbc_kernel_launches.restype = ctypes.c_int64
         lib.mbc_version.argtypes = []
         lib.mbc_version.restype = ctypes.c_char_p
         _lib = lib
@@ -438,6 +440,11 @@ def timing_read():
     n = ctypes.c_int64()
     _check(load().mbc_timing_read(ctypes.byref(ms), ctypes.byref(n)), "mbc_timing_read")
     return ms.value, n.value
+
+
+def kernel_launches() -> int:
+    """``mbc_kernel_launches``: cumulative kernel launches of the contraction."""
+    return int(load().mbc_kernel_launches())
 
 
 def fma_probe(precision: int = FP64) -> float:

@@ -17,6 +17,14 @@
 
 #include "large_kernel.cuh"
 #include "mbc_internal.h"
+
+#include <atomic>
+
+namespace mbc {
+// kernels launched by the contraction entry points since the library loaded
+std::atomic<int64_t> g_kernel_launches{0};
+inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace mbc
 #include "probe.cuh"
 #include "project_kernel.cuh"
 #include "small_kernel.cuh"
@@ -479,8 +487,10 @@ mbc_status launch_small_batch(const SmallBatch &B, const FieldDesc &F, const Mom
     MBC_CUDA_TRY(cudaMemsetAsync(B.counter, 0, sizeof(unsigned long long), stream));
     if (timed) {
         TimedLaunch tl(stream);
+        note_launch();
         kern<<<(unsigned)grid, l.threads, l.smem, stream>>>(B, F, M, phase, partial);
     } else {
+        note_launch();
         kern<<<(unsigned)grid, l.threads, l.smem, stream>>>(B, F, M, phase, partial);
     }
     MBC_CUDA_TRY(cudaGetLastError());
@@ -563,6 +573,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nchunks * nblk, (int64_t)nsm * std::max(per_sm, 1) * 4));
         {
             TimedLaunch tl(stream);
+            note_launch();
             k_large_step_gen<Tr><<<(unsigned)grid, 256, smem, stream>>>(gen_step(L, c, m), s.n_z, s.k, zchunk, zb, W,
                                                                         X, Y, Z);
         }
@@ -580,6 +591,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
     const int order = tune ? tune->wave_order : 0;
     {
         TimedLaunch tl(stream);
+        note_launch();
         if (gen)
             k_large_step<Tr, true><<<(unsigned)grid, threads, 0, stream>>>(nullptr, nullptr, gen_step(L, c, m), s.n_z,
                                                                            s.k, zchunk, W, order, X, Y, Z);
@@ -603,6 +615,7 @@ mbc_status contract_parts(const mbc_term_list *L, const DeviceCache *c, int stag
         const int n = pt.c1 - pt.c0;
         const int64_t items = (int64_t)n * (W / 32);
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
+        note_launch();
         k_large_contract<Tr><<<(unsigned)grid, 256, 0, stream>>>(c->d_fin_off + pt.c0, c->d_fin_z, c->d_fin_l, n, W,
                                                                  X, sexp, deg_per_baryon * pt.A, 1.0 / pt.norm,
                                                                  Cb + (int64_t)pt.c0 * W);
@@ -645,6 +658,7 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
         wv.v3 = F.lx * F.ly * F.lz;
         wv.v3p = v3p;
         wv.n_items = n_items;
+        note_launch();
         k_large_blocks<Tr><<<W / 16, 512, blk_smem, stream>>>(F, wv, nrow, nxi, n_g2(L), (int)L->block_size,
                                                               (int)binom64(nxi, 2), L->need_block[0],
                                                               L->need_block[1], fP, fN, sexp);
@@ -662,6 +676,7 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
         }
         {
             int64_t groups = std::min<int64_t>(W, n_items - item0) / 32;
+            note_launch();
             k_large_sitesum<<<(unsigned)groups, 256, 0, stream>>>(F, wv, M, L->n_comp, phase, Cb, partial);
             MBC_CUDA_TRY(cudaGetLastError());
         }
@@ -714,6 +729,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)nsm * 8));
         {
             TimedLaunch tl(stream);
+            note_launch();
             k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nrow, nxi, n_g2(L), bs,
                                                                     (int)binom64(nxi, 2), L->need_block[0],
                                                                     L->need_block[1], tps, n_tiles, partial);
@@ -721,6 +737,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         MBC_CUDA_TRY(cudaGetLastError());
         const int64_t outs = n_slabs * M.n_mom * n_out;
         const unsigned rg = (unsigned)std::min<int64_t>((outs + 7) / 8, 65535);
+        note_launch();
         k_reduce_tiles<<<std::max(rg, 1u), 256, 0, stream>>>(partial, n_slabs, tps, M.n_mom, (int)n_out, F.n_t, 0, 1,
                                                             (int)n_out, Pf);
         MBC_CUDA_TRY(cudaGetLastError());
@@ -729,6 +746,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
     const int64_t n_items = n_slabs * n_groups;
     const int per_spin = (int)(binom64(nxi, 2) * nxi);
     for (int64_t item0 = 0; item0 < n_items; item0 += W) {
+        note_launch();
         k_load_proj_blocks<Tr><<<(unsigned)((W + 7) / 8), 256, 0, stream>>>(Pf, n_items, item0, W, bs, per_spin, n_k,
                                                                             M.n_mom, fP, fN, sexp);
         MBC_CUDA_TRY(cudaGetLastError());
@@ -746,6 +764,7 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         {
             const int64_t tot = (int64_t)L->n_comp * W;
             const unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 65535));
+            note_launch();
             k_write_items<<<g2, 256, 0, stream>>>(Cb, n_items, item0, W, L->n_comp, n_groups, F.n_t, li, n_lists,
                                                   comp_max, out);
             MBC_CUDA_TRY(cudaGetLastError());
@@ -982,6 +1001,7 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
         if ((st = scratch_get(device, stream, phase_bytes_p + need, &scr_p)) != MBC_OK) return st;
         double2 *phase_p = reinterpret_cast<double2 *>(scr_p);
         unsigned pg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((v3 * M.n_mom + 255) / 256, 4096));
+        note_launch();
         k_phase_table<<<pg, 256, 0, stream>>>(F, M, phase_p);
         MBC_CUDA_TRY(cudaGetLastError());
         for (int li = 0; li < n_lists; ++li) {
@@ -1080,6 +1100,7 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     double2 *phase = reinterpret_cast<double2 *>(scr);
     {
         unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((v3 * M.n_mom + 255) / 256, 4096));
+        note_launch();
         k_phase_table<<<grid, 256, 0, stream>>>(F, M, phase);
         MBC_CUDA_TRY(cudaGetLastError());
     }
@@ -1088,6 +1109,7 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
         const mbc_term_list *L = lists[li];
         int64_t outs = n_slabs * M.n_mom * L->n_comp;
         unsigned grid = (unsigned)std::min<int64_t>((outs + 7) / 8, 65535);
+        note_launch();
         k_reduce_tiles<<<std::max(grid, 1u), 256, 0, stream>>>(partial, n_slabs, tiles_per_slab, M.n_mom, L->n_comp,
                                                               n_t, li, n_lists, comp_max,
                                                               reinterpret_cast<double2 *>(dev_out));
@@ -1334,6 +1356,7 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     // every phase-table entry and every tile partial is written before it is
     // read; the work counter is set to zero below
     unsigned pgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((v3 * M.n_mom + 255) / 256, 4096));
+    note_launch();
     k_phase_table<<<pgrid, 256, 0, stream>>>(F, M, phase);
     MBC_CUDA_TRY(cudaGetLastError());
     SmallBatch B;
@@ -1349,9 +1372,12 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     if ((st = launch_small_batch(B, F, M, l, false, device, stream, phase, partial, false)) != MBC_OK) return st;
     const int64_t outs = n_slabs * M.n_mom * list->n_comp;
     const unsigned rgrid = (unsigned)std::min<int64_t>((outs + 7) / 8, 65535);
+    note_launch();
     k_reduce_tiles<<<std::max(rgrid, 1u), 256, 0, stream>>>(partial, n_slabs, B.tiles_per_slab, M.n_mom,
                                                             list->n_comp, n_t, 0, 1, comp_max,
                                                             reinterpret_cast<double2 *>(out));
     MBC_CUDA_TRY(cudaGetLastError());
     return MBC_OK;
 }
+
+extern "C" int64_t mbc_kernel_launches(void) { return mbc::g_kernel_launches.load(std::memory_order_relaxed); }
