@@ -61,21 +61,6 @@ struct MixedTraits {
             kahan(sr, cr, __fmaf_rn(xr, y.x, -__fmul_rn(xi, y.y)));
             kahan(si, ci, __fmaf_rn(xr, y.y, __fmul_rn(xi, y.x)));
         }
-        // A short run of terms summed with plain FP32 FMAs (exact products,
-        // one rounding per FMA) before it joins the compensated sum: the
-        // run's error is a few units in the last place of its own terms.
-        __device__ __forceinline__ static void part_fma(float &pr, float &pi, float2 x, float2 y, uint32_t neg) {
-            const float xr = __int_as_float(__float_as_int(x.x) ^ (int)neg);
-            const float xi = __int_as_float(__float_as_int(x.y) ^ (int)neg);
-            pr = __fmaf_rn(xr, y.x, pr);
-            pr = __fmaf_rn(-xi, y.y, pr);
-            pi = __fmaf_rn(xr, y.y, pi);
-            pi = __fmaf_rn(xi, y.x, pi);
-        }
-        __device__ __forceinline__ void flush(float pr, float pi) {
-            kahan(sr, cr, pr);
-            kahan(si, ci, pi);
-        }
         // combine with another accumulator (s2 - c2): two-sum of the sums
         __device__ __forceinline__ void add(float s2r, float c2r, float s2i, float c2i) {
             float s, e;

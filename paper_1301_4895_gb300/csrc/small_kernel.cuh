@@ -455,20 +455,10 @@ __global__ void __launch_bounds__(1024, 1)
                 for (int b0 = 0; b0 < len; b0 += 32) {
                     const int nb = min(32, len - b0);
                     const uint32_t mine = lane < nb ? __ldg(op_ptr + b0 + lane) : 0u;
-                    // runs of kRun terms in plain FP32 FMAs, each run added to
-                    // the compensated sum (nb is warp-uniform)
-                    constexpr int kRun = 4;
-                    for (int q0 = 0; q0 < nb; q0 += kRun) {
-                        float pr = 0.f, pi = 0.f;
-#pragma unroll
-                        for (int g = 0; g < kRun; ++g) {
-                            if (q0 + g < nb) {
-                                const uint32_t op = __shfl_sync(full, mine, q0 + g);
-                                Tr::Acc::part_fma(pr, pi, Xl[(op & 0xffffu) << 5], Yl[((op >> 16) & 0x7fffu) << 5],
-                                                  op & 0x80000000u);
-                            }
-                        }
-                        acc.flush(pr, pi);
+#pragma unroll 4
+                    for (int q = 0; q < nb; ++q) {
+                        const uint32_t op = __shfl_sync(full, mine, q);
+                        acc.fma(Xl[(op & 0xffffu) << 5], Yl[((op >> 16) & 0x7fffu) << 5], op & 0x80000000u);
                     }
                 }
                 if (part < 0) {
