@@ -166,6 +166,12 @@ class TermList:
         return self.status == 2
 
     def stats(self) -> dict:
+        """``mbc_term_list_stats`` as a dict (a list never changes: read once)."""
+        if getattr(self, "_stats", None) is None:
+            self._stats = self._read_stats()
+        return {k: list(v) if isinstance(v, list) else v for k, v in self._stats.items()}
+
+    def _read_stats(self) -> dict:
         st = ListStats()
         _check(self._lib.mbc_term_list_stats(self._h, ctypes.byref(st)), "mbc_term_list_stats")
         A = st.A

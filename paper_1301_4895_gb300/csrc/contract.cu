@@ -28,6 +28,7 @@ inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_rel
 #include "probe.cuh"
 #include "project_kernel.cuh"
 #include "small_kernel.cuh"
+#include "small_ls_kernel.cuh"
 
 namespace mbc {
 
@@ -99,6 +100,7 @@ void place(std::vector<Interval *> &bufs) {
 struct DeviceCache {
     int device = -1;
     bool small_ok = false;
+    bool ls_ok = false;      // the lanes-are-sites (mixed) kernel can take the list
     SmallPlan sp{};          // device pointers filled in
     int64_t site_entries = 0;
     uint32_t *d_small_ops = nullptr;
@@ -298,13 +300,20 @@ DeviceCache *get_cache(const mbc_term_list *Lc, int device, mbc_status &st) {
             free_cache(c);
             return nullptr;
         }
-        // lanes-are-sites layout: z-major
+        // lanes-are-sites layout: z-major, operands as byte offsets of their
+        // 256 B shared-memory rows (x << 8 | sign in bit 0 | y << 24), which
+        // needs every stage and block index below 256 (all nonrelativistic
+        // lists); otherwise the mixed path takes the wave kernels
         std::vector<uint32_t> zpk;
+        c->ls_ok = true;
         for (size_t m = 0; m < L->steps.size(); ++m) {
             const Step &s = L->steps[m];
             c->sp.step[m].zop_off = (int64_t)zpk.size();
-            for (size_t i = 0; i < s.x.size(); ++i)
-                zpk.push_back(s.x[i] | ((uint32_t)(s.ys[i] & 0x7fffu) << 16) | ((uint32_t)(s.ys[i] >> 15) << 31));
+            for (size_t i = 0; i < s.x.size(); ++i) {
+                const uint32_t x = s.x[i], y = s.ys[i] & 0x7fffu, sg = (uint32_t)(s.ys[i] >> 15);
+                if (x >= 256 || y >= 256) c->ls_ok = false;
+                zpk.push_back((x & 0xffu) << 8 | sg | (y & 0xffu) << 24);
+            }
         }
         if ((st = upload(&c->d_small_zops, zpk.data(), zpk.size())) != MBC_OK) {
             free_cache(c);
@@ -924,7 +933,10 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     for (int i = 0; i < n_lists; ++i) comp_max = std::max(comp_max, (int)lists[i]->n_comp);
     const int n_t = t1 - t0;
     const size_t out_bytes = (size_t)props->n_cfg * n_lists * n_t * n_out_mom * comp_max * sizeof(double2);
-    if (props->memory == MBC_MEM_HOST && n_t >= 2)
+    // overlapping copies pays once the field is large enough for chunks of
+    // several MB; smaller fields are staged in one copy
+    const size_t field_bytes = (size_t)props->n_cfg * n_t * v3 * site_elems * (props->dtype == MBC_C128 ? 16 : 8);
+    if (props->memory == MBC_MEM_HOST && n_t >= 2 && field_bytes >= ((size_t)32 << 20))
         return contract_host_pipelined(props, lists, n_lists, opts, out, stream, t0, n_t, stride_cfg, stride_t,
                                        site_elems, n_out_mom, comp_max);
 
@@ -1028,7 +1040,7 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
         if (L->pauli_forbidden || L->n_comp == 0) continue;  // identically zero
         caches[(size_t)li] = get_cache(L, device, st);
         if (!caches[(size_t)li]) return st;
-        bool small = caches[(size_t)li]->small_ok && regime != 2;
+        bool small = caches[(size_t)li]->small_ok && (!mixed || caches[(size_t)li]->ls_ok) && regime != 2;
         if (small) {  // the list alone must fit the shared-memory kernel
             int32_t ss, cs;
             small = size_small_batch({caches[(size_t)li]}, F, opts->tune, mixed, ss, cs).ok;

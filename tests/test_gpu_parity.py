@@ -115,18 +115,19 @@ def test_host_memory_mode_and_determinism(mbc):
     chunks, copies overlapping the contraction) repeat bitwise and agree with
     the device call up to the summation order of the site sums (the chunks
     change the launch shape), also on a sub-range of time slices."""
-    dims = (4, 4, 4)
-    field = synth.field(5, 2, 5, dims, 0.4)
     lists = [mbc.build_term_list(1, 1, 2), mbc.build_term_list(2, 2, 2), mbc.build_term_list(2, 1, 2)]
-    for p in (0, 1):
-        for t0, t1 in ((0, 0), (1, 4)):
-            a = run(mbc, field, lists, p, t0=t0, t1=t1)
-            b = run(mbc, field, lists, p, t0=t0, t1=t1)
-            h = mbc.contract(field, lists, precision=p, t0=t0, t1=t1)
-            h2 = mbc.contract(field, lists, precision=p, t0=t0, t1=t1)
-            assert np.array_equal(a, b) and np.array_equal(h, h2)
-            scale = np.max(np.abs(a), axis=(2, 3, 4), keepdims=True) + 1e-300
-            assert float(np.max(np.abs(h - a) / scale)) <= 1e-12, (p, t0, t1)
+    # a small field is staged in one copy, a 113 MB one in overlapped chunks
+    for dims, n_cfg, nt in (((4, 4, 4), 2, 5), ((16, 16, 16), 2, 6)):
+        field = synth.field(5, n_cfg, nt, dims, 0.4)
+        for p in (0, 1):
+            for t0, t1 in ((0, 0), (1, nt - 1)):
+                a = run(mbc, field, lists, p, t0=t0, t1=t1)
+                b = run(mbc, field, lists, p, t0=t0, t1=t1)
+                h = mbc.contract(field, lists, precision=p, t0=t0, t1=t1)
+                h2 = mbc.contract(field, lists, precision=p, t0=t0, t1=t1)
+                assert np.array_equal(a, b) and np.array_equal(h, h2)
+                scale = np.max(np.abs(a), axis=(2, 3, 4), keepdims=True) + 1e-300
+                assert float(np.max(np.abs(h - a) / scale)) <= 1e-12, (dims, p, t0, t1)
 
 
 def test_pauli_forbidden_list_is_zero(mbc):
