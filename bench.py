@@ -209,11 +209,19 @@ def cpu_model() -> str:
             info = f.read()
     except OSError:
         return "unknown"
-    for key in ("model name", "Model", "CPU part"):
-        for line in info.splitlines():
-            if line.startswith(key) and ":" in line:
-                return line.split(":", 1)[1].strip()
-    return "unknown"
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    if "model name" in fields:
+        return fields["model name"]
+    # Arm: implementer and part numbers (Neoverse V2 is the Grace core)
+    parts = {"0xd4f": "Neoverse V2", "0xd40": "Neoverse V1", "0xd0c": "Neoverse N1", "0xd8e": "Neoverse N3"}
+    if "CPU part" in fields:
+        part = fields["CPU part"]
+        return f"Arm {parts.get(part, 'core')} (implementer {fields.get('CPU implementer', '?')}, part {part})"
+    return fields.get("Model", "unknown")
 
 
 def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0):

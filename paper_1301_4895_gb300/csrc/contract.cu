@@ -72,6 +72,35 @@ int pick_group(int64_t n_z, int64_t k, double c_op = 4.0, double c_level = 2.0) 
     return best;
 }
 
+// Warp-per-site step layout: n_main outputs (whole rounds of 32 / g) with g
+// lanes each and the remaining n_z - n_main with g2 lanes each, chosen by the
+// same FP64 instruction cost as pick_group.
+void split_groups(int64_t n_z, int64_t k, int32_t &g, int32_t &n_main, int32_t &g2) {
+    auto cost = [&](int64_t n, int gg) {
+        if (n <= 0) return 0.0;
+        int lg = 0;
+        while ((1 << lg) < gg) ++lg;
+        const int64_t per = 32 / gg, rounds = (n + per - 1) / per, kk = (k + gg - 1) / gg;
+        return (double)rounds * ((double)kk * 4.0 + lg * 2.0);
+    };
+    g = pick_group(n_z, k);
+    n_main = (int32_t)n_z;
+    g2 = g;
+    double best = cost(n_z, g);
+    for (int g1 = 1; g1 <= 32; g1 <<= 1) {
+        const int64_t per = 32 / g1, nm = n_z / per * per;
+        if (nm == n_z || nm == 0) continue;
+        const int gt = pick_group(n_z - nm, k);
+        const double c = cost(nm, g1) + cost(n_z - nm, gt);
+        if (c < best - 1e-9) {
+            best = c;
+            g = g1;
+            n_main = (int32_t)nm;
+            g2 = gt;
+        }
+    }
+}
+
 struct Interval {
     int start, end;
     int64_t size, off;
@@ -217,7 +246,7 @@ bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries, std
         SmallStepDesc &d = P.step[m - 1];
         d.n_z = (int)s.n_z;
         d.k = (int)s.k;
-        d.g = pick_group(s.n_z, s.k);
+        split_groups(s.n_z, s.k, d.g, d.n_main, d.g2);
         d.x_off = m == 1 ? P.blk_off[L->path[0]] : (int)stage[(size_t)m].off;
         d.y_off = P.blk_off[s.baryon];
         d.z_off = (int)stage[(size_t)m + 1].off;
@@ -280,21 +309,27 @@ DeviceCache *get_cache(const mbc_term_list *Lc, int device, mbc_status &st) {
             free_cache(c);
             return nullptr;
         }
-        // per step: [round j][z][sub], padded to a whole number of rounds
+        // per step and part (outputs [0, n_main) with g lanes, the rest with
+        // g2): [round j][z][sub], padded to a whole number of rounds
         std::vector<uint32_t> packed;
         for (size_t m = 0; m < L->steps.size(); ++m) {
             const Step &s = L->steps[m];
             SmallStepDesc &d = c->sp.step[m];
-            d.op_off = (int64_t)packed.size();
-            const int64_t g = d.g, kk = (s.k + g - 1) / g;
-            packed.resize(packed.size() + (size_t)(kk * s.n_z * g), 0u);
-            uint32_t *dst = packed.data() + d.op_off;
-            for (int64_t z = 0; z < s.n_z; ++z)
-                for (int64_t j = 0; j < s.k; ++j) {
-                    size_t i = (size_t)(z * s.k + j);
-                    uint32_t op = s.x[i] | ((uint32_t)(s.ys[i] & 0x7fffu) << 16) | ((uint32_t)(s.ys[i] >> 15) << 31);
-                    dst[((j / g) * s.n_z + z) * g + (j % g)] = op;
-                }
+            auto pack = [&](int64_t z_begin, int64_t n, int64_t g) {
+                const int64_t off = (int64_t)packed.size(), kk = (s.k + g - 1) / g;
+                packed.resize(packed.size() + (size_t)(kk * n * g), 0u);
+                uint32_t *dst = packed.data() + off;
+                for (int64_t zl = 0; zl < n; ++zl)
+                    for (int64_t j = 0; j < s.k; ++j) {
+                        const size_t i = (size_t)((z_begin + zl) * s.k + j);
+                        const uint32_t op =
+                            s.x[i] | ((uint32_t)(s.ys[i] & 0x7fffu) << 16) | ((uint32_t)(s.ys[i] >> 15) << 31);
+                        dst[((j / g) * n + zl) * g + (j % g)] = op;
+                    }
+                return off;
+            };
+            d.op_off = pack(0, d.n_main, d.g);
+            d.op_off2 = pack(d.n_main, s.n_z - d.n_main, d.g2);
         }
         if ((st = upload(&c->d_small_ops, packed.data(), packed.size())) != MBC_OK) {
             free_cache(c);

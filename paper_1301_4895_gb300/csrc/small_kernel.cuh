@@ -26,8 +26,11 @@ constexpr int kSmallMaxComp = 64;
 
 struct SmallStepDesc {
     int32_t n_z, k, g, x_off, y_off, z_off;
-    int64_t op_off;   // warp-per-site layout [round][z][sub-lane]
+    int64_t op_off;   // warp-per-site layout [round][z][sub-lane]: outputs [0, n_main) with g lanes each
     int64_t zop_off;  // lanes-are-sites layout: z-major, k ops per z
+    int32_t n_main;   // outputs in whole rounds of 32 / g; the rest take g2 lanes each
+    int32_t g2;
+    int64_t op_off2;  // the rest's ops, [round][z - n_main][sub-lane] with g2
 };
 
 struct SmallPlan {
@@ -124,29 +127,23 @@ __device__ __forceinline__ double2 mom_phase(const int32_t *n, int x, int y, int
     return make_double2(c, s);
 }
 
-// Ops of a step are stored as [round j][z][sub-lane]: in round j the g lanes
-// of output z read ops j*g + sub, so a warp reads 32 consecutive words.
+// Outputs [z_begin, z_begin + n) of a step with g lanes per output. Their ops
+// are stored as [round j][z - z_begin][sub-lane]: in round j the g lanes of
+// output z read ops j*g + sub, so a warp reads 32 consecutive words.
 template <class Tr>
-__device__ __forceinline__ void small_step(const SmallPlan &P, const SmallStepDesc &d, typename Tr::V *R,
-                                           int lane) {
-    using V = typename Tr::V;
-    const V *X = R + d.x_off;
-    const V *Y = R + d.y_off;
-    V *Z = R + d.z_off;
-    const uint32_t *ops = P.ops + d.op_off;
-    const int g = d.g;                 // lanes per z (power of two)
+__device__ __forceinline__ void small_step_part(const typename Tr::V *X, const typename Tr::V *Y, typename Tr::V *Z,
+                                                const uint32_t *ops, int z_begin, int n, int k, int g, int lane) {
     const int per = 32 / g;            // z per round
     const int sub = lane & (g - 1);
-    const int64_t round_stride = (int64_t)d.n_z * g;
+    const int rs = n * g;              // words per round
     const unsigned full = 0xffffffffu;
-    for (int z0 = 0; z0 < d.n_z; z0 += per) {
-        int z = z0 + lane / g;
+    for (int z0 = 0; z0 < n; z0 += per) {
+        const int zl = z0 + lane / g;
         typename Tr::Acc acc;
         acc.zero();
-        if (z < d.n_z) {
-            const uint32_t *oz = ops + z * g + sub;
-            const int rs = (int)round_stride;
-            const int jfull = (d.k - sub + g - 1) / g;  // rounds in which this lane has an op
+        if (zl < n) {
+            const uint32_t *oz = ops + zl * g + sub;
+            const int jfull = (k - sub + g - 1) / g;  // rounds in which this lane has an op
 #pragma unroll 4
             for (int j = 0; j < jfull; ++j) {
                 uint32_t op = __ldg(oz + j * rs);
@@ -154,8 +151,22 @@ __device__ __forceinline__ void small_step(const SmallPlan &P, const SmallStepDe
             }
         }
         for (int off = g >> 1; off > 0; off >>= 1) acc.add_shfl(full, off);
-        if (z < d.n_z && sub == 0) Z[z] = acc.store();
+        if (zl < n && sub == 0) Z[z_begin + zl] = acc.store();
     }
+}
+
+// One step for one site: whole rounds of the outputs with g lanes each, then
+// the remaining outputs with g2 lanes each (fewer idle lanes in the last round).
+template <class Tr>
+__device__ __forceinline__ void small_step(const SmallPlan &P, const SmallStepDesc &d, typename Tr::V *R,
+                                           int lane) {
+    using V = typename Tr::V;
+    const V *X = R + d.x_off;
+    const V *Y = R + d.y_off;
+    V *Z = R + d.z_off;
+    small_step_part<Tr>(X, Y, Z, P.ops + d.op_off, 0, d.n_main, d.k, d.g, lane);
+    if (d.n_main < d.n_z)
+        small_step_part<Tr>(X, Y, Z, P.ops + d.op_off2, d.n_main, d.n_z - d.n_main, d.k, d.g2, lane);
     __syncwarp();
 }
 
