@@ -555,9 +555,10 @@ LargeSizes large_sizes(const mbc_term_list *L, const DeviceCache *c, const mbc_t
     const int64_t budget = 8LL << 30;
     int64_t W = budget / per_site;
     if (tune && tune->wave_sites > 0) W = tune->wave_sites;
-    W = std::max<int64_t>(32, std::min<int64_t>(W, 4096));
-    W = std::min<int64_t>(W, (n_items + 31) / 32 * 32);
-    W = std::max<int64_t>(32, W / 32 * 32);
+    // multiples of 64 sites: the mixed step kernel covers 64 sites per warp
+    W = std::max<int64_t>(64, std::min<int64_t>(W, 4096));
+    W = std::min<int64_t>(W, (n_items + 63) / 64 * 64);
+    W = std::max<int64_t>(64, W / 64 * 64);
     s.W = (int)W;
     s.blk_bytes = (size_t)(L->block_size * W) * sizeof(V);
     s.stage_bytes = (size_t)(std::max<int64_t>(c->max_stage, 1) * W) * sizeof(V);
@@ -620,6 +621,26 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
             note_launch();
             k_large_step_gen<Tr><<<(unsigned)grid, 256, smem, stream>>>(gen_step(L, c, m), s.n_z, s.k, zchunk, zb, W,
                                                                         X, Y, Z);
+        }
+        MBC_CUDA_TRY(cudaGetLastError());
+        return MBC_OK;
+    }
+    if (!gen && sizeof(typename Tr::V) == sizeof(float2) && W % 64 == 0 && !(tune && tune->wave_order == 1)) {
+        // mixed precision, stored operations: two sites per lane
+        const int threads = 256;
+        const int64_t total_warps = (int64_t)nsm * 8 * (threads / 32);
+        const int64_t ngroups = W / 64;
+        int64_t zchunk = (s.n_z * ngroups + 8 * total_warps - 1) / (8 * total_warps);
+        zchunk = std::max<int64_t>(1, std::min<int64_t>(zchunk, 256));
+        if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
+        const int64_t items = ((s.n_z + zchunk - 1) / zchunk) * ngroups;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
+        {
+            TimedLaunch tl(stream);
+            note_launch();
+            k_large_step_mx2<<<(unsigned)grid, threads, 0, stream>>>(
+                c->d_opx[m], c->d_opy[m], s.n_z, s.k, zchunk, W, reinterpret_cast<const float2 *>(X),
+                reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
         }
         MBC_CUDA_TRY(cudaGetLastError());
         return MBC_OK;

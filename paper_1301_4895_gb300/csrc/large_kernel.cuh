@@ -190,6 +190,71 @@ __global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__
     }
 }
 
+// The mixed-precision step with two sites per lane: a warp covers 64
+// consecutive sites of the wave, every gather is one 16 B load per lane
+// (a 512 B row segment per warp), so the operand decoding and broadcast of
+// each operation is shared by twice the sites and twice the bytes are in
+// flight per load instruction. W must be a multiple of 64.
+__global__ void __launch_bounds__(256) k_large_step_mx2(const uint32_t *__restrict__ opx,
+                                                        const uint16_t *__restrict__ opy, int64_t n_z, int64_t k,
+                                                        int64_t zchunk, int W, const float2 *__restrict__ X,
+                                                        const float2 *__restrict__ Y, float2 *__restrict__ Z) {
+    using Acc = MixedTraits::Acc;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int ngroups = W >> 6;
+    const int64_t nchunks = (n_z + zchunk - 1) / zchunk;
+    const int W4 = W >> 1;  // a row in float4 units (two sites each)
+    for (int64_t item = warp_global; item < nchunks * ngroups; item += nwarps) {
+        const int64_t chunk = item / ngroups;
+        const int group = (int)(item % ngroups);
+        const int col4 = group * 32 + lane;  // float4 column: sites 2 col4, 2 col4 + 1
+        const float4 *Xc = reinterpret_cast<const float4 *>(X) + col4;
+        const float4 *Yc = reinterpret_cast<const float4 *>(Y) + col4;
+        const int64_t z_begin = chunk * zchunk;
+        const int64_t z_end = min(n_z, z_begin + zchunk);
+        for (int64_t z = z_begin; z < z_end; ++z) {
+            Acc a0, a1;
+            a0.zero();
+            a1.zero();
+            const uint32_t *ox = opx + z * k;
+            const uint16_t *oy = opy + z * k;
+            for (int64_t b0 = 0; b0 < k; b0 += 32) {
+                const int nb = (int)min((int64_t)32, k - b0);
+                uint32_t mx = 0, my = 0;
+                if (lane < nb) {
+                    mx = __ldg(ox + b0 + lane);
+                    my = __ldg(oy + b0 + lane);
+                }
+                constexpr int G = 2;
+                for (int t0 = 0; t0 < nb; t0 += G) {
+                    float4 xv[G], yv[G];
+                    uint32_t sg[G];
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const uint32_t x = __shfl_sync(0xffffffffu, mx, (t0 + g) & 31);
+                        const uint32_t y = __shfl_sync(0xffffffffu, my, (t0 + g) & 31);
+                        if (t0 + g < nb) {
+                            xv[g] = __ldg(Xc + (int64_t)x * W4);
+                            yv[g] = __ldg(Yc + (int64_t)(y & 0x7fffu) * W4);
+                        }
+                        sg[g] = (y & 0x8000u) << 16;
+                    }
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+                        if (t0 + g < nb) {
+                            a0.fma(make_float2(xv[g].x, xv[g].y), make_float2(yv[g].x, yv[g].y), sg[g]);
+                            a1.fma(make_float2(xv[g].z, xv[g].w), make_float2(yv[g].z, yv[g].w), sg[g]);
+                        }
+                }
+            }
+            const float2 r0 = a0.store(), r1 = a1.store();
+            reinterpret_cast<float4 *>(Z + z * W)[col4] = make_float4(r0.x, r0.y, r1.x, r1.y);
+        }
+    }
+}
+
 // The same step with the operations regenerated once per CTA (the mixed
 // path's choice for list-free lists). A CTA of 8 warps takes a z chunk and 8 consecutive
 // 32-site groups; for zb outputs at a time its 256 threads regenerate the
