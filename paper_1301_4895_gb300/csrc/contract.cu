@@ -604,7 +604,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
     if (gen && sizeof(typename Tr::V) == sizeof(float2)) {
         // CTA-shared regeneration: zb outputs' operations per round in shared memory
         const size_t per_z = (size_t)s.k * (sizeof(uint32_t) + sizeof(uint16_t));
-        const int64_t nblk = (W / 32 + 7) / 8;
+        const int64_t nblk = (W / 64 + 7) / 8;
         const int64_t target = (int64_t)nsm * 3 * 8;
         int64_t nchunks = std::max<int64_t>(1, std::min<int64_t>(s.n_z, (target + nblk - 1) / nblk));
         int64_t zchunk = (s.n_z + nchunks - 1) / nchunks;
@@ -613,14 +613,16 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         const int zb = (int)std::max<int64_t>(1, std::min<int64_t>(zchunk, (int64_t)((64u << 10) / per_z)));
         const size_t smem = (size_t)zb * per_z + 16;
         int per_sm = 0;
-        mbc_status pst = prepare_kernel((const void *)k_large_step_gen<Tr>, c->device, 256, smem, &per_sm);
+        mbc_status pst = prepare_kernel((const void *)k_large_step_gen, c->device, 256, smem, &per_sm);
         if (pst != MBC_OK) return pst;
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nchunks * nblk, (int64_t)nsm * std::max(per_sm, 1) * 4));
         {
             TimedLaunch tl(stream);
             note_launch();
-            k_large_step_gen<Tr><<<(unsigned)grid, 256, smem, stream>>>(gen_step(L, c, m), s.n_z, s.k, zchunk, zb, W,
-                                                                        X, Y, Z);
+            k_large_step_gen<<<(unsigned)grid, 256, smem, stream>>>(gen_step(L, c, m), s.n_z, s.k, zchunk, zb, W,
+                                                                    reinterpret_cast<const float2 *>(X),
+                                                                    reinterpret_cast<const float2 *>(Y),
+                                                                    reinterpret_cast<float2 *>(Z));
         }
         MBC_CUDA_TRY(cudaGetLastError());
         return MBC_OK;

@@ -255,31 +255,32 @@ __global__ void __launch_bounds__(256) k_large_step_mx2(const uint32_t *__restri
     }
 }
 
-// The same step with the operations regenerated once per CTA (the mixed
-// path's choice for list-free lists). A CTA of 8 warps takes a z chunk and 8 consecutive
-// 32-site groups; for zb outputs at a time its 256 threads regenerate the
-// outputs' operations once into shared memory, then every warp runs them on
-// its site group exactly as k_large_step runs the stored words (same order,
-// same arithmetic), so the integer work is shared by the CTA's 256 sites.
-template <class Tr>
+// The mixed step with the operations regenerated once per CTA (the mixed
+// path's choice for list-free lists). A CTA of 8 warps takes a z chunk and 8
+// consecutive groups of 64 sites (two per lane, as k_large_step_mx2); for zb
+// outputs at a time its 256 threads regenerate the outputs' operations once
+// into shared memory, then every warp runs them on its sites exactly as the
+// stored words would run (same order, same arithmetic), so the integer work
+// is shared by the CTA's 512 sites. W must be a multiple of 64.
 __global__ void __launch_bounds__(256, 3) k_large_step_gen(GenStep gs, int64_t n_z, int64_t k, int64_t zchunk, int zb,
-                                                        int W, const typename Tr::V *__restrict__ X,
-                                                        const typename Tr::V *__restrict__ Y,
-                                                        typename Tr::V *__restrict__ Z) {
+                                                           int W, const float2 *__restrict__ X,
+                                                           const float2 *__restrict__ Y, float2 *__restrict__ Z) {
+    using Acc = MixedTraits::Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *sx = reinterpret_cast<uint32_t *>(smem_raw);  // [zb][k]
     uint16_t *sy = reinterpret_cast<uint16_t *>(sx + (int64_t)zb * k);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ngroups = W >> 5;
+    const int ngroups = W >> 6;
     const int nblk = (ngroups + 7) / 8;
+    const int W4 = W >> 1;  // a row in float4 units (two sites each)
     const int64_t nchunks = (n_z + zchunk - 1) / zchunk;
     for (int64_t item = blockIdx.x; item < nchunks * nblk; item += gridDim.x) {
         const int64_t chunk = item / nblk;
         const int group = (int)(item % nblk) * 8 + warp;
         const bool active = group < ngroups;
-        const int col = group * 32 + lane;
-        const typename Tr::V *Xc = X + (active ? col : 0);
-        const typename Tr::V *Yc = Y + (active ? col : 0);
+        const int col4 = (active ? group : 0) * 32 + lane;
+        const float4 *Xc = reinterpret_cast<const float4 *>(X) + col4;
+        const float4 *Yc = reinterpret_cast<const float4 *>(Y) + col4;
         const int64_t z_begin = chunk * zchunk;
         const int64_t z_end = min(n_z, z_begin + zchunk);
         for (int64_t zr = z_begin; zr < z_end; zr += zb) {
@@ -298,28 +299,33 @@ __global__ void __launch_bounds__(256, 3) k_large_step_gen(GenStep gs, int64_t n
             __syncthreads();
             if (!active) continue;
             for (int q = 0; q < nzr; ++q) {
-                typename Tr::Acc acc;
-                acc.zero();
+                Acc a0, a1;
+                a0.zero();
+                a1.zero();
                 const uint32_t *ox = sx + q * k;
                 const uint16_t *oy = sy + q * k;
-                constexpr int G = sizeof(typename Tr::V) == 8 ? 4 : 2;
+                constexpr int G = 2;
                 for (int64_t t0 = 0; t0 < k; t0 += G) {
-                    typename Tr::V xv[G], yv[G];
+                    float4 xv[G], yv[G];
                     uint32_t sg[G];
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
                         if (t0 + g < k) {
                             const uint32_t x = ox[t0 + g], y = oy[t0 + g];
-                            xv[g] = __ldg(Xc + (int64_t)x * W);
-                            yv[g] = __ldg(Yc + (int64_t)(y & 0x7fffu) * W);
+                            xv[g] = __ldg(Xc + (int64_t)x * W4);
+                            yv[g] = __ldg(Yc + (int64_t)(y & 0x7fffu) * W4);
                             sg[g] = (y & 0x8000u) << 16;
                         }
                     }
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        if (t0 + g < k) acc.fma(xv[g], yv[g], sg[g]);
+                        if (t0 + g < k) {
+                            a0.fma(make_float2(xv[g].x, xv[g].y), make_float2(yv[g].x, yv[g].y), sg[g]);
+                            a1.fma(make_float2(xv[g].z, xv[g].w), make_float2(yv[g].z, yv[g].w), sg[g]);
+                        }
                 }
-                Z[(zr + q) * W + col] = acc.store();
+                const float2 r0 = a0.store(), r1 = a1.store();
+                reinterpret_cast<float4 *>(Z + (zr + q) * W)[col4] = make_float4(r0.x, r0.y, r1.x, r1.y);
             }
         }
     }
