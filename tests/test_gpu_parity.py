@@ -431,6 +431,29 @@ def test_two_quark_sources(mbc, n_p, n_n, spins):
     assert np.array_equal(host, dev)
 
 
+def test_two_sources_two_sinks_full_slab(mbc):
+    """The two-source workload of the benchmark (4He nonrelativistic, two
+    sink functions, 36 sink components x source spins (0,2,0,2), seed 5) on
+    one full 16^3 slab, in the benchmark's launch configuration, against the
+    oracle's grouped projected blocks."""
+    from oracle import gamma, projection, recursion
+    dims = (16, 16, 16)
+    field = synth.field(5, 1, 1, dims, 0.4, n_src=2)
+    pairs = ((0, 1), (0, 2), (1, 2), (0, 3), (1, 3), (2, 3))
+    spins = [(p + q, (0, 2, 0, 2)) for p in pairs for q in pairs]
+    moms = ((0, 0, 0), (1, 0, 0))
+    tl = mbc.build_term_list(2, 2, 2, spins=spins, n_sources=2, n_sinks=2)
+    comps = tl.components()
+    plan = recursion.Plan(2, 2, 2, requests=comps, G=gamma.g_tensor_sources(2, 2), G_sink=gamma.g_tensor(2))
+    ref, scale = projection.projected_correlators(plan, recursion.source_columns(field[0, 0], 2), dims, moms,
+                                                  n_sinks=2, dirac_dim=2)
+    for p in (0, 1):
+        got = run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM)[0, 0, 0, :, : len(comps)]
+        e = float(np.max(np.abs(got - ref) / scale))
+        record("(2,2) D=2 two sources, two sinks 16^3", p, e)
+        assert e <= TOL[p], (p, e)
+
+
 def test_two_quark_sources_larger_slab(mbc):
     """4He, two sources, one 8^3 slab: several waves of the large-stage path."""
     dims = (8, 8, 8)
