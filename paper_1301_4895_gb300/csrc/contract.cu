@@ -862,11 +862,66 @@ using namespace mbc;
 
 namespace {
 
+// Streams and events of the host-memory pipeline, kept per (device, caller
+// stream) like the scratch: a copy stream and two compute streams whose
+// contractions of consecutive chunks may overlap (the tail of one with the
+// start of the next).
+struct Pipe {
+    cudaStream_t copy = nullptr, comp[2] = {nullptr, nullptr};
+    cudaEvent_t start = nullptr, ready[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr},
+                done[2] = {nullptr, nullptr};
+};
+std::mutex g_pipe_mu;
+std::map<std::pair<int, cudaStream_t>, Pipe> g_pipes;
+
+mbc_status get_pipe(int device, cudaStream_t s, Pipe **out) {
+    std::lock_guard<std::mutex> g(g_pipe_mu);
+    auto it = g_pipes.find({device, s});
+    if (it != g_pipes.end()) {
+        *out = &it->second;
+        return MBC_OK;
+    }
+    Pipe p;
+    bool ok = cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaStreamCreateWithFlags(&p.comp[b], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p.ready[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p.used[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p.done[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return MBC_ERR_CUDA;  // the partial set leaks a few handles, the call fails cleanly
+    *out = &(g_pipes[{device, s}] = p);
+    return MBC_OK;
+}
+
+void release_pipes(int device) {
+    std::lock_guard<std::mutex> g(g_pipe_mu);
+    for (auto it = g_pipes.begin(); it != g_pipes.end();) {
+        if (it->first.first != device) {
+            ++it;
+            continue;
+        }
+        Pipe &p = it->second;
+        cudaStreamSynchronize(p.copy);
+        cudaStreamDestroy(p.copy);
+        cudaEventDestroy(p.start);
+        for (int b = 0; b < 2; ++b) {
+            cudaStreamSynchronize(p.comp[b]);
+            cudaStreamDestroy(p.comp[b]);
+            cudaEventDestroy(p.ready[b]);
+            cudaEventDestroy(p.used[b]);
+            cudaEventDestroy(p.done[b]);
+        }
+        it = g_pipes.erase(it);
+    }
+}
+
 // Host-memory mode with the copies overlapped: the evaluated time slices go
-// to the device in chunks through two staging buffers; a second stream copies
-// chunk i + 1 while the caller's stream contracts chunk i (a device-memory
-// call with the same lists and options), and each chunk's results are copied
-// back into their rows of out.
+// to the device in chunks through two staging buffers; the copy stream copies
+// chunk i + 1 while a compute stream contracts chunk i (a device-memory call
+// with the same lists and options), the two compute streams alternating so
+// that consecutive chunks' kernels may overlap, and each chunk's results are
+// copied back into their rows of out.
 mbc_status contract_host_pipelined(const mbc_props *props, const mbc_term_list *const *lists, int32_t n_lists,
                                    const mbc_contract_opts *opts, void *out, cudaStream_t stream, int t0, int n_t,
                                    int64_t stride_cfg, int64_t stride_t, int64_t site_elems, int n_out_mom,
@@ -882,44 +937,47 @@ mbc_status contract_host_pipelined(const mbc_props *props, const mbc_term_list *
     const size_t buf_bytes = (size_t)props->n_cfg * ct * slab_bytes;
     const size_t row_out = (size_t)n_out_mom * comp_max * sizeof(double2);  // one (cfg, list, t)
     const size_t chunk_out = (size_t)props->n_cfg * n_lists * ct * row_out;
+    int device = 0;
+    MBC_CUDA_TRY(cudaGetDevice(&device));
+    Pipe *pp = nullptr;
+    mbc_status st = get_pipe(device, stream, &pp);
+    if (st != MBC_OK) return st;
+    const Pipe &P = *pp;
+    // results gather on the device and go to the host in one copy at the end:
+    // a copy into pageable host memory would hold the host thread until the
+    // chunk is done and serialise the pipeline
+    const size_t full_out = (size_t)props->n_cfg * n_lists * n_t * row_out;
     char *stage = nullptr;
-    MBC_CUDA_TRY(cudaMallocAsync((void **)&stage, 2 * buf_bytes + chunk_out, stream));
+    MBC_CUDA_TRY(cudaMallocAsync((void **)&stage, 2 * buf_bytes + 2 * align256(chunk_out) + align256(full_out), stream));
     char *buf[2] = {stage, stage + buf_bytes};
-    char *cout = stage + 2 * buf_bytes;
-    cudaStream_t cs = nullptr;
-    cudaEvent_t ready[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr}, start = nullptr;
-    mbc_status st = MBC_OK;
+    char *cout[2] = {stage + 2 * buf_bytes, stage + 2 * buf_bytes + align256(chunk_out)};
+    char *dout = stage + 2 * buf_bytes + 2 * align256(chunk_out);
     auto cuda_ok = [&](cudaError_t e) {
         if (e != cudaSuccess && st == MBC_OK) st = MBC_ERR_CUDA;
         return st == MBC_OK;
     };
-    if (cuda_ok(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) &&
-        cuda_ok(cudaEventCreateWithFlags(&start, cudaEventDisableTiming))) {
-        for (int b = 0; b < 2 && st == MBC_OK; ++b) {
-            cuda_ok(cudaEventCreateWithFlags(&ready[b], cudaEventDisableTiming));
-            cuda_ok(cudaEventCreateWithFlags(&used[b], cudaEventDisableTiming));
-        }
-    }
-    // the copy stream starts after the staging allocation (stream order)
-    if (st == MBC_OK && cuda_ok(cudaEventRecord(start, stream))) cuda_ok(cudaStreamWaitEvent(cs, start, 0));
+    // every stream of the pipeline starts after the staging allocation
+    if (cuda_ok(cudaEventRecord(P.start, stream)) && cuda_ok(cudaStreamWaitEvent(P.copy, P.start, 0)))
+        for (int b = 0; b < 2; ++b) cuda_ok(cudaStreamWaitEvent(P.comp[b], P.start, 0));
     const char *host = reinterpret_cast<const char *>(props->s_u);
     char *hout = reinterpret_cast<char *>(out);
     for (int i = 0; i < n_chunks && st == MBC_OK; ++i) {
         const int b = i & 1;
         const int ta = t0 + i * ct, nc = std::min(ct, t0 + n_t - ta);
-        if (i >= 2 && !cuda_ok(cudaStreamWaitEvent(cs, used[b], 0))) break;  // chunk i - 2 done with buf[b]
+        if (i >= 2 && !cuda_ok(cudaStreamWaitEvent(P.copy, P.used[b], 0))) break;  // chunk i - 2 done with buf[b]
         for (int cfg = 0; cfg < props->n_cfg && st == MBC_OK; ++cfg) {
             const char *src = host + ((size_t)cfg * stride_cfg + (size_t)ta * stride_t) * elem;
             char *dst = buf[b] + (size_t)cfg * nc * slab_bytes;
             if (stride_t * (int64_t)elem == (int64_t)slab_bytes) {
-                cuda_ok(cudaMemcpyAsync(dst, src, nc * slab_bytes, cudaMemcpyHostToDevice, cs));
+                cuda_ok(cudaMemcpyAsync(dst, src, nc * slab_bytes, cudaMemcpyHostToDevice, P.copy));
             } else {
                 for (int t = 0; t < nc && st == MBC_OK; ++t)
                     cuda_ok(cudaMemcpyAsync(dst + t * slab_bytes, src + (size_t)t * stride_t * elem, slab_bytes,
-                                            cudaMemcpyHostToDevice, cs));
+                                            cudaMemcpyHostToDevice, P.copy));
             }
         }
-        if (st != MBC_OK || !cuda_ok(cudaEventRecord(ready[b], cs)) || !cuda_ok(cudaStreamWaitEvent(stream, ready[b], 0)))
+        if (st != MBC_OK || !cuda_ok(cudaEventRecord(P.ready[b], P.copy)) ||
+            !cuda_ok(cudaStreamWaitEvent(P.comp[b], P.ready[b], 0)))
             break;
         mbc_props sub = *props;
         sub.s_u = sub.s_d = buf[b];
@@ -930,20 +988,23 @@ mbc_status contract_host_pipelined(const mbc_props *props, const mbc_term_list *
         mbc_contract_opts so = *opts;
         so.t0 = 0;
         so.t1 = nc;
-        st = mbc_contract(&sub, lists, n_lists, &so, cout, stream);
-        if (st != MBC_OK || !cuda_ok(cudaEventRecord(used[b], stream))) break;
-        cuda_ok(cudaMemcpy2DAsync(hout + (size_t)(ta - t0) * row_out, (size_t)n_t * row_out, cout, (size_t)nc * row_out,
-                                  (size_t)nc * row_out, (size_t)props->n_cfg * n_lists, cudaMemcpyDeviceToHost, stream));
+        st = mbc_contract(&sub, lists, n_lists, &so, cout[b], P.comp[b]);
+        if (st != MBC_OK || !cuda_ok(cudaEventRecord(P.used[b], P.comp[b]))) break;
+        cuda_ok(cudaMemcpy2DAsync(dout + (size_t)(ta - t0) * row_out, (size_t)n_t * row_out, cout[b],
+                                  (size_t)nc * row_out, (size_t)nc * row_out, (size_t)props->n_cfg * n_lists,
+                                  cudaMemcpyDeviceToDevice, P.comp[b]));
     }
-    cudaStreamSynchronize(cs);
+    // the caller's stream frees the staging after both compute streams and
+    // the copy stream are done
+    for (int b = 0; b < 2; ++b) {
+        cudaEventRecord(P.done[b], P.comp[b]);
+        cudaStreamWaitEvent(stream, P.done[b], 0);
+    }
+    cudaEventRecord(P.start, P.copy);
+    cudaStreamWaitEvent(stream, P.start, 0);
+    if (st == MBC_OK) cuda_ok(cudaMemcpyAsync(hout, dout, full_out, cudaMemcpyDeviceToHost, stream));
     cudaFreeAsync(stage, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess && st == MBC_OK) st = MBC_ERR_CUDA;
-    for (int b = 0; b < 2; ++b) {
-        if (ready[b]) cudaEventDestroy(ready[b]);
-        if (used[b]) cudaEventDestroy(used[b]);
-    }
-    if (start) cudaEventDestroy(start);
-    if (cs) cudaStreamDestroy(cs);
     return st;
 }
 
@@ -1231,16 +1292,19 @@ extern "C" mbc_status mbc_sync_status(void *stream_v) {
 extern "C" void mbc_release_scratch(void) {
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return;
-    std::lock_guard<std::mutex> g(g_scratch_mu);
-    for (auto it = g_scratch.begin(); it != g_scratch.end();) {
-        if (it->first.first == device) {
-            cudaStreamSynchronize(it->first.second);
-            cudaFree(it->second.p);
-            it = g_scratch.erase(it);
-        } else {
-            ++it;
+    {
+        std::lock_guard<std::mutex> g(g_scratch_mu);
+        for (auto it = g_scratch.begin(); it != g_scratch.end();) {
+            if (it->first.first == device) {
+                cudaStreamSynchronize(it->first.second);
+                cudaFree(it->second.p);
+                it = g_scratch.erase(it);
+            } else {
+                ++it;
+            }
         }
     }
+    release_pipes(device);  // after the scratch of its compute streams
 }
 
 extern "C" void mbc_timing_enable(int32_t on) {
