@@ -531,7 +531,20 @@ def main():
             per_item += 8 * st["n_ops_total"] + 4 * st["n_l_total"]
         flops_step = (per_site * v3 + per_item * (n_mom // n_sinks)) * nt * args.cfgs
     else:
-        flops_step = sum(f["total"] for f in fl) * v3 * nt * args.cfgs
+        # the blocks of a site do not depend on the nucleus (Sec. 2): nuclei
+        # with the same operators need one diquark and one block of each
+        # species per site, whatever the number of nuclei
+        per_site = sum(f["recursion"] + f["contraction"] for f in fl)
+        for d in sorted(set(list_dims)):
+            nxi = 3 * d
+            species = set()
+            bs = 0
+            for st, dd in zip(stats, list_dims):
+                if dd == d:
+                    species |= set(st["path"])
+                    bs = st["block_size"]
+            per_site += 3 * nxi * nxi * (2 * (4 if d == 4 else 2)) * 8 + len(species) * bs * 6 * 8
+        flops_step = per_site * v3 * nt * args.cfgs
     peaks = measured_peaks()
     probe64 = mbc.fma_probe(0)
     probe32 = mbc.fma_probe(1)

@@ -106,10 +106,13 @@ struct Interval {
     int64_t size, off;
 };
 
-// first-fit placement of buffers with lifetimes [start, end] (inclusive)
-void place(std::vector<Interval *> &bufs) {
+// first-fit placement of buffers with lifetimes [start, end] (inclusive);
+// the first n_fixed buffers keep the offsets they carry
+void place(std::vector<Interval *> &bufs, size_t n_fixed = 0) {
     std::vector<Interval *> placed;
-    for (Interval *b : bufs) {
+    for (size_t i = 0; i < n_fixed && i < bufs.size(); ++i) placed.push_back(bufs[i]);
+    for (size_t i = n_fixed; i < bufs.size(); ++i) {
+        Interval *b = bufs[i];
         std::vector<std::pair<int64_t, int64_t>> busy;
         for (Interval *p : placed)
             if (p->start <= b->end && b->start <= p->end) busy.push_back({p->off, p->off + p->size});
@@ -210,28 +213,29 @@ bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries, std
     Interval Sb{0, 2, (int64_t)L->nxi * L->nxi, 0}, Qb{1, 2, 3LL * L->nxi * L->nxi, 0};
     Interval blk[2];
     std::vector<Interval> stage((size_t)A + 1);
-    std::vector<Interval *> order = {&Sb, &Qb};
+    // both blocks first, at fixed offsets [0, bs) and [bs, 2 bs), live to the
+    // end: lists with the same tile shape then share one block computation
+    // per site in a batch (blocks do not depend on the nucleus); the S tile,
+    // the diquark and the stages are placed after them by first fit
+    const int last_phase = 2 + A;
+    std::vector<Interval *> order;
+    for (int b = 0; b < 2; ++b) {
+        P.need_blk[b] = L->need_block[b] ? 1 : 0;
+        blk[b] = {2, last_phase, L->block_size, (int64_t)b * L->block_size};
+        order.push_back(&blk[b]);
+    }
+    order.push_back(&Sb);
+    order.push_back(&Qb);
     // a stage where a nucleus of the list ends stays live until the contraction
     std::vector<bool> contracted((size_t)A + 1, false);
     for (const auto &pt : L->parts) contracted[(size_t)pt.A] = true;
-    const int last_phase = 2 + A;
-    for (int b = 0; b < 2; ++b) {
-        P.need_blk[b] = L->need_block[b] ? 1 : 0;
-        if (!P.need_blk[b]) continue;
-        int last = 2;
-        for (int m = 1; m < A; ++m)
-            if (L->path[m] == b) last = std::max(last, 3 + m - 1);
-        if (L->path[0] == b) last = std::max(last, contracted[1] ? last_phase : 3);
-        blk[b] = {2, last, L->block_size, 0};
-        order.push_back(&blk[b]);
-    }
     for (int m = 1; m < A; ++m) {
         stage[(size_t)m + 1] = {3 + m - 1, contracted[(size_t)m + 1] ? last_phase : 3 + m,
                                 L->steps[(size_t)m - 1].n_z, 0};
         order.push_back(&stage[(size_t)m + 1]);
     }
     (void)n_ph;
-    place(order);
+    place(order, 2);
     int64_t top = 0;
     for (auto *b : order) top = std::max(top, b->off + b->size);
     site_entries = (top + 1) & ~int64_t(1);
@@ -239,7 +243,7 @@ bool plan_small(const mbc_term_list *L, SmallPlan &P, int64_t &site_entries, std
     P.part_off = (int)site_entries;  // lanes-are-sites kernel: 64 partial rows after the site region
     P.s_off = (int)Sb.off;
     P.q_off = (int)Qb.off;
-    for (int b = 0; b < 2; ++b) P.blk_off[b] = P.need_blk[b] ? (int)blk[b].off : 0;
+    for (int b = 0; b < 2; ++b) P.blk_off[b] = (int)blk[b].off;
     int64_t op_off = 0;
     for (int m = 1; m < A; ++m) {
         const Step &s = L->steps[(size_t)m - 1];
@@ -1207,6 +1211,21 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
         }
         br.B.item_base[br.B.n_lists] = items;
         br.B.total_items = items;
+        // lists with the same tile shape and S / diquark / block offsets share
+        // one tile load and block computation per site: items become tiles
+        bool share = br.B.n_lists > 1;
+        for (int j = 1; j < br.B.n_lists && share; ++j) {
+            const SmallPlan &a = br.B.plan[0], &b = br.B.plan[j];
+            share = a.nxi == b.nxi && a.dim == b.dim && a.n_g2 == b.n_g2 && a.block_size == b.block_size &&
+                    a.npair == b.npair && a.s_off == b.s_off && a.q_off == b.q_off && a.blk_off[0] == b.blk_off[0] &&
+                    a.blk_off[1] == b.blk_off[1];
+        }
+        if (share) {
+            br.B.shared = 1;
+            for (int j = 0; j < br.B.n_lists; ++j)
+                for (int b = 0; b < 2; ++b) br.B.need_union[b] |= br.B.plan[j].need_blk[b];
+            br.B.total_items = n_slabs * br.sl.tiles_per_slab;
+        }
         br.part_bytes = (size_t)poff * sizeof(double2);
         batches.push_back(br);
     }

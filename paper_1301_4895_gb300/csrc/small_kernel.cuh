@@ -54,13 +54,19 @@ struct SmallPlan {
 
 // A batch of term lists contracted by one persistent launch: the work items
 // are (list, tile) pairs, numbered list by list in the order given (the host
-// puts the most expensive list first), handed out by an atomic counter.
+// puts the most expensive list first), handed out by an atomic counter. In a
+// shared batch (lists with the same tile shape and buffer offsets of the S
+// tile, diquark and blocks) an item is a tile and covers every list: the
+// tile and the blocks (of the baryons any list needs) are computed once per
+// site, then each list runs its steps and contraction.
 constexpr int kMaxBatch = 8;
 struct SmallBatch {
     int32_t n_lists;
     int32_t site_stride;      // warp-per-site kernel: entries of one site region (max over lists)
     int32_t comp_stride;      // warp-per-site kernel: components per site in the C area (max)
     int32_t tiles_per_slab;
+    int32_t shared;           // items are tiles covering every list
+    int32_t need_union[2];    // shared: blocks some list needs
     int64_t total_items;
     int64_t item_base[kMaxBatch + 1];
     int64_t partial_off[kMaxBatch];  // in double2 units
@@ -76,6 +82,10 @@ __device__ __forceinline__ int next_item(const SmallBatch &B, int64_t &tile) {
     __syncthreads();
     const int64_t item = s_item;
     if (item >= B.total_items) return -1;
+    if (B.shared) {
+        tile = item;
+        return 0;
+    }
     int l = 0;
     while (l + 1 < B.n_lists && item >= B.item_base[l + 1]) ++l;
     tile = item - B.item_base[l];
@@ -172,7 +182,7 @@ __device__ __forceinline__ void small_step(const SmallPlan &P, const SmallStepDe
 
 // Blocks (Sec. 2) for one site: Q, then f_P and/or f_N antisymmetric parts.
 template <class Tr>
-__device__ __forceinline__ void small_blocks(const SmallPlan &P, typename Tr::V *R, int lane) {
+__device__ __forceinline__ void small_blocks(const SmallPlan &P, const int32_t *need, typename Tr::V *R, int lane) {
     using V = typename Tr::V;
     const int nxi = P.nxi;
     const V *S = R + P.s_off;
@@ -184,7 +194,7 @@ __device__ __forceinline__ void small_blocks(const SmallPlan &P, typename Tr::V 
     __syncwarp();
     const int per_spin = P.npair * nxi;
     for (int b = 0; b < 2; ++b) {
-        if (!P.need_blk[b]) continue;
+        if (!need[b]) continue;
         V *F = R + P.blk_off[b];
         for (int e = lane; e < P.block_size; e += 32) {
             int dl = e / per_spin, r = e % per_spin;
@@ -231,10 +241,10 @@ __global__ void __launch_bounds__(1024, 1)
     const int V3 = F.lx * F.ly * F.lz;
     const int tiles_per_slab = B.tiles_per_slab;
     int64_t tile;
-    for (int li; (li = next_item(B, tile)) >= 0;) {
-        const SmallPlan &P = B.plan[li];
-        double2 *partial = partial_base + B.partial_off[li];
-        const int nxi = P.nxi;
+    for (int li0; (li0 = next_item(B, tile)) >= 0;) {
+        const int l_end = B.shared ? B.n_lists : li0 + 1;
+        const SmallPlan &P0 = B.plan[li0];
+        const int nxi = P0.nxi;
         const int64_t slab = tile / tiles_per_slab;
         const int tin = (int)(tile % tiles_per_slab);
         const int cfg = (int)(slab / F.n_t), t = F.t0 + (int)(slab % F.n_t);
@@ -244,47 +254,54 @@ __global__ void __launch_bounds__(1024, 1)
             const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * site_elems(F);
             // 1. propagator tile
             const int nent = nxi * nxi;
-            for (int e = lane; e < nent; e += 32) R[P.s_off + e] = Tr::from_d(load_prop(F, base, (e / nxi) * 12 + (e % nxi)));
+            for (int e = lane; e < nent; e += 32) R[P0.s_off + e] = Tr::from_d(load_prop(F, base, (e / nxi) * 12 + (e % nxi)));
             __syncwarp();
-            // 2. blocks
-            small_blocks<Tr>(P, R, lane);
-            // 3. recursion
-            for (int m = 0; m < P.n_steps; ++m) small_step<Tr>(P, P.step[m], R, lane);
-            // 4. contraction with L, FP64
-            const int g = P.fin_g, per = 32 / g, sub = lane & (g - 1);
-            for (int c0 = 0; c0 < P.n_comp; c0 += per) {
-                int c = c0 + lane / g;
-                double re = 0.0, im = 0.0;
-                if (c < P.n_comp) {
-                    for (int64_t e = P.fin_off[c] + sub; e < P.fin_off[c + 1]; e += g) {
-                        double2 f = Tr::to_d(R[__ldg(P.fin_z + e)]);
-                        double l = __ldg(P.fin_l + e);
-                        re = __fma_rn(l, f.x, re);
-                        im = __fma_rn(l, f.y, im);
-                    }
-                }
-                for (int off = g >> 1; off > 0; off >>= 1) {
-                    re += __shfl_xor_sync(0xffffffffu, re, off);
-                    im += __shfl_xor_sync(0xffffffffu, im, off);
-                }
-                if (c < P.n_comp && sub == 0) Cs[warp * B.comp_stride + c] = make_double2(re, im);
-            }
-        } else {
-            for (int c = lane; c < P.n_comp; c += 32) Cs[warp * B.comp_stride + c] = make_double2(0, 0);
+            // 2. blocks, once for every list of the item
+            small_blocks<Tr>(P0, B.shared ? B.need_union : P0.need_blk, R, lane);
         }
-        __syncthreads();
-        // tile partial: (1/N) sum over the T sites, in a fixed order, of phase * C
-        const int site0 = tin * T;
-        for (int o = threadIdx.x; o < M.n_mom * P.n_comp; o += blockDim.x) {
-            int q = o / P.n_comp, c = o % P.n_comp;
-            double re = 0.0, im = 0.0;
-            for (int w = 0; w < T && site0 + w < V3; ++w) {
-                double2 ph = __ldg(phase + (int64_t)(site0 + w) * M.n_mom + q), cv = Cs[w * B.comp_stride + c];
-                re = __fma_rn(ph.x, cv.x, __fma_rn(-ph.y, cv.y, re));
-                im = __fma_rn(ph.x, cv.y, __fma_rn(ph.y, cv.x, im));
+        for (int li = li0; li < l_end; ++li) {
+            const SmallPlan &P = B.plan[li];
+            double2 *partial = partial_base + B.partial_off[li];
+            if (live) {
+                // 3. recursion
+                for (int m = 0; m < P.n_steps; ++m) small_step<Tr>(P, P.step[m], R, lane);
+                // 4. contraction with L, FP64
+                const int g = P.fin_g, per = 32 / g, sub = lane & (g - 1);
+                for (int c0 = 0; c0 < P.n_comp; c0 += per) {
+                    int c = c0 + lane / g;
+                    double re = 0.0, im = 0.0;
+                    if (c < P.n_comp) {
+                        for (int64_t e = P.fin_off[c] + sub; e < P.fin_off[c + 1]; e += g) {
+                            double2 f = Tr::to_d(R[__ldg(P.fin_z + e)]);
+                            double l = __ldg(P.fin_l + e);
+                            re = __fma_rn(l, f.x, re);
+                            im = __fma_rn(l, f.y, im);
+                        }
+                    }
+                    for (int off = g >> 1; off > 0; off >>= 1) {
+                        re += __shfl_xor_sync(0xffffffffu, re, off);
+                        im += __shfl_xor_sync(0xffffffffu, im, off);
+                    }
+                    if (c < P.n_comp && sub == 0) Cs[warp * B.comp_stride + c] = make_double2(re, im);
+                }
+            } else {
+                for (int c = lane; c < P.n_comp; c += 32) Cs[warp * B.comp_stride + c] = make_double2(0, 0);
             }
-            const double inv_norm = __ldg(P.comp_inv_norm + c);
-            partial[tile * (int64_t)(M.n_mom * P.n_comp) + o] = make_double2(re * inv_norm, im * inv_norm);
+            __syncthreads();
+            // tile partial: (1/N) sum over the T sites, in a fixed order, of phase * C
+            const int site0 = tin * T;
+            for (int o = threadIdx.x; o < M.n_mom * P.n_comp; o += blockDim.x) {
+                int q = o / P.n_comp, c = o % P.n_comp;
+                double re = 0.0, im = 0.0;
+                for (int w = 0; w < T && site0 + w < V3; ++w) {
+                    double2 ph = __ldg(phase + (int64_t)(site0 + w) * M.n_mom + q), cv = Cs[w * B.comp_stride + c];
+                    re = __fma_rn(ph.x, cv.x, __fma_rn(-ph.y, cv.y, re));
+                    im = __fma_rn(ph.x, cv.y, __fma_rn(ph.y, cv.x, im));
+                }
+                const double inv_norm = __ldg(P.comp_inv_norm + c);
+                partial[tile * (int64_t)(M.n_mom * P.n_comp) + o] = make_double2(re * inv_norm, im * inv_norm);
+            }
+            if (li + 1 < l_end) __syncthreads();  // Cs is read before the next list writes it
         }
     }
 }

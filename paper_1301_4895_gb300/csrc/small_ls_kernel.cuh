@@ -63,9 +63,11 @@ __global__ void __launch_bounds__(1024, 1)
 #define ROW(e) R[(int64_t)(e) * 32 + lane]
 
     int64_t tile;
-    for (int li; (li = next_item(B, tile)) >= 0;) {  // next_item synchronises the CTA
-        const SmallPlan &P = B.plan[li];
-        double2 *partial = partial_base + B.partial_off[li];
+    for (int li0; (li0 = next_item(B, tile)) >= 0;) {  // next_item synchronises the CTA
+        // a shared batch's item is a tile of every list: tile and blocks once
+        const int l_end = B.shared ? B.n_lists : li0 + 1;
+        const SmallPlan &P = B.plan[li0];
+        const int32_t *need = B.shared ? B.need_union : P.need_blk;
         const int nxi = P.nxi, nent = nxi * nxi;
         const int64_t slab = tile / tiles_per_slab;
         const int tin = (int)(tile % tiles_per_slab);
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(1024, 1)
         __syncthreads();
         const int per_spin = P.npair * nxi;
         for (int b = 0; b < 2; ++b) {
-            if (!P.need_blk[b]) continue;
+            if (!need[b]) continue;
             for (int e = warp; e < P.block_size; e += NW) {
                 const int dl = e / per_spin, r = e % per_spin;
                 const int pr = r / nxi, single = r % nxi;
@@ -145,104 +147,110 @@ __global__ void __launch_bounds__(1024, 1)
             }
         }
         __syncthreads();
-        // 3. recursion
-        for (int m = 0; m < P.n_steps; ++m) {
-            const SmallStepDesc &d = P.step[m];
-            const uint32_t *ops = P.zops + d.zop_off;
-            const int split = d.n_z < NW ? NW / d.n_z : 1;  // CTA-uniform
-            int64_t o_begin, o_end, zb;
-            int part = -1;
-            if (split <= 1) {
-                zb = (int64_t)warp * d.n_z / NW;
-                const int64_t ze = (int64_t)(warp + 1) * d.n_z / NW;
-                o_begin = zb * d.k;
-                o_end = ze * d.k;
-            } else {
-                const int u = warp;  // unit = (z, part)
-                if (u < d.n_z * split) {
-                    zb = u / split;
-                    part = u % split;
-                    o_begin = zb * d.k + (int64_t)part * d.k / split;
-                    o_end = zb * d.k + (int64_t)(part + 1) * d.k / split;
+        for (int li = li0; li < l_end; ++li) {
+            const SmallPlan &P = B.plan[li];
+            double2 *partial = partial_base + B.partial_off[li];
+            // 3. recursion
+            for (int m = 0; m < P.n_steps; ++m) {
+                const SmallStepDesc &d = P.step[m];
+                const uint32_t *ops = P.zops + d.zop_off;
+                const int split = d.n_z < NW ? NW / d.n_z : 1;  // CTA-uniform
+                int64_t o_begin, o_end, zb;
+                int part = -1;
+                if (split <= 1) {
+                    zb = (int64_t)warp * d.n_z / NW;
+                    const int64_t ze = (int64_t)(warp + 1) * d.n_z / NW;
+                    o_begin = zb * d.k;
+                    o_end = ze * d.k;
                 } else {
-                    zb = 0;
-                    o_begin = o_end = 0;
-                }
-            }
-            typename Tr::Acc acc;
-            acc.zero();
-            // 32-bit lane pointers: row e of lane l sits at R[e * 32 + l]
-            static_assert(sizeof(V) == 8, "a row of 32 lanes is 256 B");
-            const char *Xb = reinterpret_cast<const char *>(R + (d.x_off << 5) + lane);
-            const char *Yb = reinterpret_cast<const char *>(R + (d.y_off << 5) + lane);
-            V *Zl = R + (d.z_off << 5) + lane;
-            // output by output: each output's k terms are contiguous, loaded
-            // 32 at a time and broadcast by shuffles; no per-term branch
-            const int n_out = part < 0 ? (int)((o_end - o_begin) / d.k) : 1;
-            const int len = part < 0 ? d.k : (int)(o_end - o_begin);
-            const uint32_t *op_ptr = ops + o_begin;
-            for (int zz = 0; zz < n_out; ++zz, op_ptr += len) {
-                for (int b0 = 0; b0 < len; b0 += 32) {
-                    const int nb = min(32, len - b0);
-                    const uint32_t mine = lane < nb ? __ldg(op_ptr + b0 + lane) : 0u;
-#pragma unroll 4
-                    for (int q = 0; q < nb; ++q) {
-                        // operands are byte offsets of 256 B rows, the sign is bit 0
-                        const uint32_t op = __shfl_sync(full, mine, q);
-                        acc.fma(*reinterpret_cast<const V *>(Xb + (op & 0xff00u)),
-                                *reinterpret_cast<const V *>(Yb + (op >> 16)), op << 31);
+                    const int u = warp;  // unit = (z, part)
+                    if (u < d.n_z * split) {
+                        zb = u / split;
+                        part = u % split;
+                        o_begin = zb * d.k + (int64_t)part * d.k / split;
+                        o_end = zb * d.k + (int64_t)(part + 1) * d.k / split;
+                    } else {
+                        zb = 0;
+                        o_begin = o_end = 0;
                     }
                 }
-                if (part < 0) {
-                    Zl[((int)zb + zz) << 5] = acc.store();
-                    acc.zero();
+                typename Tr::Acc acc;
+                acc.zero();
+                // 32-bit lane pointers: row e of lane l sits at R[e * 32 + l]
+                static_assert(sizeof(V) == 8, "a row of 32 lanes is 256 B");
+                const char *Xb = reinterpret_cast<const char *>(R + (d.x_off << 5) + lane);
+                const char *Yb = reinterpret_cast<const char *>(R + (d.y_off << 5) + lane);
+                V *Zl = R + (d.z_off << 5) + lane;
+                // output by output: each output's k terms are contiguous, loaded
+                // 32 at a time and broadcast by shuffles; no per-term branch
+                const int n_out = part < 0 ? (int)((o_end - o_begin) / d.k) : 1;
+                const int len = part < 0 ? d.k : (int)(o_end - o_begin);
+                const uint32_t *op_ptr = ops + o_begin;
+                for (int zz = 0; zz < n_out; ++zz, op_ptr += len) {
+                    for (int b0 = 0; b0 < len; b0 += 32) {
+                        const int nb = min(32, len - b0);
+                        const uint32_t mine = lane < nb ? __ldg(op_ptr + b0 + lane) : 0u;
+    #pragma unroll 4
+                        for (int q = 0; q < nb; ++q) {
+                            // operands are byte offsets of 256 B rows, the sign is bit 0
+                            const uint32_t op = __shfl_sync(full, mine, q);
+                            acc.fma(*reinterpret_cast<const V *>(Xb + (op & 0xff00u)),
+                                    *reinterpret_cast<const V *>(Yb + (op >> 16)), op << 31);
+                        }
+                    }
+                    if (part < 0) {
+                        Zl[((int)zb + zz) << 5] = acc.store();
+                        acc.zero();
+                    }
                 }
-            }
-            if (split > 1) {
-                if (part >= 0) {
-                    ROW(P.part_off + 2 * warp) = V{acc.sr, acc.cr};
-                    ROW(P.part_off + 2 * warp + 1) = V{acc.si, acc.ci};
+                if (split > 1) {
+                    if (part >= 0) {
+                        ROW(P.part_off + 2 * warp) = V{acc.sr, acc.cr};
+                        ROW(P.part_off + 2 * warp + 1) = V{acc.si, acc.ci};
+                    }
+                    __syncthreads();
+                    for (int zz = warp; zz < d.n_z; zz += NW) {
+                        typename Tr::Acc a;
+                        a.zero();
+                        for (int pp = 0; pp < split; ++pp) {
+                            const V r0 = ROW(P.part_off + 2 * (zz * split + pp));
+                            const V r1 = ROW(P.part_off + 2 * (zz * split + pp) + 1);
+                            a.add(r0.x, r0.y, r1.x, r1.y);
+                        }
+                        ROW(d.z_off + zz) = a.store();
+                    }
                 }
                 __syncthreads();
-                for (int zz = warp; zz < d.n_z; zz += NW) {
-                    typename Tr::Acc a;
-                    a.zero();
-                    for (int pp = 0; pp < split; ++pp) {
-                        const V r0 = ROW(P.part_off + 2 * (zz * split + pp));
-                        const V r1 = ROW(P.part_off + 2 * (zz * split + pp) + 1);
-                        a.add(r0.x, r0.y, r1.x, r1.y);
+            }
+            // 4. contraction with L in FP64, undo the scaling, phase, sum over the
+            //    32 sites of the tile by a fixed xor tree
+            const int site = site0 + lane;
+            const bool live = site < V3;
+            for (int c = warp; c < P.n_comp; c += NW) {
+                const int ue = -__ldg(P.comp_deg + c) * sexp_s[lane];
+                const double inv_norm = __ldg(P.comp_inv_norm + c);
+                double re = 0.0, im = 0.0;
+                for (int64_t e = P.fin_off[c]; e < P.fin_off[c + 1]; ++e) {
+                    const double2 f = Tr::to_d(ROW(__ldg(P.fin_z + e)));
+                    const double l = __ldg(P.fin_l + e);
+                    re = __fma_rn(l, f.x, re);
+                    im = __fma_rn(l, f.y, im);
+                }
+                re = live ? scalbn(re * inv_norm, ue) : 0.0;
+                im = live ? scalbn(im * inv_norm, ue) : 0.0;
+                for (int q = 0; q < M.n_mom; ++q) {
+                    const double2 ph = live ? __ldg(phase + (int64_t)site * M.n_mom + q) : make_double2(0, 0);
+                    double pr = __fma_rn(ph.x, re, -ph.y * im), pi = __fma_rn(ph.x, im, ph.y * re);
+                    for (int off = 16; off > 0; off >>= 1) {
+                        pr += __shfl_xor_sync(full, pr, off);
+                        pi += __shfl_xor_sync(full, pi, off);
                     }
-                    ROW(d.z_off + zz) = a.store();
+                    if (lane == 0)
+                        partial[tile * (int64_t)(M.n_mom * P.n_comp) + q * P.n_comp + c] = make_double2(pr, pi);
                 }
             }
-            __syncthreads();
-        }
-        // 4. contraction with L in FP64, undo the scaling, phase, sum over the
-        //    32 sites of the tile by a fixed xor tree
-        const int site = site0 + lane;
-        const bool live = site < V3;
-        for (int c = warp; c < P.n_comp; c += NW) {
-            const int ue = -__ldg(P.comp_deg + c) * sexp_s[lane];
-            const double inv_norm = __ldg(P.comp_inv_norm + c);
-            double re = 0.0, im = 0.0;
-            for (int64_t e = P.fin_off[c]; e < P.fin_off[c + 1]; ++e) {
-                const double2 f = Tr::to_d(ROW(__ldg(P.fin_z + e)));
-                const double l = __ldg(P.fin_l + e);
-                re = __fma_rn(l, f.x, re);
-                im = __fma_rn(l, f.y, im);
-            }
-            re = live ? scalbn(re * inv_norm, ue) : 0.0;
-            im = live ? scalbn(im * inv_norm, ue) : 0.0;
-            for (int q = 0; q < M.n_mom; ++q) {
-                const double2 ph = live ? __ldg(phase + (int64_t)site * M.n_mom + q) : make_double2(0, 0);
-                double pr = __fma_rn(ph.x, re, -ph.y * im), pi = __fma_rn(ph.x, im, ph.y * re);
-                for (int off = 16; off > 0; off >>= 1) {
-                    pr += __shfl_xor_sync(full, pr, off);
-                    pi += __shfl_xor_sync(full, pi, off);
-                }
-                if (lane == 0) partial[tile * (int64_t)(M.n_mom * P.n_comp) + q * P.n_comp + c] = make_double2(pr, pi);
-            }
-        }
+            if (li + 1 < l_end) __syncthreads();  // the stages are read before the next list writes them
+        }  // lists of the item
     }
 #undef ROW
 }
