@@ -21,6 +21,13 @@
  *                          C_final) and the sum over sink sites with a
  *                          momentum phase.
  *
+ * Beyond one nucleus at a point sink: momentum-projected blocks (Sec. 2 sink
+ * functions, mbc_contract_opts.sink_mode), spin projections (Sec. 5,
+ * MBC_SPIN_PROJECTED), several quark sources and sink functions (Sec. 6,
+ * n_sources / n_sinks), several nuclei on one recursion path (Sec. 7,
+ * mbc_build_combined) and lists without operation arrays (Sec. 3,
+ * list_free). Term lists can be written to and read from files.
+ *
  * Conventions (the paper leaves them open; every choice below changes at
  * most a global sign, identically for every component):
  *   - spinor-colour index xi = 3 * spin + colour, 0..11;
