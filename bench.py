@@ -115,7 +115,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+        out_dir = os.environ.get("MBC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"mbc_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -308,7 +310,7 @@ def cpu_baseline_projected(wl, lists_spec, nt_used, moms, n_src, n_sinks, budget
 
 
 def run_reference(args, wl):
-    """--impl reference: the CPU oracle as it stands, on the machine's host cores."""
+    """--impl reference: the CPU oracle as it stands, on the host's cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
