@@ -790,10 +790,14 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
     int32_t *sexp = reinterpret_cast<int32_t *>(p);
     const int nsm = sm_count(device);
     // 1. blocks of every site, phase-weighted tile sums, reduction over tiles
-    const size_t smem = project_smem_bytes(nrow, nxi, M.n_mom);
+    // FP64 blocks and sums for the FP64 path, FP32 products with compensated
+    // FP32 sums for the mixed path
+    const bool mx = sizeof(V) == sizeof(float2);
+    const void *pkern = mx ? (const void *)k_project_blocks_mx : (const void *)k_project_blocks;
+    const size_t smem = mx ? project_smem_bytes_mx(nrow, nxi, M.n_mom) : project_smem_bytes(nrow, nxi, M.n_mom);
     {
         int per_sm = 0;
-        mbc_status pst = prepare_kernel((const void *)k_project_blocks, device, 512, smem, &per_sm);
+        mbc_status pst = prepare_kernel(pkern, device, 512, smem, &per_sm);
         if (pst != MBC_OK) return pst;
     }
     {
@@ -801,12 +805,16 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         {
             TimedLaunch tl(stream);
             note_launch();
-            k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nrow, nxi, n_g2(L), bs,
-                                                                    (int)binom64(nxi, 2), L->need_block[0],
-                                                                    L->need_block[1], tps, n_tiles, partial);
+            if (mx)
+                k_project_blocks_mx<<<(unsigned)grid, 512, smem, stream>>>(
+                    F, M, phase, nrow, nxi, n_g2(L), bs, (int)binom64(nxi, 2), L->need_block[0], L->need_block[1],
+                    tps, n_tiles, partial);
+            else
+                k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nrow, nxi, n_g2(L), bs,
+                                                                        (int)binom64(nxi, 2), L->need_block[0],
+                                                                        L->need_block[1], tps, n_tiles, partial);
         }
-        MBC_CUDA_TRY(cudaGetLastError());
-        const int64_t outs = n_slabs * M.n_mom * n_out;
+        MBC_CUDA_TRY(cudaGetLastError());        const int64_t outs = n_slabs * M.n_mom * n_out;
         const unsigned rg = (unsigned)std::min<int64_t>((outs + 7) / 8, 65535);
         note_launch();
         k_reduce_tiles<<<std::max(rg, 1u), 256, 0, stream>>>(partial, n_slabs, tps, M.n_mom, (int)n_out, F.n_t, 0, 1,

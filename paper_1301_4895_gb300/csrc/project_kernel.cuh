@@ -8,6 +8,8 @@
 //                      in a fixed order by one thread per (block, momentum,
 //                      entry) -> tile partials, reduced over tiles by
 //                      k_reduce_tiles (compensated, fixed order);
+//   k_project_blocks_mx the same with FP32 products and compensated FP32
+//                      sums (mixed precision);
 //   k_load_proj_blocks copies the summed blocks of a wave of items into the
 //                      [component][item] layout of the wave kernels (MIXED:
 //                      exact power-of-two scaling per item);
@@ -115,6 +117,102 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
                 partial[(tile * M.n_mom + q) * (int64_t)n_out + b * block_size + e] = make_double2(re, im);
             }
             __syncthreads();  // the chunk's values are consumed
+        }
+    }
+}
+
+// Shared memory of k_project_blocks_mx (FP32 values) for tiles of 16 sites.
+inline size_t project_smem_bytes_mx(int nrow, int nxi, int n_mom) {
+    return sizeof(float2) * (16 * (size_t)nrow * nxi + 16 * 3 * (size_t)nxi * nxi + 2 * (size_t)kProjChunk * kProjPad +
+                             16 * (size_t)n_mom);
+}
+
+// The same projection for the mixed path: the tile, the diquark and the
+// blocks in FP32 products, the phase-weighted sum over the tile's 16 sites
+// with compensated (two-word) FP32 accumulation in the same fixed order, the
+// tile partial handed to the FP64 reduction over tiles.
+__global__ void __launch_bounds__(512) k_project_blocks_mx(FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
+                                                           int nrow, int nxi, int n_g2, int block_size, int npair,
+                                                           int need_p, int need_n, int tiles_per_slab, int64_t n_tiles,
+                                                           double2 *__restrict__ partial) {
+    constexpr int NS = 16;
+    using Acc = MixedTraits::Acc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *S = reinterpret_cast<float2 *>(smem_raw);  // [NS][nrow*nxi]
+    float2 *Q = S + NS * nrow * nxi;                   // [NS][3*nxi*nxi]
+    float2 *Fb = Q + NS * 3 * nxi * nxi;               // [2][kProjChunk][kProjPad]
+    float2 *Ph = Fb + 2 * kProjChunk * kProjPad;       // [NS][n_mom]
+    const int sl = threadIdx.x % NS, slice = threadIdx.x / NS, nslice = blockDim.x / NS;
+    const int nent = nrow * nxi, nq = nxi * nxi;
+    const int v3 = F.lx * F.ly * F.lz;
+    const int n_out = 2 * block_size;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t slab = tile / tiles_per_slab;
+        const int tin = (int)(tile % tiles_per_slab);
+        const int cfg = (int)(slab / F.n_t), t = F.t0 + (int)(slab % F.n_t);
+        __syncthreads();  // shared memory of the previous tile is free
+        for (int s = threadIdx.x >> 5; s < NS; s += blockDim.x >> 5) {
+            const int lane = threadIdx.x & 31;
+            const int site = tin * NS + s;
+            const bool live = site < v3;
+            const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * site_elems(F);
+            for (int e = lane; e < nent; e += 32) {
+                const double2 v = live ? load_prop(F, base, tile_index(F, e, nxi)) : make_double2(0, 0);
+                S[s * nent + e] = make_float2((float)v.x, (float)v.y);
+            }
+        }
+        for (int o = threadIdx.x; o < NS * M.n_mom; o += blockDim.x) {
+            const int site = tin * NS + o / M.n_mom;
+            const double2 p = site < v3 ? __ldg(phase + (int64_t)site * M.n_mom + o % M.n_mom) : make_double2(0, 0);
+            Ph[o] = make_float2((float)p.x, (float)p.y);
+        }
+        __syncthreads();
+        for (int e = slice; e < 3 * nq; e += nslice) {
+            const int c = e / nq, r = e % nq;
+            Q[sl * 3 * nq + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
+        }
+        __syncthreads();
+        const int site = tin * NS + sl;
+        const bool live = site < v3;
+        const float2 *Ss = S + sl * nent;
+        const float2 *Qs = Q + sl * 3 * nq;
+        const int per_spin = npair * nxi;
+        for (int e0 = 0; e0 < block_size; e0 += kProjChunk) {
+            for (int el = slice; el < kProjChunk; el += nslice) {
+                const int e = e0 + el;
+                const bool ok = live && e < block_size;
+                const int dl = e / per_spin, r = e % per_spin;
+                const int pr = r / nxi, single = r % nxi;
+                const int i = ok ? c_pair_i[pr] : 0, j = ok ? c_pair_j[pr] : 0;
+                for (int b = 0; b < 2; ++b) {
+                    float2 f = make_float2(0.f, 0.f);
+                    if (ok && (b == 0 ? need_p : need_n)) {
+                        for (int c = 0; c < 3; ++c) {
+                            const float2 *Sr = Ss + (3 * dl + c) * nxi;
+                            if (b == 0) {
+                                f = cfma(Sr[i], Qs[(c * nxi + j) * nxi + single], f);
+                                f = cfms(Sr[j], Qs[(c * nxi + i) * nxi + single], f);
+                            } else {
+                                f = cfma(Sr[i], Qs[(c * nxi + single) * nxi + j], f);
+                                f = cfms(Sr[j], Qs[(c * nxi + single) * nxi + i], f);
+                            }
+                        }
+                    }
+                    Fb[(b * kProjChunk + el) * kProjPad + sl] = f;
+                }
+            }
+            __syncthreads();
+            for (int o = threadIdx.x; o < 2 * M.n_mom * kProjChunk; o += blockDim.x) {
+                const int el = o % kProjChunk, q = (o / kProjChunk) % M.n_mom, b = o / (kProjChunk * M.n_mom);
+                const int e = e0 + el;
+                if (e >= block_size) continue;
+                const float2 *fv = Fb + (b * kProjChunk + el) * kProjPad;
+                Acc acc;
+                acc.zero();
+                for (int w = 0; w < NS; ++w) acc.fma(Ph[w * M.n_mom + q], fv[w], 0u);
+                partial[(tile * M.n_mom + q) * (int64_t)n_out + b * block_size + e] = acc.value();
+            }
+            __syncthreads();
         }
     }
 }
