@@ -608,7 +608,7 @@ def main():
         "gpu_launches_per_step": {"fp64": launch_count[0] / args.steps, "mixed": launch_count[1] / args.steps},
         "n_ops": [st["n_ops_total"] for st in stats],
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the oracle baseline is a single-GPU figure
         if sink == "block":
             line["cpu_baseline"] = cpu_baseline_projected(wl, [(n, tl.components()) for n, tl in zip(nuclei, lists)],
                                                           nt, moms, n_src, n_sinks)
