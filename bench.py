@@ -556,10 +556,11 @@ def main():
     has_small = any(n[2] == 2 for n in nuclei)
     has_large = any(n[2] == 4 for n in nuclei)
     kname = {0: " + ".join(k for k, on in (("k_small<FP64>", has_small), ("k_large_step<FP64>", has_large)) if on),
-             1: " + ".join(k for k, on in (("k_small_ls<Mixed>", has_small), ("k_large_step<Mixed>", has_large))
+             1: " + ".join(k for k, on in (("k_small_ls<Mixed>", has_small),
+                                            ("k_large_step_gen" if args.list_free else "k_large_step_mx2", has_large))
                            if on)}
     if sink == "block" or n_src > 1 or args.list_free:  # wave kernels only
-        kname = {0: "k_large_step<FP64>", 1: "k_large_step<Mixed>"}
+        kname = {0: "k_large_step<FP64>", 1: "k_large_step_gen" if args.list_free else "k_large_step_mx2"}
         if sink == "block":
             kname = {p: "k_project_blocks + " + k for p, k in kname.items()}
 

@@ -284,9 +284,10 @@ typedef struct {
     int32_t wave_sites;         /* large-stage kernels: sites in flight        */
     int32_t regime;             /* 0 auto, 1 force small-stage, 2 force large  */
     int32_t zchunk;             /* large-stage step kernel: outputs per warp item */
-    int32_t wave_order;         /* large-stage step kernel: 0 site groups of a chunk
-                                   side by side, 1 a CTA's warps on consecutive chunks
-                                   of one site group                              */
+    int32_t wave_order;         /* FP64 large-stage step kernel: 0 site groups of a
+                                   chunk side by side, 1 a CTA's warps on consecutive
+                                   chunks of one site group (the mixed step kernels
+                                   have one order)                                */
     int32_t list_free;          /* large-stage step kernel: 0 regenerate the splits of
                                    list-free lists, read the arrays of the others;
                                    1 also regenerate the dense steps of lists with

@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <new>
 #include <vector>
 
@@ -607,7 +608,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
     // path regenerates once per CTA into shared memory
     if (gen && sizeof(typename Tr::V) == sizeof(float2)) {
         // CTA-shared regeneration: zb outputs' operations per round in shared memory
-        const size_t per_z = (size_t)s.k * (sizeof(uint32_t) + sizeof(uint16_t));
+        const size_t per_z = (size_t)s.k * sizeof(OpRec);
         const int64_t nblk = (W / 64 + 7) / 8;
         const int64_t target = (int64_t)nsm * 3 * 8;
         int64_t nchunks = std::max<int64_t>(1, std::min<int64_t>(s.n_z, (target + nblk - 1) / nblk));
@@ -631,8 +632,10 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         MBC_CUDA_TRY(cudaGetLastError());
         return MBC_OK;
     }
-    if (!gen && sizeof(typename Tr::V) == sizeof(float2) && W % 64 == 0 && !(tune && tune->wave_order == 1)) {
-        // mixed precision, stored operations: two sites per lane
+    if constexpr (!std::is_same<Tr, FP64Traits>::value) {
+        // mixed precision, stored operations: two sites per lane (W is a
+        // multiple of 64; the planar pair layout of the wave buffers is this
+        // kernel's)
         const int threads = 256;
         const int64_t total_warps = (int64_t)nsm * 8 * (threads / 32);
         const int64_t ngroups = W / 64;
@@ -650,7 +653,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         }
         MBC_CUDA_TRY(cudaGetLastError());
         return MBC_OK;
-    }
+    } else {
     const int threads = 256;
     const int64_t total_warps = (int64_t)nsm * 8 * (threads / 32);
     const int64_t ngroups = W / 32;
@@ -672,6 +675,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
     }
     MBC_CUDA_TRY(cudaGetLastError());
     return MBC_OK;
+    }
 }
 
 // Contraction with L (eq. C_final) of every nucleus of the list that ends at

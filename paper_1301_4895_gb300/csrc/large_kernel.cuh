@@ -1,12 +1,12 @@
 // Large-stage contraction kernels (relativistic nuclei: blocks of 3168
 // components, stages up to millions of components per site, Sec. 7 P bound
 // with D = 4). Stage buffers live in device scratch with the layout
-// [component][wave site], so 32 consecutive sites of one component are one
-// coalesced row; a "wave" of W sites (a multiple of 32) is processed by the
-// whole GPU one step at a time, and each step streams its term list once per
-// wave. Lanes are sites; a warp walks the z-major list of its chunk with
-// warp-uniform (x, y, sign) operands that the lanes load cooperatively and
-// broadcast by shuffles.
+// [component][wave site], so consecutive sites of one component are one
+// coalesced row (mixed precision: sites in planar pairs, MixedTraits::wave_ld);
+// a "wave" of W sites (a multiple of 64) is processed by the whole GPU one step
+// at a time, and each step streams its term list once per wave. Lanes are
+// sites; a warp walks the z-major list of its chunk with warp-uniform
+// (x, y, sign) operands that the lanes load cooperatively and broadcast.
 #pragma once
 
 #include "device_common.cuh"
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, 
                     acc = cfms(Sr[j], Qs[(c * nxi + single) * nxi + i], acc);
                 }
             }
-            out[(int64_t)e * wv.W + w0 + sl] = acc;
+            Tr::wave_st(out, (int64_t)e * wv.W + w0 + sl, acc);
         }
     }
 }
@@ -192,65 +192,77 @@ __global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__
 
 // The mixed-precision step with two sites per lane: a warp covers 64
 // consecutive sites of the wave, every gather is one 16 B load per lane
-// (a 512 B row segment per warp), so the operand decoding and broadcast of
-// each operation is shared by twice the sites and twice the bytes are in
-// flight per load instruction. W must be a multiple of 64.
-__global__ void __launch_bounds__(256) k_large_step_mx2(const uint32_t *__restrict__ opx,
+// (a 512 B row segment per warp), and both sites' products and compensated
+// sums are packed FP32-pair instructions (PairAcc). The lanes decode 32
+// operations at a time into per-warp shared-memory records (x, y, sign,
+// sign), so a term costs one broadcast shared load, one multiply-add per
+// operand address, two gathers and the arithmetic. W must be a multiple of 64.
+struct __align__(16) OpRec {
+    uint32_t x, y;  // rows of X and Y
+    uint64_t sg;    // (+-1, +-1)
+};
+__device__ __forceinline__ OpRec op_rec(uint32_t x, uint32_t y) {
+    const float s = __uint_as_float(0x3f800000u | ((y & 0x8000u) << 16));
+    return OpRec{x, y & 0x7fffu, f2_pack(s, s)};
+}
+
+template <int G>
+__device__ __forceinline__ void pair_terms(const OpRec *rec, int n, const unsigned char *Xc, const unsigned char *Yc,
+                                           uint32_t row_bytes, PairAcc &acc) {
+    int t = 0;
+    for (; t + G <= n; t += G) {
+        ulonglong2 xv[G], yv[G];
+        uint64_t sg[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const OpRec r = rec[t + g];
+            xv[g] = __ldg(reinterpret_cast<const ulonglong2 *>(Xc + (size_t)r.x * row_bytes));
+            yv[g] = __ldg(reinterpret_cast<const ulonglong2 *>(Yc + (size_t)r.y * row_bytes));
+            sg[g] = r.sg;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc.fma(xv[g], yv[g], sg[g]);
+    }
+    for (; t < n; ++t) {
+        const OpRec r = rec[t];
+        acc.fma(__ldg(reinterpret_cast<const ulonglong2 *>(Xc + (size_t)r.x * row_bytes)),
+                __ldg(reinterpret_cast<const ulonglong2 *>(Yc + (size_t)r.y * row_bytes)), r.sg);
+    }
+}
+
+__global__ void __launch_bounds__(256, 4) k_large_step_mx2(const uint32_t *__restrict__ opx,
                                                         const uint16_t *__restrict__ opy, int64_t n_z, int64_t k,
                                                         int64_t zchunk, int W, const float2 *__restrict__ X,
                                                         const float2 *__restrict__ Y, float2 *__restrict__ Z) {
-    using Acc = MixedTraits::Acc;
+    __shared__ OpRec recs[8][32];
     const int lane = threadIdx.x & 31;
+    OpRec *rec = recs[(threadIdx.x >> 5) & 7];
     const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int ngroups = W >> 6;
     const int64_t nchunks = (n_z + zchunk - 1) / zchunk;
-    const int W4 = W >> 1;  // a row in float4 units (two sites each)
+    const uint32_t row_bytes = (uint32_t)W * (uint32_t)sizeof(float2);
     for (int64_t item = warp_global; item < nchunks * ngroups; item += nwarps) {
         const int64_t chunk = item / ngroups;
         const int group = (int)(item % ngroups);
         const int col4 = group * 32 + lane;  // float4 column: sites 2 col4, 2 col4 + 1
-        const float4 *Xc = reinterpret_cast<const float4 *>(X) + col4;
-        const float4 *Yc = reinterpret_cast<const float4 *>(Y) + col4;
+        const unsigned char *Xc = reinterpret_cast<const unsigned char *>(reinterpret_cast<const float4 *>(X) + col4);
+        const unsigned char *Yc = reinterpret_cast<const unsigned char *>(reinterpret_cast<const float4 *>(Y) + col4);
         const int64_t z_begin = chunk * zchunk;
         const int64_t z_end = min(n_z, z_begin + zchunk);
         for (int64_t z = z_begin; z < z_end; ++z) {
-            Acc a0, a1;
-            a0.zero();
-            a1.zero();
+            PairAcc acc;
+            acc.zero();
             const uint32_t *ox = opx + z * k;
             const uint16_t *oy = opy + z * k;
             for (int64_t b0 = 0; b0 < k; b0 += 32) {
                 const int nb = (int)min((int64_t)32, k - b0);
-                uint32_t mx = 0, my = 0;
-                if (lane < nb) {
-                    mx = __ldg(ox + b0 + lane);
-                    my = __ldg(oy + b0 + lane);
-                }
-                constexpr int G = 2;
-                for (int t0 = 0; t0 < nb; t0 += G) {
-                    float4 xv[G], yv[G];
-                    uint32_t sg[G];
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const uint32_t x = __shfl_sync(0xffffffffu, mx, (t0 + g) & 31);
-                        const uint32_t y = __shfl_sync(0xffffffffu, my, (t0 + g) & 31);
-                        if (t0 + g < nb) {
-                            xv[g] = __ldg(Xc + (int64_t)x * W4);
-                            yv[g] = __ldg(Yc + (int64_t)(y & 0x7fffu) * W4);
-                        }
-                        sg[g] = (y & 0x8000u) << 16;
-                    }
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
-                        if (t0 + g < nb) {
-                            a0.fma(make_float2(xv[g].x, xv[g].y), make_float2(yv[g].x, yv[g].y), sg[g]);
-                            a1.fma(make_float2(xv[g].z, xv[g].w), make_float2(yv[g].z, yv[g].w), sg[g]);
-                        }
-                }
+                __syncwarp();  // the previous records are consumed
+                if (lane < nb) rec[lane] = op_rec(__ldg(ox + b0 + lane), __ldg(oy + b0 + lane));
+                __syncwarp();
+                pair_terms<4>(rec, nb, Xc, Yc, row_bytes, acc);
             }
-            const float2 r0 = a0.store(), r1 = a1.store();
-            reinterpret_cast<float4 *>(Z + z * W)[col4] = make_float4(r0.x, r0.y, r1.x, r1.y);
+            reinterpret_cast<ulonglong2 *>(Z + z * W)[col4] = acc.store();
         }
     }
 }
@@ -261,26 +273,25 @@ __global__ void __launch_bounds__(256) k_large_step_mx2(const uint32_t *__restri
 // outputs at a time its 256 threads regenerate the outputs' operations once
 // into shared memory, then every warp runs them on its sites exactly as the
 // stored words would run (same order, same arithmetic), so the integer work
-// is shared by the CTA's 512 sites. W must be a multiple of 64.
+// is shared by the CTA's 512 sites (records as in k_large_step_mx2).
+// W must be a multiple of 64.
 __global__ void __launch_bounds__(256, 3) k_large_step_gen(GenStep gs, int64_t n_z, int64_t k, int64_t zchunk, int zb,
                                                            int W, const float2 *__restrict__ X,
                                                            const float2 *__restrict__ Y, float2 *__restrict__ Z) {
-    using Acc = MixedTraits::Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t *sx = reinterpret_cast<uint32_t *>(smem_raw);  // [zb][k]
-    uint16_t *sy = reinterpret_cast<uint16_t *>(sx + (int64_t)zb * k);
+    OpRec *srec = reinterpret_cast<OpRec *>(smem_raw);  // [zb][k]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ngroups = W >> 6;
     const int nblk = (ngroups + 7) / 8;
-    const int W4 = W >> 1;  // a row in float4 units (two sites each)
+    const uint32_t row_bytes = (uint32_t)W * (uint32_t)sizeof(float2);
     const int64_t nchunks = (n_z + zchunk - 1) / zchunk;
     for (int64_t item = blockIdx.x; item < nchunks * nblk; item += gridDim.x) {
         const int64_t chunk = item / nblk;
         const int group = (int)(item % nblk) * 8 + warp;
         const bool active = group < ngroups;
         const int col4 = (active ? group : 0) * 32 + lane;
-        const float4 *Xc = reinterpret_cast<const float4 *>(X) + col4;
-        const float4 *Yc = reinterpret_cast<const float4 *>(Y) + col4;
+        const unsigned char *Xc = reinterpret_cast<const unsigned char *>(reinterpret_cast<const float4 *>(X) + col4);
+        const unsigned char *Yc = reinterpret_cast<const unsigned char *>(reinterpret_cast<const float4 *>(Y) + col4);
         const int64_t z_begin = chunk * zchunk;
         const int64_t z_end = min(n_z, z_begin + zchunk);
         for (int64_t zr = z_begin; zr < z_end; zr += zb) {
@@ -292,40 +303,16 @@ __global__ void __launch_bounds__(256, 3) k_large_step_gen(GenStep gs, int64_t n
                 for (int64_t j = threadIdx.x; j < k; j += blockDim.x) {
                     uint32_t ox, oy;
                     g_op(gs, zkey, j, ox, oy);
-                    sx[q * k + j] = ox;
-                    sy[q * k + j] = (uint16_t)oy;
+                    srec[q * k + j] = op_rec(ox, oy);
                 }
             }
             __syncthreads();
             if (!active) continue;
             for (int q = 0; q < nzr; ++q) {
-                Acc a0, a1;
-                a0.zero();
-                a1.zero();
-                const uint32_t *ox = sx + q * k;
-                const uint16_t *oy = sy + q * k;
-                constexpr int G = 2;
-                for (int64_t t0 = 0; t0 < k; t0 += G) {
-                    float4 xv[G], yv[G];
-                    uint32_t sg[G];
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        if (t0 + g < k) {
-                            const uint32_t x = ox[t0 + g], y = oy[t0 + g];
-                            xv[g] = __ldg(Xc + (int64_t)x * W4);
-                            yv[g] = __ldg(Yc + (int64_t)(y & 0x7fffu) * W4);
-                            sg[g] = (y & 0x8000u) << 16;
-                        }
-                    }
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
-                        if (t0 + g < k) {
-                            a0.fma(make_float2(xv[g].x, xv[g].y), make_float2(yv[g].x, yv[g].y), sg[g]);
-                            a1.fma(make_float2(xv[g].z, xv[g].w), make_float2(yv[g].z, yv[g].w), sg[g]);
-                        }
-                }
-                const float2 r0 = a0.store(), r1 = a1.store();
-                reinterpret_cast<float4 *>(Z + (zr + q) * W)[col4] = make_float4(r0.x, r0.y, r1.x, r1.y);
+                PairAcc acc;
+                acc.zero();
+                pair_terms<4>(srec + q * k, (int)k, Xc, Yc, row_bytes, acc);  // k * 16 B fit shared memory
+                reinterpret_cast<ulonglong2 *>(Z + (zr + q) * W)[col4] = acc.store();
             }
         }
     }
@@ -348,7 +335,7 @@ __global__ void __launch_bounds__(256) k_large_contract(const int64_t *__restric
         const int col = (int)(item % ngroups) * 32 + lane;
         double re = 0.0, im = 0.0;
         for (int64_t e = fin_off[c]; e < fin_off[c + 1]; ++e) {
-            double2 f = Tr::to_d(FA[(int64_t)__ldg(fin_z + e) * W + col]);
+            double2 f = Tr::to_d(Tr::wave_ld(FA, (int64_t)__ldg(fin_z + e) * W + col));
             double l = __ldg(fin_l + e);
             re = __fma_rn(l, f.x, re);
             im = __fma_rn(l, f.y, im);

@@ -255,8 +255,8 @@ __global__ void __launch_bounds__(256) k_load_proj_blocks(const double2 *__restr
         const double2 *s_k = src + (int64_t)k * 2 * bs_site + alpha * per_spin + r;
         const double2 p = live ? s_k[0] : make_double2(0, 0);
         const double2 n = live ? s_k[bs_site] : make_double2(0, 0);
-        fP[(int64_t)e * W + col] = Tr::from_d(make_double2(scalbn(p.x, se), scalbn(p.y, se)));
-        fN[(int64_t)e * W + col] = Tr::from_d(make_double2(scalbn(n.x, se), scalbn(n.y, se)));
+        Tr::wave_st(fP, (int64_t)e * W + col, Tr::from_d(make_double2(scalbn(p.x, se), scalbn(p.y, se))));
+        Tr::wave_st(fN, (int64_t)e * W + col, Tr::from_d(make_double2(scalbn(n.x, se), scalbn(n.y, se))));
     }
     if (lane == 0) sexp[col] = se;
 }

@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(1024, 1)
                 }
                 if (split > 1) {
                     if (part >= 0) {
-                        ROW(P.part_off + 2 * warp) = V{acc.sr, acc.cr};
-                        ROW(P.part_off + 2 * warp + 1) = V{acc.si, acc.ci};
+                        ROW(P.part_off + 2 * warp) = f2_unpack(acc.s);      // (sum re, sum im)
+                        ROW(P.part_off + 2 * warp + 1) = f2_unpack(acc.c);  // their compensations
                     }
                     __syncthreads();
                     for (int zz = warp; zz < d.n_z; zz += NW) {
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(1024, 1)
                         for (int pp = 0; pp < split; ++pp) {
                             const V r0 = ROW(P.part_off + 2 * (zz * split + pp));
                             const V r1 = ROW(P.part_off + 2 * (zz * split + pp) + 1);
-                            a.add(r0.x, r0.y, r1.x, r1.y);
+                            a.add(r0.x, r1.x, r0.y, r1.y);
                         }
                         ROW(d.z_off + zz) = a.store();
                     }
