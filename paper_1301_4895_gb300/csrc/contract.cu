@@ -511,9 +511,14 @@ SmallLaunch size_small_batch(const std::vector<const DeviceCache *> &cs, const F
         l.smem = (size_t)l.T * per_site;
     } else {
         l.T = 32;
-        l.smem = (size_t)(site_stride + 64) * 32 * sizeof(float2);
         l.threads = (tune && tune->threads_per_cta > 0) ? tune->threads_per_cta : 1024;
         l.threads = std::max(64, std::min(1024, l.threads / 32 * 32));
+        // rows of 32 lanes (site region + 64 partial rows), then 32 operation
+        // records of 16 B per warp; fewer warps where the records do not fit
+        const size_t rows = (size_t)(site_stride + 64) * 32 * sizeof(float2);
+        while (l.threads > 256 && rows + (size_t)l.threads * 16 > (size_t)kSmemLimit - 2048) l.threads /= 2;
+        l.threads = l.threads / 32 * 32;
+        l.smem = rows + (size_t)l.threads * 16;
         if (l.smem > (size_t)kSmemLimit - 2048) return l;
     }
     if (l.T < 1) return l;
@@ -720,7 +725,7 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
     int32_t *sexp = reinterpret_cast<int32_t *>(p);
     const int nsm = sm_count(device);
     const int nxi = L->nxi, nrow = 3 * L->dim;
-    const size_t blk_smem = (size_t)16 * (nrow * nxi + 3 * nxi * nxi) * sizeof(V);
+    const size_t blk_smem = (size_t)16 * (tile_stride(nrow, nxi) + diquark_stride(nxi)) * sizeof(V);
     {
         int per_sm = 0;
         mbc_status pst = prepare_kernel((const void *)k_large_blocks<Tr>, device, 512, blk_smem, &per_sm);
@@ -818,11 +823,13 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
                                                                         (int)binom64(nxi, 2), L->need_block[0],
                                                                         L->need_block[1], tps, n_tiles, partial);
         }
-        MBC_CUDA_TRY(cudaGetLastError());        const int64_t outs = n_slabs * M.n_mom * n_out;
-        const unsigned rg = (unsigned)std::min<int64_t>((outs + 7) / 8, 65535);
+        MBC_CUDA_TRY(cudaGetLastError());
+        // thousands of outputs per slab: one thread per output, coalesced
+        const int64_t outs = n_slabs * M.n_mom * n_out;
+        const unsigned rg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((outs + 255) / 256, (int64_t)nsm * 16));
         note_launch();
-        k_reduce_tiles<<<std::max(rg, 1u), 256, 0, stream>>>(partial, n_slabs, tps, M.n_mom, (int)n_out, F.n_t, 0, 1,
-                                                            (int)n_out, Pf);
+        k_reduce_tiles_cols<<<rg, 256, 0, stream>>>(partial, n_slabs, tps, M.n_mom, (int)n_out, F.n_t, 0, 1, (int)n_out,
+                                                    Pf);
         MBC_CUDA_TRY(cudaGetLastError());
     }
     // 2. recursion and contraction per item, a wave of W items at a time

@@ -11,6 +11,7 @@
 
 #include "device_common.cuh"
 #include "gen_ops.cuh"
+#include "mixed_common.cuh"
 #include "small_kernel.cuh"
 
 namespace mbc {
@@ -33,6 +34,12 @@ __device__ __forceinline__ bool item_site(const FieldDesc &F, const WaveDesc &wv
     return site < wv.v3;
 }
 
+// Per-site regions of the block kernels' shared memory are padded by one
+// element: the 16 sites of a warp then read the same entry from 16 distinct
+// banks (an unpadded 12 x 12 tile puts all of them in one bank).
+__host__ __device__ constexpr int tile_stride(int nrow, int nxi) { return nrow * nxi + 1; }
+__host__ __device__ constexpr int diquark_stride(int nxi) { return 3 * nxi * nxi + 1; }
+
 // Blocks for 16 sites per CTA (512 threads): thread = (site lane, entry slice).
 // The tile of a site has nrow sink rows (3 x Dirac dimension) and nxi source
 // columns (quark index over all sources).
@@ -43,8 +50,9 @@ __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, 
     using V = typename Tr::V;
     constexpr int NS = 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *S = reinterpret_cast<V *>(smem_raw);  // [NS][nrow*nxi]
-    V *Q = S + NS * nrow * nxi;              // [NS][3*nxi*nxi]
+    const int sst = tile_stride(nrow, nxi), qst = diquark_stride(nxi);
+    V *S = reinterpret_cast<V *>(smem_raw);  // [NS][sst]: nrow*nxi entries each
+    V *Q = S + NS * sst;                     // [NS][qst]: 3*nxi*nxi entries each
     const int sl = threadIdx.x % NS, slice = threadIdx.x / NS, nslice = blockDim.x / NS;
     const int w0 = blockIdx.x * NS;  // first site of this CTA within the wave
     const int nent = nrow * nxi, nq = nxi * nxi;
@@ -71,18 +79,18 @@ __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, 
         }
         for (int q = 0; q < 5; ++q) {
             int e = lane + 32 * q;
-            if (e < nent) S[s * nent + e] = Tr::from_d(make_double2(scalbn(sv[q].x, se), scalbn(sv[q].y, se)));
+            if (e < nent) S[s * sst + e] = Tr::from_d(make_double2(scalbn(sv[q].x, se), scalbn(sv[q].y, se)));
         }
         if (lane == 0) sexp_out[w0 + s] = se;
     }
     __syncthreads();
     for (int e = slice; e < 3 * nq; e += nslice) {
         int c = e / nq, r = e % nq;
-        Q[sl * 3 * nq + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
+        Q[sl * qst + e] = diquark(S + sl * sst, nxi, nxi, n_g2, c, r / nxi, r % nxi);
     }
     __syncthreads();
-    const V *Ss = S + sl * nent;
-    const V *Qs = Q + sl * 3 * nq;
+    const V *Ss = S + sl * sst;
+    const V *Qs = Q + sl * qst;
     const int per_spin = npair * nxi;
     for (int b = 0; b < 2; ++b) {
         if (b == 0 ? !need_p : !need_n) continue;
@@ -197,13 +205,8 @@ __global__ void __launch_bounds__(256) k_large_step(const uint32_t *__restrict__
 // operations at a time into per-warp shared-memory records (x, y, sign,
 // sign), so a term costs one broadcast shared load, one multiply-add per
 // operand address, two gathers and the arithmetic. W must be a multiple of 64.
-struct __align__(16) OpRec {
-    uint32_t x, y;  // rows of X and Y
-    uint64_t sg;    // (+-1, +-1)
-};
 __device__ __forceinline__ OpRec op_rec(uint32_t x, uint32_t y) {
-    const float s = __uint_as_float(0x3f800000u | ((y & 0x8000u) << 16));
-    return OpRec{x, y & 0x7fffu, f2_pack(s, s)};
+    return OpRec{x, y & 0x7fffu, f2_sign_pair((y & 0x8000u) != 0)};
 }
 
 template <int G>
@@ -416,6 +419,50 @@ __global__ void k_reduce_tiles(const double2 *__restrict__ partial, int64_t n_sl
             const int64_t oi = ((((int64_t)cfg * n_lists + list_idx) * n_t + tt) * n_mom + q) * comp_stride + c;
             out[oi] = make_double2(sr + cr, si + ci);
         }
+    }
+}
+
+// The same reduction for slabs with many outputs (momentum-projected blocks:
+// n_mom x 2 x block entries each, a few hundred tiles per slab): one thread
+// per output adds the slab's tiles in a fixed order, tile tl into partial sum
+// tl mod 4, then ((s0 + s1) + (s2 + s3)). Plain FP64 additions: GB300 issues
+// few FP64 operations per clock, and with hundreds of thousands of outputs a
+// compensated sum (six FP64 operations a term) costs more than the rest of
+// the step; the error of this order is below (tiles/4 + 2) ulp of the sum of
+// the magnitudes. Consecutive threads take consecutive outputs, so every load
+// of a warp is one contiguous 512 B segment. out as in k_reduce_tiles.
+__global__ void __launch_bounds__(256) k_reduce_tiles_cols(const double2 *__restrict__ partial, int64_t n_slabs,
+                                                           int tiles_per_slab, int n_mom, int n_comp, int n_t,
+                                                           int list_idx, int n_lists, int comp_stride,
+                                                           double2 *out) {
+    const int64_t per_slab = (int64_t)n_mom * n_comp;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_slabs * per_slab; o += stride) {
+        const int64_t slab = o / per_slab;
+        const int r = (int)(o % per_slab);
+        const double2 *p = partial + slab * tiles_per_slab * per_slab + r;
+        double2 acc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = make_double2(0.0, 0.0);
+        int tl = 0;
+        for (; tl + 4 <= tiles_per_slab; tl += 4) {
+            double2 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = __ldg(p + (int64_t)(tl + j) * per_slab);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] = make_double2(acc[j].x + v[j].x, acc[j].y + v[j].y);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (tl + j < tiles_per_slab) {
+                const double2 v = __ldg(p + (int64_t)(tl + j) * per_slab);
+                acc[j] = make_double2(acc[j].x + v.x, acc[j].y + v.y);
+            }
+        const int cfg = (int)(slab / n_t), tt = (int)(slab % n_t);
+        const int q = r / n_comp, c = r % n_comp;
+        const int64_t oi = ((((int64_t)cfg * n_lists + list_idx) * n_t + tt) * n_mom + q) * comp_stride + c;
+        out[oi] = make_double2((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
+                               (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
     }
 }
 

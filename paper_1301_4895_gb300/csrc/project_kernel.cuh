@@ -28,8 +28,8 @@ constexpr int kProjPad = 17;
 
 // Shared memory of k_project_blocks for tiles of 16 sites.
 inline size_t project_smem_bytes(int nrow, int nxi, int n_mom) {
-    return sizeof(double2) * (16 * (size_t)nrow * nxi + 16 * 3 * (size_t)nxi * nxi + 2 * (size_t)kProjChunk * kProjPad +
-                              16 * (size_t)n_mom);
+    return sizeof(double2) * (16 * (size_t)tile_stride(nrow, nxi) + 16 * (size_t)diquark_stride(nxi) +
+                              2 * (size_t)kProjChunk * kProjPad + 16 * (size_t)n_mom);
 }
 
 __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
@@ -39,9 +39,10 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
                                                         double2 *__restrict__ partial) {
     constexpr int NS = 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2 *S = reinterpret_cast<double2 *>(smem_raw);  // [NS][nrow*nxi]
-    double2 *Q = S + NS * nrow * nxi;                    // [NS][3*nxi*nxi]
-    double2 *Fb = Q + NS * 3 * nxi * nxi;                // [2][kProjChunk][kProjPad]: block values of the chunk
+    const int sst = tile_stride(nrow, nxi), qst = diquark_stride(nxi);
+    double2 *S = reinterpret_cast<double2 *>(smem_raw);  // [NS][sst]
+    double2 *Q = S + NS * sst;                    // [NS][3*nxi*nxi]
+    double2 *Fb = Q + NS * qst;                          // [2][kProjChunk][kProjPad]: block values of the chunk
     double2 *Ph = Fb + 2 * kProjChunk * kProjPad;        // [NS][n_mom]: the tile's phases
     const int sl = threadIdx.x % NS, slice = threadIdx.x / NS, nslice = blockDim.x / NS;
     const int nent = nrow * nxi, nq = nxi * nxi;
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
             const bool live = site < v3;
             const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * site_elems(F);
             for (int e = lane; e < nent; e += 32)
-                S[s * nent + e] = live ? load_prop(F, base, tile_index(F, e, nxi)) : make_double2(0, 0);
+                S[s * sst + e] = live ? load_prop(F, base, tile_index(F, e, nxi)) : make_double2(0, 0);
         }
         for (int o = threadIdx.x; o < NS * M.n_mom; o += blockDim.x) {
             const int site = tin * NS + o / M.n_mom;
@@ -67,13 +68,13 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
         __syncthreads();
         for (int e = slice; e < 3 * nq; e += nslice) {
             const int c = e / nq, r = e % nq;
-            Q[sl * 3 * nq + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
+            Q[sl * qst + e] = diquark(S + sl * sst, nxi, nxi, n_g2, c, r / nxi, r % nxi);
         }
         __syncthreads();
         const int site = tin * NS + sl;
         const bool live = site < v3;
-        const double2 *Ss = S + sl * nent;
-        const double2 *Qs = Q + sl * 3 * nq;
+        const double2 *Ss = S + sl * sst;
+        const double2 *Qs = Q + sl * qst;
         const int per_spin = npair * nxi;
         for (int e0 = 0; e0 < block_size; e0 += kProjChunk) {
             // 1. block values of the chunk's entries for the tile's sites
@@ -123,8 +124,8 @@ __global__ void __launch_bounds__(512) k_project_blocks(FieldDesc F, MomDesc M, 
 
 // Shared memory of k_project_blocks_mx (FP32 values) for tiles of 16 sites.
 inline size_t project_smem_bytes_mx(int nrow, int nxi, int n_mom) {
-    return sizeof(float2) * (16 * (size_t)nrow * nxi + 16 * 3 * (size_t)nxi * nxi + 2 * (size_t)kProjChunk * kProjPad +
-                             16 * (size_t)n_mom);
+    return sizeof(float2) * (16 * (size_t)tile_stride(nrow, nxi) + 16 * (size_t)diquark_stride(nxi) +
+                             2 * (size_t)kProjChunk * kProjPad + 16 * (size_t)n_mom);
 }
 
 // The same projection for the mixed path: the tile, the diquark and the
@@ -138,9 +139,10 @@ __global__ void __launch_bounds__(512) k_project_blocks_mx(FieldDesc F, MomDesc 
     constexpr int NS = 16;
     using Acc = MixedTraits::Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *S = reinterpret_cast<float2 *>(smem_raw);  // [NS][nrow*nxi]
-    float2 *Q = S + NS * nrow * nxi;                   // [NS][3*nxi*nxi]
-    float2 *Fb = Q + NS * 3 * nxi * nxi;               // [2][kProjChunk][kProjPad]
+    const int sst = tile_stride(nrow, nxi), qst = diquark_stride(nxi);
+    float2 *S = reinterpret_cast<float2 *>(smem_raw);  // [NS][sst]
+    float2 *Q = S + NS * sst;                   // [NS][3*nxi*nxi]
+    float2 *Fb = Q + NS * qst;                         // [2][kProjChunk][kProjPad]
     float2 *Ph = Fb + 2 * kProjChunk * kProjPad;       // [NS][n_mom]
     const int sl = threadIdx.x % NS, slice = threadIdx.x / NS, nslice = blockDim.x / NS;
     const int nent = nrow * nxi, nq = nxi * nxi;
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(512) k_project_blocks_mx(FieldDesc F, MomDesc 
             const int64_t base = cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * site_elems(F);
             for (int e = lane; e < nent; e += 32) {
                 const double2 v = live ? load_prop(F, base, tile_index(F, e, nxi)) : make_double2(0, 0);
-                S[s * nent + e] = make_float2((float)v.x, (float)v.y);
+                S[s * sst + e] = make_float2((float)v.x, (float)v.y);
             }
         }
         for (int o = threadIdx.x; o < NS * M.n_mom; o += blockDim.x) {
@@ -169,13 +171,13 @@ __global__ void __launch_bounds__(512) k_project_blocks_mx(FieldDesc F, MomDesc 
         __syncthreads();
         for (int e = slice; e < 3 * nq; e += nslice) {
             const int c = e / nq, r = e % nq;
-            Q[sl * 3 * nq + e] = diquark(S + sl * nent, nxi, nxi, n_g2, c, r / nxi, r % nxi);
+            Q[sl * qst + e] = diquark(S + sl * sst, nxi, nxi, n_g2, c, r / nxi, r % nxi);
         }
         __syncthreads();
         const int site = tin * NS + sl;
         const bool live = site < v3;
-        const float2 *Ss = S + sl * nent;
-        const float2 *Qs = Q + sl * 3 * nq;
+        const float2 *Ss = S + sl * sst;
+        const float2 *Qs = Q + sl * qst;
         const int per_spin = npair * nxi;
         for (int e0 = 0; e0 < block_size; e0 += kProjChunk) {
             for (int el = slice; el < kProjChunk; el += nslice) {

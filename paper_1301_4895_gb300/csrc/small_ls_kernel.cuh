@@ -3,6 +3,7 @@
 // its own source here, apart from the FP64 kernel.
 #pragma once
 
+#include "mixed_common.cuh"
 #include "small_kernel.cuh"
 
 namespace mbc {
@@ -11,10 +12,12 @@ namespace mbc {
 // A CTA owns a tile of 32 sites, lane l of every warp works on site l; all
 // per-site values are rows of 32 lanes in shared memory ([entry][lane], 8 B
 // per lane), so every access of a warp is one conflict-free row. The warps
-// split the output components of each step (warp-uniform op stream, loaded
-// cooperatively and broadcast by shuffles); steps with fewer outputs than
-// warps split each output's terms over several warps and combine the
-// compensated partials in a fixed order.
+// split the output components of each step; a warp's lanes decode 32
+// operations at a time into the warp's records (row offsets and the sign as
+// a +-1 pair, OpRec), which every lane then reads by broadcast; steps with
+// fewer outputs than warps split each output's terms over several warps and
+// combine the compensated partials in a fixed order. Shared memory: the
+// site region and 64 partial rows of 32 lanes, then 32 records per warp.
 
 // RN(d * 2^e) as FP32 from the bits of an FP64 value, integer operations only
 // (GB300's FP64 pipe is 1/64 of FP32). Results below the FP32 normal range
@@ -57,6 +60,8 @@ __global__ void __launch_bounds__(1024, 1)
     __shared__ int sexp_s[32];
     const int NW = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // after the site region and the 64 partial rows: 32 operation records per warp
+    OpRec *rec = reinterpret_cast<OpRec *>(R + (int64_t)(B.site_stride + 64) * 32) + warp * 32;
     const int V3 = F.lx * F.ly * F.lz;
     const unsigned full = 0xffffffffu;
     const int tiles_per_slab = B.tiles_per_slab;
@@ -189,13 +194,19 @@ __global__ void __launch_bounds__(1024, 1)
                 for (int zz = 0; zz < n_out; ++zz, op_ptr += len) {
                     for (int b0 = 0; b0 < len; b0 += 32) {
                         const int nb = min(32, len - b0);
-                        const uint32_t mine = lane < nb ? __ldg(op_ptr + b0 + lane) : 0u;
+                        // operands are byte offsets of 256 B rows, the sign is
+                        // bit 0: decoded once per batch into the warp's records
+                        __syncwarp();
+                        if (lane < nb) {
+                            const uint32_t op = __ldg(op_ptr + b0 + lane);
+                            rec[lane] = OpRec{op & 0xff00u, op >> 16, f2_sign_pair(op & 1u)};
+                        }
+                        __syncwarp();
     #pragma unroll 4
                         for (int q = 0; q < nb; ++q) {
-                            // operands are byte offsets of 256 B rows, the sign is bit 0
-                            const uint32_t op = __shfl_sync(full, mine, q);
-                            acc.fma(*reinterpret_cast<const V *>(Xb + (op & 0xff00u)),
-                                    *reinterpret_cast<const V *>(Yb + (op >> 16)), op << 31);
+                            const OpRec r = rec[q];
+                            acc.fma_sg(*reinterpret_cast<const V *>(Xb + r.x), *reinterpret_cast<const V *>(Yb + r.y),
+                                       r.sg);
                         }
                     }
                     if (part < 0) {
@@ -206,7 +217,7 @@ __global__ void __launch_bounds__(1024, 1)
                 if (split > 1) {
                     if (part >= 0) {
                         ROW(P.part_off + 2 * warp) = f2_unpack(acc.s);      // (sum re, sum im)
-                        ROW(P.part_off + 2 * warp + 1) = f2_unpack(acc.c);  // their compensations
+                        ROW(P.part_off + 2 * warp + 1) = f2_unpack(acc.n);  // their negated compensations
                     }
                     __syncthreads();
                     for (int zz = warp; zz < d.n_z; zz += NW) {
