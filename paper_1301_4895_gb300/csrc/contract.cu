@@ -802,7 +802,9 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
     // FP64 blocks and sums for the FP64 path, FP32 products with compensated
     // FP32 sums for the mixed path
     const bool mx = sizeof(V) == sizeof(float2);
-    const void *pkern = mx ? (const void *)k_project_blocks_mx : (const void *)k_project_blocks;
+    if (mx && nxi != 6 && nxi != 12) return MBC_ERR_UNSUPPORTED;  // 3 x Dirac dimension x sources
+    const void *pkern = !mx ? (const void *)k_project_blocks
+                            : nxi == 6 ? (const void *)k_project_blocks_mx<6> : (const void *)k_project_blocks_mx<12>;
     const size_t smem = mx ? project_smem_bytes_mx(nrow, nxi, M.n_mom) : project_smem_bytes(nrow, nxi, M.n_mom);
     {
         int per_sm = 0;
@@ -814,10 +816,12 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         {
             TimedLaunch tl(stream);
             note_launch();
-            if (mx)
-                k_project_blocks_mx<<<(unsigned)grid, 512, smem, stream>>>(
-                    F, M, phase, nrow, nxi, n_g2(L), bs, (int)binom64(nxi, 2), L->need_block[0], L->need_block[1],
-                    tps, n_tiles, partial);
+            if (mx && nxi == 6)
+                k_project_blocks_mx<6><<<(unsigned)grid, 512, smem, stream>>>(
+                    F, M, phase, nrow, n_g2(L), bs, L->need_block[0], L->need_block[1], tps, n_tiles, partial);
+            else if (mx)
+                k_project_blocks_mx<12><<<(unsigned)grid, 512, smem, stream>>>(
+                    F, M, phase, nrow, n_g2(L), bs, L->need_block[0], L->need_block[1], tps, n_tiles, partial);
             else
                 k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nrow, nxi, n_g2(L), bs,
                                                                         (int)binom64(nxi, 2), L->need_block[0],

@@ -131,12 +131,16 @@ inline size_t project_smem_bytes_mx(int nrow, int nxi, int n_mom) {
 // The same projection for the mixed path: the tile, the diquark and the
 // blocks in FP32 products, the phase-weighted sum over the tile's 16 sites
 // with compensated (two-word) FP32 accumulation in the same fixed order, the
-// tile partial handed to the FP64 reduction over tiles.
+// tile partial handed to the FP64 reduction over tiles. The number of
+// quark-index columns is a template parameter (6 or 12), so the decoding
+// of an entry into (spin, pair, single) divides by constants.
+template <int NXI>
 __global__ void __launch_bounds__(512) k_project_blocks_mx(FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
-                                                           int nrow, int nxi, int n_g2, int block_size, int npair,
-                                                           int need_p, int need_n, int tiles_per_slab, int64_t n_tiles,
+                                                           int nrow, int n_g2, int block_size, int need_p, int need_n,
+                                                           int tiles_per_slab, int64_t n_tiles,
                                                            double2 *__restrict__ partial) {
     constexpr int NS = 16;
+    constexpr int nxi = NXI, npair = NXI * (NXI - 1) / 2;
     using Acc = MixedTraits::Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int sst = tile_stride(nrow, nxi), qst = diquark_stride(nxi);
