@@ -816,12 +816,13 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         {
             TimedLaunch tl(stream);
             note_launch();
+            float2 *partial_mx = reinterpret_cast<float2 *>(partial);  // the mixed path's FP32 partials
             if (mx && nxi == 6)
                 k_project_blocks_mx<6><<<(unsigned)grid, 512, smem, stream>>>(
-                    F, M, phase, nrow, n_g2(L), bs, L->need_block[0], L->need_block[1], tps, n_tiles, partial);
+                    F, M, phase, nrow, n_g2(L), bs, L->need_block[0], L->need_block[1], tps, n_tiles, partial_mx);
             else if (mx)
                 k_project_blocks_mx<12><<<(unsigned)grid, 512, smem, stream>>>(
-                    F, M, phase, nrow, n_g2(L), bs, L->need_block[0], L->need_block[1], tps, n_tiles, partial);
+                    F, M, phase, nrow, n_g2(L), bs, L->need_block[0], L->need_block[1], tps, n_tiles, partial_mx);
             else
                 k_project_blocks<<<(unsigned)grid, 512, smem, stream>>>(F, M, phase, nrow, nxi, n_g2(L), bs,
                                                                         (int)binom64(nxi, 2), L->need_block[0],
@@ -832,8 +833,12 @@ mbc_status run_projected(const mbc_term_list *L, const DeviceCache *c, const Fie
         const int64_t outs = n_slabs * M.n_mom * n_out;
         const unsigned rg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((outs + 255) / 256, (int64_t)nsm * 16));
         note_launch();
-        k_reduce_tiles_cols<<<rg, 256, 0, stream>>>(partial, n_slabs, tps, M.n_mom, (int)n_out, F.n_t, 0, 1, (int)n_out,
-                                                    Pf);
+        if (mx)
+            k_reduce_tiles_cols_mx<<<rg, 256, 0, stream>>>(reinterpret_cast<const float2 *>(partial), n_slabs, tps,
+                                                           (int64_t)M.n_mom * n_out, Pf);
+        else
+            k_reduce_tiles_cols<<<rg, 256, 0, stream>>>(partial, n_slabs, tps, M.n_mom, (int)n_out, F.n_t, 0, 1,
+                                                        (int)n_out, Pf);
         MBC_CUDA_TRY(cudaGetLastError());
     }
     // 2. recursion and contraction per item, a wave of W items at a time

@@ -9,7 +9,8 @@
 //                      entry) -> tile partials, reduced over tiles by
 //                      k_reduce_tiles (compensated, fixed order);
 //   k_project_blocks_mx the same with FP32 products and compensated FP32
-//                      sums (mixed precision);
+//                      sums (mixed precision), FP32 tile partials reduced by
+//                      k_reduce_tiles_cols_mx;
 //   k_load_proj_blocks copies the summed blocks of a wave of items into the
 //                      [component][item] layout of the wave kernels (MIXED:
 //                      exact power-of-two scaling per item);
@@ -131,14 +132,14 @@ inline size_t project_smem_bytes_mx(int nrow, int nxi, int n_mom) {
 // The same projection for the mixed path: the tile, the diquark and the
 // blocks in FP32 products, the phase-weighted sum over the tile's 16 sites
 // with compensated (two-word) FP32 accumulation in the same fixed order, the
-// tile partial handed to the FP64 reduction over tiles. The number of
+// tile partial rounded once to FP32 for the reduction over tiles. The number of
 // quark-index columns is a template parameter (6 or 12), so the decoding
 // of an entry into (spin, pair, single) divides by constants.
 template <int NXI>
 __global__ void __launch_bounds__(512) k_project_blocks_mx(FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
                                                            int nrow, int n_g2, int block_size, int need_p, int need_n,
                                                            int tiles_per_slab, int64_t n_tiles,
-                                                           double2 *__restrict__ partial) {
+                                                           float2 *__restrict__ partial) {
     constexpr int NS = 16;
     constexpr int nxi = NXI, npair = NXI * (NXI - 1) / 2;
     using Acc = MixedTraits::Acc;
@@ -216,10 +217,32 @@ __global__ void __launch_bounds__(512) k_project_blocks_mx(FieldDesc F, MomDesc 
                 Acc acc;
                 acc.zero();
                 for (int w = 0; w < NS; ++w) acc.fma(Ph[w * M.n_mom + q], fv[w], 0u);
-                partial[(tile * M.n_mom + q) * (int64_t)n_out + b * block_size + e] = acc.value();
+                partial[(tile * M.n_mom + q) * (int64_t)n_out + b * block_size + e] = acc.store();
             }
             __syncthreads();
         }
+    }
+}
+
+// The reduction over tiles of the mixed projection: one thread per output
+// (consecutive threads, consecutive outputs: coalesced) adds the slab's FP32
+// tile partials in tile order with a packed Kahan step on (re, im); the sum
+// goes out in FP64, Pf[slab][per_slab].
+__global__ void __launch_bounds__(256) k_reduce_tiles_cols_mx(const float2 *__restrict__ partial, int64_t n_slabs,
+                                                              int tiles_per_slab, int64_t per_slab,
+                                                              double2 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_slabs * per_slab; o += stride) {
+        const int64_t slab = o / per_slab, r = o % per_slab;
+        const float2 *p = partial + slab * tiles_per_slab * per_slab + r;
+        MixedTraits::Acc acc;
+        acc.zero();
+#pragma unroll 4
+        for (int tl = 0; tl < tiles_per_slab; ++tl) {
+            const float2 v = __ldg(p + (int64_t)tl * per_slab);
+            f2_kahan(acc.s, acc.n, f2_pack(v.x, v.y));
+        }
+        out[o] = acc.value();
     }
 }
 
