@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(1024, 1)
                 const char *Xb = reinterpret_cast<const char *>(R + (d.x_off << 5) + lane);
                 const char *Yb = reinterpret_cast<const char *>(R + (d.y_off << 5) + lane);
                 V *Zl = R + (d.z_off << 5) + lane;
-                // output by output: each output's k terms are contiguous, loaded
-                // 32 at a time and broadcast by shuffles; no per-term branch
+                // output by output: each output's k terms are contiguous, decoded
+                // 32 at a time into the warp's records; no per-term branch
                 const int n_out = part < 0 ? (int)((o_end - o_begin) / d.k) : 1;
                 const int len = part < 0 ? d.k : (int)(o_end - o_begin);
                 const uint32_t *op_ptr = ops + o_begin;
