@@ -40,19 +40,24 @@ struct Writer {
 
 struct Reader {
     FILE *f;
+    uint64_t left;  // bytes of the file not read yet
     bool ok = true;
     void bytes(void *p, size_t n) {
+        if (ok && n > left) ok = false;
         if (ok && n && std::fread(p, 1, n, f) != n) ok = false;
+        if (ok) left -= n;
     }
     template <class T>
     void pod(T &v) {
         bytes(&v, sizeof(T));
     }
+    // a length is checked against the bytes left before anything is
+    // allocated, so a damaged length field cannot request a huge vector
     template <class T>
-    void vec(std::vector<T> &v, uint64_t max_elems = (uint64_t)1 << 36) {
+    void vec(std::vector<T> &v) {
         uint64_t n = 0;
         pod(n);
-        if (!ok || n > max_elems) {
+        if (!ok || n > left / sizeof(T)) {
             ok = false;
             return;
         }
@@ -60,6 +65,14 @@ struct Reader {
         bytes(v.data(), (size_t)n * sizeof(T));
     }
 };
+
+// size of an open file, or -1
+int64_t file_size(FILE *f) {
+    if (std::fseek(f, 0, SEEK_END) != 0) return -1;
+    const long n = std::ftell(f);
+    if (n < 0 || std::fseek(f, 0, SEEK_SET) != 0) return -1;
+    return (int64_t)n;
+}
 
 template <class IO, class L>
 void fields(IO &io, L &list) {
@@ -203,7 +216,13 @@ mbc_status mbc_load_term_list(const char *path, mbc_term_list **out) {
         std::fclose(f);
         return MBC_ERR_OOM;
     }
-    Reader r{f};
+    const int64_t size = file_size(f);
+    if (size < 0) {
+        std::fclose(f);
+        delete L;
+        return MBC_ERR_INVALID_ARG;
+    }
+    Reader r{f, (uint64_t)size};
     mbc_status st = MBC_OK;
     try {
         if (!header_ok(r)) {

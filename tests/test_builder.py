@@ -339,3 +339,38 @@ def test_term_list_cache(tmp_path):
     assert b.stats() == a.stats() and b.components() == a.components()
     c = mbc.build_term_list(**dict(kw, spins=[((0, 1, 1), (0, 1, 1))]), cache_dir=str(tmp_path))
     assert len(list(tmp_path.iterdir())) == 2 and c.components() != a.components()
+
+
+def test_term_list_files_damaged_anywhere(tmp_path):
+    """Loading a damaged file never crashes and never allocates more than the
+    file holds: every 8-byte word set to a huge length, and random byte
+    flips, either load (the loader has checked every index the kernels use)
+    or are refused with an error."""
+    import numpy as np
+    a = mbc.build_term_list(2, 1, 2, spins=[((0, 1, 0), (0, 1, 1))])
+    src = tmp_path / "a.bin"
+    a.save(str(src))
+    raw = bytearray(src.read_bytes())
+    bad = tmp_path / "bad.bin"
+    refused = 0
+    huge = ((1 << 36) - 1).to_bytes(8, "little")
+    for off in range(16, len(raw) - 8, 8):
+        damaged = bytearray(raw)
+        damaged[off:off + 8] = huge
+        bad.write_bytes(bytes(damaged))
+        try:
+            mbc.load_term_list(str(bad))
+        except mbc.MbcError:
+            refused += 1
+    assert refused > 0
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        damaged = bytearray(raw)
+        for pos in rng.integers(16, len(raw), size=int(rng.integers(1, 5))):
+            damaged[int(pos)] = int(rng.integers(0, 256))
+        bad.write_bytes(bytes(damaged))
+        try:
+            b = mbc.load_term_list(str(bad))
+            b.stats()
+        except mbc.MbcError:
+            pass
