@@ -312,9 +312,10 @@ typedef struct {
  *                (Sec. 2 sink function s(x)), and the recursion runs once
  *                per (configuration, time slice, momentum) on those blocks.
  *                The blocks and their site sums are FP64 in the FP64 path;
- *                the mixed path forms them with FP32 products and sums each
- *                16-site tile with compensated FP32 accumulation, the tiles
- *                in FP64. Lists built
+ *                the mixed path forms them with FP32 products, sums each
+ *                16-site tile with compensated FP32 accumulation, rounds the
+ *                tile sum once to FP32 and adds the tiles with compensated
+ *                FP32 accumulation, the result in FP64. Lists built
  *                with n_sinks = N_k > 1 (Sec. 6 sink functions s_1 .. s_N_k)
  *                take the momenta in groups of N_k (n_mom a multiple of N_k,
  *                all lists of the call with the same N_k): sink function k
