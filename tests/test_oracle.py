@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from conftest import read_golden, spins_of
-from oracle import counts, gamma, minors, recursion, site_sum, wick
+from oracle import counts, gamma, grassmann, minors, recursion, site_sum, wick
 
 
 def rand_prop(rng, n=None):
@@ -282,21 +282,50 @@ def test_site_sum_phases(rng):
         assert np.allclose(out[q], fft[nz % lz, ny % ly, nx % lx], rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("bs,alpha,D", [("P", (0,), 4), ("N", (3,), 4), ("PN", (0, 1), 4), ("PN", (1, 1), 2),
+                                         ("NN", (0, 1), 4), ("PP", (2, 3), 4), ("PPN", (0, 1, 1), 2),
+                                         ("PNN", (1, 0, 1), 2), ("PPNN", (0, 1, 0, 1), 2)])
+def test_exterior_algebra_l_equals_enumeration(bs, alpha, D):
+    """L of eq. tensor_L two ways: the coefficients of the product of baryon
+    elements in the exterior algebra (grassmann.py) equal O2's enumeration of
+    G tuples with the sorting signs, entry by entry (Tables 4/5 counts)."""
+    assert grassmann.l_tensor(bs, alpha, D) == minors.l_tensor(bs, alpha, D)
+
+
+def test_exterior_algebra_saturated_values():
+    """Saturated nuclei have one L entry (N_L = 1, Tables 4 and 5): nonrel 4He
+    fills the 6 upper u and d indices, 8Be all 12 of each."""
+    he4 = grassmann.l_tensor("PPNN", (0, 1, 0, 1), 2)
+    assert list(he4) == [(tuple(range(6)), tuple(range(6)))]
+    assert abs(list(he4.values())[0]) == 360  # 129600 = 360^2, the nonrel 4He constant
+    be8 = grassmann.l_tensor("PPPPNNNN", (0, 1, 2, 3, 0, 1, 2, 3), 4)
+    assert list(be8) == [(tuple(range(12)), tuple(range(12)))]
+
+
+def near_identity(rng, eps, n):
+    return np.eye(12)[None] + eps * rand_prop(rng, n)
+
+
 @pytest.mark.slow
 def test_be8_saturated_ratio(rng):
     """8Be fills all 12 u and 12 d spinor-colour states at sink and source, so
-    C = K det S_u det S_d with one constant K for every propagator (the
+    C = K det S_u det S_d with K = (L value)^2 for every propagator (the
     saturation that also trivialises the determinant method, Sec. 8); the
-    recursion needs every one of the 448,496,928 operations (Tables 1, 5)."""
+    recursion needs every one of the 448,496,928 operations (Tables 1, 5).
+    Near the identity C is of the order of sum|terms| (no cancellation), so
+    the K-relative tolerance 1e-12 pins O3's value at A = 8: a dropped term,
+    a wrong sign or a wrong normalisation moves K far beyond it."""
     sp = (0, 1, 2, 3, 0, 1, 2, 3)
     plan = recursion.Plan(4, 4, 4, requests=[(sp, sp)])
     assert plan.ops()[0] == 448496928
     assert plan.n_l() == [1]
-    S = rand_prop(rng, 3)
+    (L,) = grassmann.l_tensor("PPPPNNNN", sp, 4).values()
+    K = float(L) ** 2
+    S = np.concatenate([np.eye(12)[None], near_identity(rng, 0.02, 2)])
     C, sc = plan.evaluate(S, batch=3)
     ratio = C[:, 0] / np.linalg.det(S) ** 2
-    tol = 1e-13 * sc[:, 0] / abs(np.linalg.det(S) ** 2)
-    assert np.all(abs(ratio - ratio[0]) <= tol + tol[0])
+    assert np.all(np.abs(ratio - K) <= 1e-12 * K), ratio / K - 1
+    assert np.all(np.abs(C[:, 0]) >= 0.1 * sc[:, 0])  # the tolerance is far below |C|
 
 
 @pytest.mark.slow
