@@ -3,17 +3,23 @@
 Tolerances (the bounds the method must meet): |dC| / sum|terms| <= 1e-13
 for the FP64 path and <= 1e-6 for the mixed FP32-product / compensated
 path, where sum|terms| is the oracle's magnitude recursion summed over the
-sites of the slab.
+sites of the slab. Every comparison goes through ``parity.check``, which
+also refuses inputs on which the bound could not fail (a zero output must
+fail every test): FP64 runs on the configurations' Gaussian propagators,
+where the bound discriminates, and both precisions run on near-identity
+propagators from the same draws (``gpu_helpers.legs``), where it
+discriminates for the mixed bound too. 8Be and the saturated nuclei are
+also checked against the closed form C = K det S_u det S_d on full slabs.
 """
 import numpy as np
 import pytest
 
+import parity
 import synth
-from gpu_helpers import WORST, max_rel_err, oracle_plan, oracle_slab, record
+from gpu_helpers import EPS, WORST, legs, oracle_plan, oracle_slab, record
+from parity import TOL
 
 pytestmark = pytest.mark.gpu
-
-TOL = {0: 1e-13, 1: 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -38,12 +44,15 @@ def run(mbc, field, lists, precision, **kw):
 
 def check_slabs(mbc, field, lists, specs, dims, precisions=(0, 1), moms=((0, 0, 0),), t_sel=None, t0=0, t1=0,
                 tune=None):
-    """Compare the GPU result of every listed nucleus on the selected slabs."""
+    """Compare the GPU result of every listed nucleus on the selected slabs.
+    Returns (outputs per precision, worst error per precision, smallest
+    |C| / sum|terms| over the compared slabs)."""
     nt = field.shape[1]
     t1e = nt if t1 == 0 else t1
     outs = {p: run(mbc, field, lists, p, moms=moms, t0=t0, t1=t1, tune=tune) for p in precisions}
     t_sel = list(range(t0, t1e)) if t_sel is None else t_sel
     worst = {p: 0.0 for p in precisions}
+    cond = np.inf
     for li, (tl, (n_p, n_n, D)) in enumerate(zip(lists, specs)):
         comps = tl.components()
         if not comps:
@@ -54,60 +63,77 @@ def check_slabs(mbc, field, lists, specs, dims, precisions=(0, 1), moms=((0, 0, 
         for cfg in range(field.shape[0]):
             for t in t_sel:
                 ref, scale = oracle_slab(plan, field[cfg, t], dims, list(moms))
+                cond = min(cond, parity.margin(ref, scale[None, :]))
                 for p in precisions:
                     got = outs[p][cfg, li, t - t0, :, : len(comps)]
-                    e = max_rel_err(got, ref, scale)
+                    e = parity.check(got, ref, scale[None, :], p, what=f"({n_p},{n_n}) D={D} cfg {cfg} t {t}")
                     worst[p] = max(worst[p], e)
                     record(f"({n_p},{n_n}) D={D}", p, e)
-                    assert e <= TOL[p], (n_p, n_n, D, cfg, t, p, e)
-    return outs, worst
+    return outs, worst, cond
+
+
+def check_legs(mbc, seed, n_cfg, nt, dims, lam, lists, specs, dtype=np.complex128, gauss=True, **kw):
+    """check_slabs on both input legs (gpu_helpers.legs)."""
+    for field, precs in legs(seed, n_cfg, nt, dims, lam, dtype=dtype, gauss=gauss):
+        check_slabs(mbc, field, lists, specs, dims, precisions=precs, **kw)
 
 
 def test_deuteron_config(mbc):
     """4^3 x 8, seed 0, exp(-0.5 t), all 16 nonrelativistic pn components."""
     dims = (4, 4, 4)
-    field = synth.field(0, 1, 8, dims, 0.5)
     tl = mbc.build_term_list(1, 1, 2)
-    check_slabs(mbc, field, [tl], [(1, 1, 2)], dims)
+    check_legs(mbc, 0, 1, 8, dims, 0.5, [tl], [(1, 1, 2)])
+
+
+def _he4_nonrel_K():
+    """C / (det S_u[up; up] det S_d[up; up]) for nonrelativistic 4He: the
+    square of its single L entry (exterior-algebra oracle)."""
+    from oracle import grassmann
+    (L,) = grassmann.l_tensor("PPNN", (0, 1, 0, 1), 2).values()
+    return float(L) ** 2
 
 
 def test_nonrel_he3_he4_full_size(mbc):
     """16^3 x 32, seed 1, exp(-0.4 t): 3He and 4He in one call, as timed by the
-    benchmark; oracle on sampled slabs, the 4He determinant form on all."""
+    benchmark; the oracle on sampled slabs and the 4He closed form
+    C(x) = K det(S_x[up; up])^2 (saturated upper components) on every slab."""
     dims = (16, 16, 16)
-    field = synth.field(1, 1, 32, dims, 0.4)
     he3 = mbc.build_term_list(2, 1, 2)
     he4 = mbc.build_term_list(2, 2, 2)
-    outs, worst = check_slabs(mbc, field, [he3, he4], [(2, 1, 2), (2, 2, 2)], dims, t_sel=[0, 17, 31])
-    # every slab: C_4He(x) = K det(S_x[up; up])^2 (saturated upper components)
-    plan = oracle_plan(2, 2, 2, he4.components())
-    s0 = field[0, 0, 0, 0, 0]
-    c0, _ = plan.evaluate(s0[None])
-    K = c0[0, 0] / np.linalg.det(s0[:6, :6]) ** 2
-    for t in range(32):
-        d = np.linalg.det(field[0, t, ..., :6, :6].reshape(-1, 6, 6))
-        ref = K * np.sum(d ** 2)
-        scale = np.abs(K) * np.sum(np.abs(d) ** 2)
-        # the determinant form is exact; |K| sum |det|^2 is far below sum|terms|
-        # (random propagators cancel strongly), so only the FP64 path is held to it
-        assert abs(outs[0][0, 1, t, 0, 0] - ref) <= 1e-9 * scale, t
+    K = _he4_nonrel_K()
+    for field, precs in legs(1, 1, 32, dims, 0.4):
+        outs, worst, cond = check_slabs(mbc, field, [he3, he4], [(2, 1, 2), (2, 2, 2)], dims, precisions=precs,
+                                        t_sel=[0, 17, 31])
+        near = 1 in precs
+        for t in range(32):
+            d2 = np.linalg.det(field[0, t, ..., :6, :6].reshape(-1, 6, 6)) ** 2
+            ref = K * np.sum(d2)
+            mag = K * np.sum(np.abs(d2))
+            for p in precs:
+                if near:
+                    # sum|terms| <= |C| / cond on the sampled slabs: the bound
+                    # TOL sum|terms| as a relative tolerance on these inputs
+                    assert cond >= 0.1
+                    parity.check_rel(outs[p][0, 1, t, 0, 0], ref, 10 * TOL[p], what=f"4He closed form t {t}")
+                else:
+                    # Gaussian slabs cancel against |K| sum|det|^2 by ~1e-2,
+                    # far below sum|terms|; the FP64 path still meets 1e-9 of it
+                    assert abs(outs[p][0, 1, t, 0, 0] - ref) <= 1e-9 * mag, t
 
 
 def test_ragged_lattice_momenta_and_subrange(mbc):
     dims = (3, 5, 7)  # 105 sites: no multiple of any tile width
-    field = synth.field(11, 2, 4, dims, 0.3)
     lists = [mbc.build_term_list(1, 1, 2), mbc.build_term_list(2, 2, 2), mbc.build_term_list(2, 1, 2)]
     specs = [(1, 1, 2), (2, 2, 2), (2, 1, 2)]
     moms = ((0, 0, 0), (1, 0, 0), (0, 2, 1), (-1, 1, 3))
-    check_slabs(mbc, field, lists, specs, dims, moms=moms, t0=1, t1=3)
+    check_legs(mbc, 11, 2, 4, dims, 0.3, lists, specs, moms=moms, t0=1, t1=3)
 
 
 def test_complex64_storage(mbc):
     dims = (4, 4, 4)
-    field = synth.field(3, 1, 3, dims, 0.4, dtype=np.complex64)
     lists = [mbc.build_term_list(1, 1, 2), mbc.build_term_list(2, 2, 2)]
     # the oracle sees the stored (rounded) values promoted to FP64
-    check_slabs(mbc, field, lists, [(1, 1, 2), (2, 2, 2)], dims)
+    check_legs(mbc, 3, 1, 3, dims, 0.4, lists, [(1, 1, 2), (2, 2, 2)], dtype=np.complex64)
 
 
 def test_host_memory_mode_and_determinism(mbc):
@@ -142,55 +168,90 @@ def test_pauli_forbidden_list_is_zero(mbc):
 
 def test_he4_rel_single_component_large_path(mbc):
     dims = (2, 2, 2)
-    field = synth.field(2, 1, 2, dims, 0.4)
     sp = (0, 1, 0, 1)
     tl = mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])
-    check_slabs(mbc, field, [tl], [(2, 2, 4)], dims)
+    check_legs(mbc, 2, 1, 2, dims, 0.4, [tl], [(2, 2, 4)])
 
 
 def test_large_path_multiple_waves_ragged(mbc):
     dims = (3, 3, 3)  # 27 sites, padded to 32 per slab
-    field = synth.field(7, 2, 2, dims, 0.4)
     sp = (0, 1, 0, 1)
     tl = mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])
-    check_slabs(mbc, field, [tl], [(2, 2, 4)], dims, tune={"wave_sites": 32, "regime": 2},
-                moms=((0, 0, 0), (1, 1, 0)))
+    check_legs(mbc, 7, 2, 2, dims, 0.4, [tl], [(2, 2, 4)], tune={"wave_sites": 32, "regime": 2},
+               moms=((0, 0, 0), (1, 1, 0)))
 
 
 def test_large_path_on_nonrel_lists(mbc):
     """Force the wave kernels on lists that normally take the shared-memory
     kernel: both regimes must meet the bound."""
     dims = (4, 4, 4)
-    field = synth.field(8, 1, 2, dims, 0.4)
     lists = [mbc.build_term_list(1, 1, 2), mbc.build_term_list(2, 1, 2), mbc.build_term_list(2, 2, 2)]
-    check_slabs(mbc, field, lists, [(1, 1, 2), (2, 1, 2), (2, 2, 2)], dims, tune={"regime": 2})
+    check_legs(mbc, 8, 1, 2, dims, 0.4, lists, [(1, 1, 2), (2, 1, 2), (2, 2, 2)], tune={"regime": 2})
 
 
 def test_he4_rel_all_components(mbc):
     dims = (1, 2, 2)
-    field = synth.field(2, 1, 1, dims, 0.4)
     tl = mbc.build_term_list(2, 2, 4)
-    check_slabs(mbc, field, [tl], [(2, 2, 4)], dims)
+    check_legs(mbc, 2, 1, 1, dims, 0.4, [tl], [(2, 2, 4)])
+
+
+BE8 = (0, 1, 2, 3, 0, 1, 2, 3)
+
+
+def _be8_K():
+    """C / (det S_u det S_d) for 8Be: the square of its single L entry
+    (exterior-algebra oracle; O3 is pinned to it on the CPU)."""
+    from oracle import grassmann
+    (L,) = grassmann.l_tensor("PPPPNNNN", BE8, 4).values()
+    return float(L) ** 2
 
 
 def test_be8_large_path(mbc):
-    dims = (2, 2, 2)
-    field = synth.field(4, 1, 2, dims, 0.4, dtype=np.complex64)
-    sp = (0, 1, 2, 3, 0, 1, 2, 3)
-    tl = mbc.build_term_list(4, 4, 4, spins=[(sp, sp)])
-    check_slabs(mbc, field, [tl], [(4, 4, 4)], dims)
+    """8Be against O3 on near-identity propagators, where the bound
+    discriminates (on Gaussian ones |C| / sum|terms| ~ 5e-14)."""
+    dims = (1, 2, 2)
+    tl = mbc.build_term_list(4, 4, 4, spins=[(BE8, BE8)])
+    check_legs(mbc, 4, 1, 2, dims, 0.4, [tl], [(4, 4, 4)], dtype=np.complex64, gauss=False)
+
+
+def test_be8_full_slab_closed_form(mbc):
+    """One 16^3 slab of the 8Be configuration's geometry (complex64 storage)
+    with every site live, FP64 and mixed, against the exact closed form
+    C(x) = K det S(x)^2 (all 12 u and 12 d states saturated, Sec. 8) summed
+    over the sites with two momenta. On these inputs (eps = 0.02)
+    sum|terms| <= 10 |C| at every sampled site (checked with O3 below), so
+    the bound TOL sum|terms| is at least as strict as 10 TOL |C|."""
+    from oracle import site_sum
+    dims = (16, 16, 16)
+    field = synth.field(4, 1, 1, dims, 0.4, dtype=np.complex64, eps=0.02)
+    tl = mbc.build_term_list(4, 4, 4, spins=[(BE8, BE8)])
+    K = _be8_K()
+    S = field[0, 0].reshape(-1, 12, 12).astype(np.complex128)
+    Cx = K * np.linalg.det(S) ** 2
+    plan = oracle_plan(4, 4, 4, [(BE8, BE8)])
+    Co, sc = plan.evaluate(S[[0, 2345]], batch=2)
+    assert np.all(np.abs(Co[:, 0] - Cx[[0, 2345]]) <= 1e-12 * np.abs(Cx[[0, 2345]]))
+    assert np.all(sc[:, 0] <= 10 * np.abs(Co[:, 0]))
+    moms = ((0, 0, 0), (1, 0, 0))
+    ref = site_sum.site_sum(Cx[:, None], synth.site_coords(dims), tuple(dims[::-1]), list(moms))[:, 0]
+    mag = float(np.sum(np.abs(Cx)))
+    for p in (0, 1):
+        got = run(mbc, field, [tl], p, moms=moms)[0, 0, 0, :, 0]
+        e = float(np.max(np.abs(got - ref)) / mag)
+        record("(4,4) D=4 full slab closed form (rel. to sum|C|)", p, e)
+        assert e <= 10 * TOL[p], (p, e)
+        assert abs(ref[0]) >= 0.5 * mag  # the zero-momentum sum does not cancel
 
 
 def test_batched_launch_mixed_regimes(mbc):
     """One call over several configurations, time slices and nuclei of both
     regimes (the nonrelativistic ones share one persistent launch)."""
     dims = (2, 2, 3)
-    field = synth.field(3, 2, 2, dims, 0.4, dtype=np.complex64)
     sp = (0, 1, 0, 1)
     lists = [mbc.build_term_list(1, 1, 2), mbc.build_term_list(2, 1, 2), mbc.build_term_list(2, 2, 2),
              mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])]
     specs = [(1, 1, 2), (2, 1, 2), (2, 2, 2), (2, 2, 4)]
-    check_slabs(mbc, field, lists, specs, dims)
+    check_legs(mbc, 3, 2, 2, dims, 0.4, lists, specs, dtype=np.complex64)
 
 
 def test_graph_capture_replays_bitwise(mbc):
@@ -217,11 +278,11 @@ def test_graph_capture_replays_bitwise(mbc):
             assert torch.equal(out, ref)
 
 
-def _sparse_slab_field(seed, dims, lam, sites, dtype=np.complex128):
+def _sparse_slab_field(seed, dims, lam, sites, dtype=np.complex128, eps=None):
     """Full-size slab whose propagators vanish except at the listed sites:
     every other site contributes exactly zero, so the slab sum is the sum
     over the listed sites, which the oracle evaluates one by one."""
-    full = synth.field(seed, 1, 1, dims, lam, dtype=dtype)
+    full = synth.field(seed, 1, 1, dims, lam, dtype=dtype, eps=eps)
     out = np.zeros_like(full)
     flat_o = out.reshape(-1, 12, 12)
     flat_f = full.reshape(-1, 12, 12)
@@ -229,47 +290,41 @@ def _sparse_slab_field(seed, dims, lam, sites, dtype=np.complex128):
     return out
 
 
-def _check_sparse(mbc, field, tl, spec, dims, sites, precisions=(0, 1)):
+def _check_sparse(mbc, seed, dims, lam, sites, tl, spec, dtype=np.complex128, gauss=True):
     from oracle import site_sum
     coords = synth.site_coords(dims)[sites]
     plan = oracle_plan(*spec, tl.components())
-    C, sc = plan.evaluate(field.reshape(-1, 12, 12)[sites].astype(np.complex128))
-    ref = site_sum.site_sum(C, coords, tuple(dims[::-1]), [(0, 0, 0)])
-    scale = site_sum.scale_sum(sc)
-    for p in precisions:
-        got = run(mbc, field, [tl], p)[0, 0, 0, :, : len(tl.components())]
-        e = max_rel_err(got, ref, scale)
-        record(f"({spec[0]},{spec[1]}) D={spec[2]} full lattice", p, e)
-        assert e <= TOL[p], p
+    kinds = ([(None, (0,))] if gauss else []) + [(EPS, (0, 1))]
+    for eps, precs in kinds:
+        field = _sparse_slab_field(seed, dims, lam, sites, dtype=dtype, eps=eps)
+        C, sc = plan.evaluate(field.reshape(-1, 12, 12)[sites].astype(np.complex128))
+        ref = site_sum.site_sum(C, coords, tuple(dims[::-1]), [(0, 0, 0)])
+        scale = site_sum.scale_sum(sc)
+        for p in precs:
+            got = run(mbc, field, [tl], p)[0, 0, 0, :, : len(tl.components())]
+            e = parity.check(got, ref, scale[None, :], p, what=f"{spec} sparse eps {eps}")
+            record(f"({spec[0]},{spec[1]}) D={spec[2]} full lattice", p, e)
 
 
 def test_he4_rel_all_components_full_lattice_sampled(mbc):
     """16^3 slab (the relativistic 4He configuration's geometry and launch
     shape), all 1296 components, four live sites."""
-    dims = (16, 16, 16)
-    sites = [0, 1337, 2048, 4095]
-    field = _sparse_slab_field(2, dims, 0.4, sites)
-    _check_sparse(mbc, field, mbc.build_term_list(2, 2, 4), (2, 2, 4), dims, sites, precisions=(1,))
+    _check_sparse(mbc, 2, (16, 16, 16), 0.4, [0, 1337, 2048, 4095], mbc.build_term_list(2, 2, 4), (2, 2, 4))
 
 
 def test_be8_full_lattice_sampled(mbc):
-    dims = (16, 16, 16)
-    sites = [5, 3000]
-    field = _sparse_slab_field(4, dims, 0.4, sites, dtype=np.complex64)
-    sp = (0, 1, 2, 3, 0, 1, 2, 3)
-    _check_sparse(mbc, field, mbc.build_term_list(4, 4, 4, spins=[(sp, sp)]), (4, 4, 4), dims, sites,
-                  precisions=(1,))
+    _check_sparse(mbc, 4, (16, 16, 16), 0.4, [5, 3000], mbc.build_term_list(4, 4, 4, spins=[(BE8, BE8)]),
+                  (4, 4, 4), dtype=np.complex64, gauss=False)
 
 
 def test_batched_geometry_sampled(mbc):
     """24^3 geometry of the batched configuration, complex64, four nuclei."""
     dims = (24, 24, 24)
     sites = [0, 7777, 13823]
-    field = _sparse_slab_field(3, dims, 0.4, sites, dtype=np.complex64)
     sp = (0, 1, 0, 1)
     for tl, spec in ((mbc.build_term_list(1, 1, 2), (1, 1, 2)), (mbc.build_term_list(2, 2, 2), (2, 2, 2)),
                      (mbc.build_term_list(2, 2, 4, spins=[(sp, sp)]), (2, 2, 4))):
-        _check_sparse(mbc, field, tl, spec, dims, sites)
+        _check_sparse(mbc, 3, dims, 0.4, sites, tl, spec, dtype=np.complex64)
 
 
 def test_out_of_memory_is_a_clean_error(mbc):
@@ -291,12 +346,11 @@ def test_out_of_memory_is_a_clean_error(mbc):
 def test_wave_order_and_chunking_variants(mbc):
     """Every launch shape the autotuner may pick gives the oracle's result."""
     dims = (2, 2, 2)
-    field = synth.field(14, 1, 2, dims, 0.4)
     sp = (0, 1, 0, 1)
     tl = mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])
     for tune in ({"wave_order": 1, "zchunk": 8}, {"wave_order": 1, "zchunk": 3, "wave_sites": 32},
                  {"wave_order": 0, "zchunk": 1}):
-        check_slabs(mbc, field, [tl], [(2, 2, 4)], dims, tune=tune)
+        check_legs(mbc, 14, 1, 2, dims, 0.4, [tl], [(2, 2, 4)], tune=tune)
 
 
 @pytest.mark.parametrize("n_p,n_n,D,spins", [(1, 0, 4, None), (1, 1, 2, None), (2, 1, 2, None), (2, 2, 2, None),
@@ -306,19 +360,19 @@ def test_momentum_projected_blocks(mbc, n_p, n_n, D, spins):
     (Sec. 2 sink functions), against the oracle's projection."""
     from oracle import projection
     dims = (2, 3, 4)
-    field = synth.field(21, 2, 2, dims, 0.4)
     moms = ((0, 0, 0), (1, 0, 0), (0, 1, 3))
     tl = mbc.build_term_list(n_p, n_n, D, spins=spins)
     comps = tl.components()
     plan = oracle_plan(n_p, n_n, D, comps)
-    outs = {p: run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM) for p in (0, 1)}
-    for cfg in range(2):
-        for t in range(2):
-            C, sc = projection.projected_correlators(plan, field[cfg, t], dims, moms)
-            for p in (0, 1):
-                got = outs[p][cfg, 0, t, :, : len(comps)]
-                record(f"({n_p},{n_n}) D={D} projected blocks", p, float(np.max(np.abs(got - C) / sc)))
-                assert np.all(np.abs(got - C) <= TOL[p] * sc), (p, cfg, t, float(np.max(np.abs(got - C) / sc)))
+    for field, precs in legs(21, 2, 2, dims, 0.4):
+        outs = {p: run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM) for p in precs}
+        for cfg in range(2):
+            for t in range(2):
+                C, sc = projection.projected_correlators(plan, field[cfg, t], dims, moms)
+                for p in precs:
+                    got = outs[p][cfg, 0, t, :, : len(comps)]
+                    e = parity.check(got, C, sc, p, what=f"projected ({n_p},{n_n}) D={D} cfg {cfg} t {t}")
+                    record(f"({n_p},{n_n}) D={D} projected blocks", p, e)
 
 
 def test_momentum_projected_blocks_full_slab(mbc):
@@ -326,15 +380,18 @@ def test_momentum_projected_blocks_full_slab(mbc):
     lattice, few items (one per momentum)."""
     from oracle import projection
     dims = (16, 16, 16)
-    field = synth.field(22, 1, 1, dims, 0.4)
     moms = ((0, 0, 0), (1, 0, 0))
     sp = (0, 1, 0, 1)
     tl = mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])
     plan = oracle_plan(2, 2, 4, tl.components())
-    C, sc = projection.projected_correlators(plan, field[0, 0], dims, moms)
-    for p in (0, 1):
-        got = run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM)[0, 0, 0, :, :1]
-        assert np.all(np.abs(got - C) <= TOL[p] * sc), p
+    # near-identity only: Gaussian blocks summed over 4096 sites leave
+    # |C| / sum|terms| ~ 1e-13, where not even the FP64 bound discriminates
+    for field, precs in legs(22, 1, 1, dims, 0.4, gauss=False):
+        C, sc = projection.projected_correlators(plan, field[0, 0], dims, moms)
+        for p in precs:
+            got = run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM)[0, 0, 0, :, :1]
+            e = parity.check(got, C, sc, p, what="projected 4He rel 16^3")
+            record("(2,2) D=4 projected blocks 16^3", p, e)
 
 
 def _sorted_with_sign(spins, n_p):
@@ -356,25 +413,25 @@ def test_spin_projection_outputs(mbc, n_p, n_n, D, projections):
     """Sec. 5 projections C_M = sum_t w_t C(snk_t; src_t) (spins in any order
     within a species) against the oracle's components."""
     dims = (2, 2, 2)
-    field = synth.field(23, 1, 2, dims, 0.4)
     tl = mbc.build_term_list(n_p, n_n, D, projections=projections)
     pairs = sorted({(_sorted_with_sign(s, n_p)[0], _sorted_with_sign(a, n_p)[0])
                     for proj in projections for (s, a, _) in proj})
     plan = oracle_plan(n_p, n_n, D, pairs)
     idx = {pr: i for i, pr in enumerate(pairs)}
-    outs = {p: run(mbc, field, [tl], p) for p in (0, 1)}
-    for t in range(2):
-        ref, scale = oracle_slab(plan, field[0, t], dims, [(0, 0, 0)])
-        for k, proj in enumerate(projections):
-            exp, sc = 0j, 0.0
-            for s, a, w in proj:
-                (ss, g1), (aa, g2) = _sorted_with_sign(s, n_p), _sorted_with_sign(a, n_p)
-                exp += w * g1 * g2 * ref[0, idx[(ss, aa)]]
-                sc += abs(w) * scale[idx[(ss, aa)]]
-            for p in (0, 1):
-                e = abs(outs[p][0, 0, t, 0, k] - exp) / sc
+    for field, precs in legs(23, 1, 2, dims, 0.4):
+        outs = {p: run(mbc, field, [tl], p) for p in precs}
+        for t in range(2):
+            ref, scale = oracle_slab(plan, field[0, t], dims, [(0, 0, 0)])
+            exp = np.zeros(len(projections), dtype=complex)
+            sc = np.zeros(len(projections))
+            for k, proj in enumerate(projections):
+                for s, a, w in proj:
+                    (ss, g1), (aa, g2) = _sorted_with_sign(s, n_p), _sorted_with_sign(a, n_p)
+                    exp[k] += w * g1 * g2 * ref[0, idx[(ss, aa)]]
+                    sc[k] += abs(w) * scale[idx[(ss, aa)]]
+            for p in precs:
+                e = parity.check(outs[p][0, 0, t, 0, :len(projections)], exp, sc, p, what=f"projection t {t}")
                 record(f"({n_p},{n_n}) D={D} projection", p, e)
-                assert e <= TOL[p], (k, t, p, e)
 
 
 _TWO_SRC_PLANS = {}
@@ -404,27 +461,28 @@ def test_two_quark_sources(mbc, n_p, n_n, spins):
     propagator."""
     from oracle import projection, recursion
     dims = (3, 2, 5)
-    field = synth.field(24, 2, 2, dims, 0.4, n_src=2)
     moms = ((0, 0, 0), (1, 0, 2))
     tl = mbc.build_term_list(n_p, n_n, 2, spins=spins, n_sources=2)
     comps = tl.components()
     plan = two_source_plan(n_p, n_n, comps)
     label = f"({n_p},{n_n}) D=2 two sources"
-    for sink in (mbc.SINK_POINT, mbc.SINK_BLOCK_MOMENTUM):
-        outs = {p: run(mbc, field, [tl], p, moms=moms, sink=sink) for p in (0, 1)}
-        for cfg in range(2):
-            for t in range(2):
-                S = recursion.source_columns(field[cfg, t], 2)
-                if sink == mbc.SINK_POINT:
-                    ref, scale = oracle_slab(plan, S, dims, list(moms))
-                    scale = scale[None, :]
-                else:
-                    ref, scale = projection.projected_correlators(plan, S, dims, moms)
-                for p in (0, 1):
-                    got = outs[p][cfg, 0, t, :, : len(comps)]
-                    e = float(np.max(np.abs(got - ref) / scale))
-                    record(label + (" projected" if sink else ""), p, e)
-                    assert e <= TOL[p], (sink, p, cfg, t, e)
+    field = None
+    for field, precs in legs(24, 2, 2, dims, 0.4, n_src=2):
+        for sink in (mbc.SINK_POINT, mbc.SINK_BLOCK_MOMENTUM):
+            pr = precs
+            outs = {p: run(mbc, field, [tl], p, moms=moms, sink=sink) for p in pr}
+            for cfg in range(2):
+                for t in range(2):
+                    S = recursion.source_columns(field[cfg, t], 2)
+                    if sink == mbc.SINK_POINT:
+                        ref, scale = oracle_slab(plan, S, dims, list(moms))
+                        scale = scale[None, :]
+                    else:
+                        ref, scale = projection.projected_correlators(plan, S, dims, moms)
+                    for p in pr:
+                        got = outs[p][cfg, 0, t, :, : len(comps)]
+                        e = parity.check(got, ref, scale, p, what=f"{label} sink {sink} cfg {cfg} t {t}")
+                        record(label + (" projected" if sink else ""), p, e)
     # host-memory staging of the source axis
     host = mbc.contract(field, [tl], precision=0, moms=moms)
     dev = run(mbc, field, [tl], 0, moms=moms)
@@ -438,7 +496,7 @@ def test_two_sources_two_sinks_full_slab(mbc):
     oracle's grouped projected blocks."""
     from oracle import gamma, projection, recursion
     dims = (16, 16, 16)
-    field = synth.field(5, 1, 1, dims, 0.4, n_src=2)
+    field = synth.field(5, 1, 1, dims, 0.4, n_src=2, eps=EPS)  # Gaussian: |C| / sum|terms| ~ 2e-11
     pairs = ((0, 1), (0, 2), (1, 2), (0, 3), (1, 3), (2, 3))
     spins = [(p + q, (0, 2, 0, 2)) for p in pairs for q in pairs]
     moms = ((0, 0, 0), (1, 0, 0))
@@ -449,25 +507,23 @@ def test_two_sources_two_sinks_full_slab(mbc):
                                                   n_sinks=2, dirac_dim=2)
     for p in (0, 1):
         got = run(mbc, field, [tl], p, moms=moms, sink=mbc.SINK_BLOCK_MOMENTUM)[0, 0, 0, :, : len(comps)]
-        e = float(np.max(np.abs(got - ref) / scale))
+        e = parity.check(got, ref, scale, p, what="two sources two sinks 16^3")
         record("(2,2) D=2 two sources, two sinks 16^3", p, e)
-        assert e <= TOL[p], (p, e)
 
 
 def test_two_quark_sources_larger_slab(mbc):
     """4He, two sources, one 8^3 slab: several waves of the large-stage path."""
     dims = (8, 8, 8)
-    field = synth.field(25, 1, 1, dims, 0.4, n_src=2)
     spins = [((0, 1, 0, 1), (0, 3, 1, 2))]
     tl = mbc.build_term_list(2, 2, 2, spins=spins, n_sources=2)
     plan = two_source_plan(2, 2, tl.components())
     from oracle import recursion
-    ref, scale = oracle_slab(plan, recursion.source_columns(field[0, 0], 2), dims, [(0, 0, 0), (0, 1, 0)])
-    for p in (0, 1):
-        got = run(mbc, field, [tl], p, moms=((0, 0, 0), (0, 1, 0)), tune={"wave_sites": 128})[0, 0, 0, :, :1]
-        e = max_rel_err(got, ref, scale)
-        record("(2,2) D=2 two sources 8^3", p, e)
-        assert e <= TOL[p], (p, e)
+    for field, precs in legs(25, 1, 1, dims, 0.4, n_src=2):
+        ref, scale = oracle_slab(plan, recursion.source_columns(field[0, 0], 2), dims, [(0, 0, 0), (0, 1, 0)])
+        for p in precs:
+            got = run(mbc, field, [tl], p, moms=((0, 0, 0), (0, 1, 0)), tune={"wave_sites": 128})[0, 0, 0, :, :1]
+            e = parity.check(got, ref, scale[None, :], p, what="two sources 8^3")
+            record("(2,2) D=2 two sources 8^3", p, e)
 
 
 def test_loaded_term_lists_contract_identically(mbc, tmp_path):
@@ -497,7 +553,7 @@ def test_list_free_steps_match_stored_lists(mbc, n_p, n_n, D, spins):
     and within the bound of the oracle. Regenerating the dense steps of a
     list with arrays (tune list_free = 1) is bitwise equal too."""
     dims = (3, 2, 5)
-    field = synth.field(28, 1, 2, dims, 0.4)
+    field = synth.field(28, 1, 2, dims, 0.4, eps=EPS)
     stored = mbc.build_term_list(n_p, n_n, D, spins=spins)
     free = mbc.build_term_list(n_p, n_n, D, spins=spins, list_free=True)
     st, sf = stored.stats(), free.stats()
@@ -511,18 +567,17 @@ def test_list_free_steps_match_stored_lists(mbc, n_p, n_n, D, spins):
             c = run(mbc, field, [stored], p, moms=moms, tune={"regime": 2, "list_free": 1})
             assert np.array_equal(a, c), p
     check_slabs(mbc, field, [free], [(n_p, n_n, D)], dims, moms=moms)
+    check_slabs(mbc, synth.field(28, 1, 2, dims, 0.4), [free], [(n_p, n_n, D)], dims, precisions=(0,), moms=moms)
 
 
 def test_list_free_be8(mbc):
     """8Be (0,1,2,3,0,1,2,3): every stage is dense, so the list-free list
     stores no operations at all (against 2.7 GB of arrays)."""
-    dims = (2, 2, 2)
-    field = synth.field(4, 1, 1, dims, 0.4, dtype=np.complex64)
-    sp = (0, 1, 2, 3, 0, 1, 2, 3)
-    tl = mbc.build_term_list(4, 4, 4, spins=[(sp, sp)], list_free=True)
+    dims = (1, 2, 2)
+    tl = mbc.build_term_list(4, 4, 4, spins=[(BE8, BE8)], list_free=True)
     st = tl.stats()
     assert st["op_bytes"] == 0 and st["dense_steps"] == list(range(1, 8))
-    check_slabs(mbc, field, [tl], [(4, 4, 4)], dims)
+    check_legs(mbc, 4, 1, 1, dims, 0.4, [tl], [(4, 4, 4)], dtype=np.complex64, gauss=False)
 
 
 @pytest.mark.parametrize("n_p,n_n,n_src,spins", [
@@ -537,7 +592,7 @@ def test_two_sink_functions(mbc, n_p, n_n, n_src, spins):
     Table 6), against the oracle's grouped projected blocks."""
     from oracle import gamma, projection, recursion
     dims = (2, 3, 4)
-    field = synth.field(27, 1, 2, dims, 0.4, n_src=n_src if n_src > 1 else 0)
+    field = synth.field(27, 1, 2, dims, 0.4, n_src=n_src if n_src > 1 else 0, eps=EPS)
     moms = ((0, 0, 0), (1, 0, 0), (0, 1, 2), (0, 0, 1))
     tl = mbc.build_term_list(n_p, n_n, 2, spins=spins, n_sources=n_src, n_sinks=2)
     comps = tl.components()
@@ -551,10 +606,8 @@ def test_two_sink_functions(mbc, n_p, n_n, n_src, spins):
         ref, scale = projection.projected_correlators(plan, S, dims, moms, n_sinks=2, dirac_dim=2)
         for p in (0, 1):
             got = outs[p][0, 0, t, :, : len(comps)]
-            assert got.shape == ref.shape
-            e = float(np.max(np.abs(got - ref) / scale))
+            e = parity.check(got, ref, scale, p, what=f"two sinks ({n_p},{n_n}) {n_src} source(s) t {t}")
             record(f"({n_p},{n_n}) D=2 {n_src} source(s), 2 sinks", p, e)
-            assert e <= TOL[p], (t, p, e)
 
 
 @pytest.mark.parametrize("D,path,nuclei,regime,sink", [
@@ -571,7 +624,7 @@ def test_combined_path_lists(mbc, D, path, nuclei, regime, sink):
     momentum-projected blocks)."""
     from oracle import projection
     dims = (2, 3, 5)
-    field = synth.field(26, 1, 2, dims, 0.4)
+    field = synth.field(26, 1, 2, dims, 0.4, eps=EPS)
     moms = ((0, 0, 0), (0, 2, 1))
     tl = mbc.build_combined([dict(n_p=a, n_n=b, spins=sp) for a, b, sp in nuclei], D, path=path)
     comps = tl.components()
@@ -588,9 +641,8 @@ def test_combined_path_lists(mbc, D, path, nuclei, regime, sink):
                 ref, scale = projection.projected_correlators(plan, field[0, t], dims, moms)
             for p in (0, 1):
                 got = outs[p][0, 0, t, :, part["c0"]:part["c1"]]
-                e = float(np.max(np.abs(got - ref) / scale))
+                e = parity.check(got, ref, scale, p, what=f"combined ({a},{b}) t {t}")
                 record(f"({a},{b}) D={D} on a combined path", p, e)
-                assert e <= TOL[p], (a, b, t, p, e)
 
 
 def test_zz_accuracy_report(mbc, capsys):
@@ -600,4 +652,4 @@ def test_zz_accuracy_report(mbc, capsys):
         print("\naccuracy: worst |dC| / sum|terms| against the oracle")
         for (label, prec), e in sorted(WORST.items()):
             print(f"  {label:40s} {prec:6s} {e:.3e}")
-    assert all(e <= TOL[0 if prec == "fp64" else 1] for (label, prec), e in WORST.items())
+    assert all(e <= 10 * TOL[0 if prec == "fp64" else 1] for (label, prec), e in WORST.items())
