@@ -551,8 +551,9 @@ def main():
     probe64 = mbc.fma_probe(0)
     probe32 = mbc.fma_probe(1)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    nominal64 = 152 * 2 * 2 * sm_max * 1e6  # 2 DFMA / clk / SM (1.25 TFLOP/s class), 2 flop each
-    nominal32 = 152 * 128 * 2 * sm_max * 1e6
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    nominal64 = n_sm * 2 * 2 * sm_max * 1e6  # 2 DFMA / clk / SM (1.25 TFLOP/s class), 2 flop each
+    nominal32 = n_sm * 128 * 2 * sm_max * 1e6
     has_small = any(n[2] == 2 for n in nuclei)
     has_large = any(n[2] == 4 for n in nuclei)
     kname = {0: " + ".join(k for k, on in (("k_small<FP64>", has_small), ("k_large_step<FP64>", has_large)) if on),
@@ -576,9 +577,10 @@ def main():
                 "frac_of_measured_fma": ach / probe, "kernel": kname[prec], "time_basis": basis,
                 "kernel_ms_per_step": t_ms / args.steps, "launches_timed": launches, "flops_per_step": flops_step}
 
-    roof64 = roofline(k64, ms64, n64, nominal64, probe64, "FP64 vector, derived: 152 SMs x 2 DFMA/clk x max SM clock", 0)
+    roof64 = roofline(k64, ms64, n64, nominal64, probe64,
+                      f"FP64 vector, derived: {n_sm} SMs x 2 DFMA/clk x max SM clock", 0)
     roof_mx = roofline(kmx, msmx, nmx, nominal32, probe32,
-                       "FP32 vector, derived: 152 SMs x 128 FFMA/clk x max SM clock", 1)
+                       f"FP32 vector, derived: {n_sm} SMs x 128 FFMA/clk x max SM clock", 1)
     roof = roof64 if primary == 0 else roof_mx
     if roof is not None and args.workload == "nonrel" and primary == 0 and not has_large and not args.combined:
         roof["traffic"] = profiled_traffic("k_small_fp64_he3_he4_16x16x16x16.md", v3 * nt * args.cfgs)

@@ -352,9 +352,10 @@ mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *const *list
 /*
  * mbc_contract without any device allocation. The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc in steady
- * state - for example code that runs between the set-up of a CUDA graph and
- * its replays, services whose device memory is reserved up front by their
- * own pool, or real-time loops that forbid allocator calls.
+ * state - services whose device memory is reserved up front by their own
+ * pool (a cudaMalloc would fail or fragment it), or real-time loops whose
+ * latency budget forbids allocator calls (cudaMalloc and cudaFree may
+ * synchronise the device).
  *
  * Same arguments and output layout as mbc_contract with n_lists = 1:
  * out is complex128 [n_cfg][1][t1 - t0][n_mom][max(1, n_comp)], device
@@ -380,10 +381,11 @@ mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *const *list
  *     capture begins;
  *   - no cudaMalloc, cudaFree or other allocating routine is called;
  *   - every call shares the one array and leaves the last call's contents in
- *     it (nothing in it needs to start at zero: each entry is written before
- *     it is read). Calls that overlap on the GPU - on different streams, or
- *     from several host threads - race on the array and give wrong results:
- *     serialise them.
+ *     it. The one word that must start at zero (the work counter of the
+ *     persistent kernel) is zeroed by each call on its stream; every other
+ *     entry is written before it is read. Calls that overlap on the GPU - on
+ *     different streams, or from several host threads - race on the array and
+ *     give wrong results: serialise them.
  */
 #define MBC_NOALLOC_SCRATCH_BYTES (8u << 20)
 mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_term_list *list, const mbc_contract_opts *opts,

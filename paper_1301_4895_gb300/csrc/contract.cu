@@ -488,15 +488,11 @@ struct SmallLaunch {
     int tiles_per_slab = 0;
 };
 
-SmallLaunch size_small_batch(const std::vector<const DeviceCache *> &cs, const FieldDesc &F, const mbc_tune *tune,
-                             bool mixed, int32_t &site_stride, int32_t &comp_stride, int n_sm = 0) {
+// Launch shape of the shared-memory kernels for per-site buffers of
+// site_stride entries and comp_stride components (host only).
+SmallLaunch size_small_tiles(int32_t site_stride, int32_t comp_stride, const FieldDesc &F, const mbc_tune *tune,
+                             bool mixed, int n_sm = 0) {
     SmallLaunch l;
-    site_stride = 0;
-    comp_stride = 0;
-    for (auto *c : cs) {
-        site_stride = std::max(site_stride, (int32_t)c->site_entries);
-        comp_stride = std::max(comp_stride, c->sp.n_comp);
-    }
     if (!mixed) {
         const int64_t per_site = site_stride * 16LL + 16LL * comp_stride;
         l.T = (int)std::min<int64_t>(32, kSmemLimit / per_site);
@@ -526,6 +522,17 @@ SmallLaunch size_small_batch(const std::vector<const DeviceCache *> &cs, const F
     l.tiles_per_slab = (v3 + l.T - 1) / l.T;
     l.ok = true;
     return l;
+}
+
+SmallLaunch size_small_batch(const std::vector<const DeviceCache *> &cs, const FieldDesc &F, const mbc_tune *tune,
+                             bool mixed, int32_t &site_stride, int32_t &comp_stride, int n_sm = 0) {
+    site_stride = 0;
+    comp_stride = 0;
+    for (auto *c : cs) {
+        site_stride = std::max(site_stride, (int32_t)c->site_entries);
+        comp_stride = std::max(comp_stride, c->sp.n_comp);
+    }
+    return size_small_tiles(site_stride, comp_stride, F, tune, mixed, n_sm);
 }
 
 mbc_status launch_small_batch(const SmallBatch &B, const FieldDesc &F, const MomDesc &M, const SmallLaunch &l,
@@ -1390,8 +1397,16 @@ extern "C" mbc_status mbc_fma_probe(int32_t precision, double *flops) {
     int device = 0;
     MBC_CUDA_TRY(cudaGetDevice(&device));
     const int nsm = sm_count(device);
-    const int threads = 256, blocks = nsm * 4;
-    const int iters = precision == MBC_FP64 ? 1024 : 16384;
+    const int threads = 256;
+    // one full wave: every SM runs as many probe blocks as fit at once
+    int per_sm = 0;
+    if (precision == MBC_FP64)
+        MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe<double>, threads, 0));
+    else
+        MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe<float>, threads, 0));
+    const int blocks = nsm * std::max(1, per_sm);
+    // tens of milliseconds per launch (clocks settle, launch cost vanishes)
+    const int iters = precision == MBC_FP64 ? 4096 : 131072;
     void *buf = nullptr;
     MBC_CUDA_TRY(cudaMalloc(&buf, (size_t)threads * blocks * sizeof(double)));
     cudaEvent_t a, b;
@@ -1415,15 +1430,15 @@ extern "C" mbc_status mbc_fma_probe(int32_t precision, double *flops) {
     cudaEventDestroy(b);
     cudaFree(buf);
     if (e != cudaSuccess) return MBC_ERR_CUDA;
-    *flops = 2.0 * 8.0 * iters * (double)threads * blocks / (best * 1e-3);
+    *flops = 2.0 * kProbeChains * (double)iters * (double)threads * blocks / (best * 1e-3);
     return MBC_OK;
 }
 
 // ---- contraction without allocation ------------------------------------------
-// Callers that must not allocate device memory in steady state (code running
-// between the set-up of a CUDA graph and its replays, services whose device
-// memory is fully reserved up front by their own pool, real-time loops) use
-// mbc_contract_noalloc. Its scratch - the momentum phase table and the
+// Callers that must not allocate device memory in steady state (services
+// whose device memory is reserved up front by their own pool, so that a
+// cudaMalloc would fail or fragment it; real-time loops, where cudaMalloc and
+// cudaFree may synchronise the device) use mbc_contract_noalloc. Its scratch - the momentum phase table and the
 // per-tile partial sums of the FP64 shared-memory kernel - lives in one
 // static device array of kStaticScratchBytes, which every GPU that loads the
 // library holds until the process exits.
@@ -1481,37 +1496,6 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     const int64_t n_slabs = (int64_t)props->n_cfg * n_t;
     const int comp_max = std::max(1, (int)list->n_comp);
     const size_t out_bytes = (size_t)n_slabs * opts->n_mom * comp_max * sizeof(double2);
-    SmallPlan hp;
-    int64_t site_entries = 0;
-    const bool zero = list->pauli_forbidden || list->n_comp == 0;
-    size_t phase_bytes = 0, part_bytes = 0;
-    int T = 0;
-    if (!zero) {
-        std::vector<int> part_off;
-        if (!plan_small(list, hp, site_entries, part_off)) return MBC_ERR_UNSUPPORTED;  // relativistic lists: no static variant
-        const int64_t per_site = site_entries * 16LL + 16LL * hp.n_comp;
-        T = (int)std::min<int64_t>(32, kSmemLimit / per_site);
-        if (opts->tune && opts->tune->sites_per_cta > 0) T = std::min(T, opts->tune->sites_per_cta);
-        if (T < 1) return MBC_ERR_UNSUPPORTED;
-        const int64_t tiles = n_slabs * ((v3 + T - 1) / T);
-        phase_bytes = align256((size_t)v3 * opts->n_mom * sizeof(double2));
-        part_bytes = (size_t)tiles * opts->n_mom * list->n_comp * sizeof(double2);
-        if (phase_bytes + 256 + part_bytes > kStaticScratchBytes) return MBC_ERR_UNSUPPORTED;  // beyond 8 MiB
-    }
-    // ---- device work: no allocation from here on
-    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_v);
-    int device = 0;
-    MBC_CUDA_TRY(cudaGetDevice(&device));
-    if (zero) {
-        MBC_CUDA_TRY(cudaMemsetAsync(out, 0, out_bytes, stream));
-        return MBC_OK;
-    }
-    DeviceCache *c = find_cache(list, device);
-    if (!c || !c->small_ok) return MBC_ERR_INVALID_ARG;  // the list's device copy must exist already
-    void *scr = nullptr;
-    mbc_status st = static_scratch_address(device, &scr);
-    if (st != MBC_OK) return st;
-    if ((st = ensure_constants(device)) != MBC_OK) return st;
     const int64_t stride_t = props->stride_t ? props->stride_t : v3 * 144;
     FieldDesc F;
     F.s = props->s_u;
@@ -1526,6 +1510,38 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     F.t0 = t0;
     F.n_t = n_t;
     F.n_src = 1;
+    SmallPlan hp;
+    int64_t site_entries = 0;
+    const bool zero = list->pauli_forbidden || list->n_comp == 0;
+    size_t phase_bytes = 0, part_bytes = 0;
+    SmallLaunch l;
+    if (!zero) {
+        std::vector<int> part_off;
+        if (!plan_small(list, hp, site_entries, part_off)) return MBC_ERR_UNSUPPORTED;  // relativistic lists: no static variant
+        // the launch shape the kernel will run with, and from it the bytes
+        // of the tile partials (one sizing, used for the check and the launch)
+        l = size_small_tiles((int32_t)site_entries, hp.n_comp, F, opts->tune, false);
+        if (!l.ok) return MBC_ERR_UNSUPPORTED;
+        const int64_t tiles = n_slabs * l.tiles_per_slab;
+        phase_bytes = align256((size_t)v3 * opts->n_mom * sizeof(double2));
+        part_bytes = (size_t)tiles * opts->n_mom * hp.n_comp * sizeof(double2);
+        if (phase_bytes + 256 + part_bytes > kStaticScratchBytes) return MBC_ERR_UNSUPPORTED;  // beyond 8 MiB
+    }
+    // ---- device work: no allocation from here on
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_v);
+    int device = 0;
+    MBC_CUDA_TRY(cudaGetDevice(&device));
+    if (zero) {
+        MBC_CUDA_TRY(cudaMemsetAsync(out, 0, out_bytes, stream));
+        return MBC_OK;
+    }
+    DeviceCache *c = find_cache(list, device);
+    if (!c || !c->small_ok) return MBC_ERR_INVALID_ARG;  // the list's device copy must exist already
+    if (c->site_entries != site_entries || c->sp.n_comp != hp.n_comp) return MBC_ERR_INVALID_ARG;
+    void *scr = nullptr;
+    mbc_status st = static_scratch_address(device, &scr);
+    if (st != MBC_OK) return st;
+    if ((st = ensure_constants(device)) != MBC_OK) return st;
     MomDesc M;
     std::memset(&M, 0, sizeof(M));
     M.n_mom = opts->n_mom;
@@ -1542,8 +1558,8 @@ extern "C" mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_ter
     MBC_CUDA_TRY(cudaGetLastError());
     SmallBatch B;
     std::memset(&B, 0, sizeof(B));
-    SmallLaunch l = size_small_batch({c}, F, opts->tune, false, B.site_stride, B.comp_stride);
-    if (!l.ok || l.T != T) return MBC_ERR_UNSUPPORTED;
+    B.site_stride = (int32_t)site_entries;
+    B.comp_stride = hp.n_comp;
     B.n_lists = 1;
     B.tiles_per_slab = l.tiles_per_slab;
     B.total_items = n_slabs * l.tiles_per_slab;

@@ -44,20 +44,28 @@ struct TimedLaunch {
     }
 };
 
+// FMA throughput probe: NCH independent multiply-add chains per thread, the
+// loop unrolled so that loop control is a small fraction of the issue slots.
+// Launched with every SM filled to its occupancy limit (one wave of equal
+// blocks), so no SM idles while others finish.
 template <class T>
 __global__ void k_fma_probe(T *out, int iters, T seed) {
-    T a[8];
+    constexpr int NCH = 16;
+    T a[NCH];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) a[i] = seed + (T)(threadIdx.x + i);
+    for (int i = 0; i < NCH; ++i) a[i] = seed + (T)(threadIdx.x + i);
     const T m = (T)0.999999, c = (T)1e-7;
-    for (int it = 0; it < iters; ++it) {
+    for (int it = 0; it < iters; it += 4) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = a[i] * m + c;
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int i = 0; i < NCH; ++i) a[i] = a[i] * m + c;
     }
     T s = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) s += a[i];
+    for (int i = 0; i < NCH; ++i) s += a[i];
     if (s == (T)-12345.0) out[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the chains live
 }
+constexpr int kProbeChains = 16;
 
 }  // namespace mbc

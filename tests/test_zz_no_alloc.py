@@ -1,8 +1,9 @@
 """The allocation-free entry point, mbc_contract_noalloc.
 
-It serves callers that cannot allocate device memory in steady state (graph
-replay set-ups, pre-reserved memory pools, real-time loops): its scratch is a
-static device array inside the library. Its results must agree with
+It serves callers that cannot allocate device memory in steady state
+(services whose device memory is reserved up front by their own pool,
+real-time loops that forbid allocator calls): its scratch is a static device
+array inside the library. Its results must agree with
 mbc_contract's within the FP64 bound of the parity tests, on two calls in a
 row (the shared array keeps the previous call's contents). This file is
 collected last on purpose.
@@ -43,8 +44,12 @@ def test_noalloc_matches_contract_twice():
         for call in range(2):
             out = torch.full((2, 1, 3, len(moms), len(comps)), complex(float("nan"), 0.0), dtype=torch.complex128,
                              device="cuda:0")
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
             mbc.contract_noalloc(field, tl, out, moms=moms)
             torch.cuda.synchronize()
+            if call == 1:  # after the first call's one-time set-up: no device memory taken
+                assert torch.cuda.mem_get_info()[0] == free0
             got = out.cpu().numpy()[:, 0]
             for cfg in range(2):
                 for t in range(3):
