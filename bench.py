@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--tune", default="", help='fixed launch shape as JSON, e.g. {"wave_sites": 256}')
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-config", action="store_true",
+                    help="skip the relativistic 4He and 8Be entries reported beside the default line")
     return ap.parse_args()
 
 
@@ -166,10 +168,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def profiled_traffic(name, sites):
-    """DRAM bytes per launch of a kernel from its committed ncu summary
-    (bytes per site x sites), or None when the kernel source changed since
-    the counters were taken."""
+def profiled_traffic(name, sites, sources=("small_kernel.cuh", "device_common.cuh")):
+    """DRAM bytes of a kernel from its committed ncu summary (bytes per site
+    x sites), or None when the kernel source changed since the counters were
+    taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
@@ -181,7 +183,7 @@ def profiled_traffic(name, sites):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for src in ("small_kernel.cuh", "device_common.cuh"):
+    for src in sources:
         with open(os.path.join(ROOT, "paper_1301_4895_gb300", "csrc", src), "rb") as f:
             h.update(f.read())
     if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16] or "traffic_bytes_per_site" not in vals:
@@ -226,9 +228,10 @@ def cpu_model() -> str:
     return fields.get("Model", "unknown")
 
 
-def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0):
+def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0, max_sites=None):
     """The oracle (O3, plain C with OpenMP) on a bounded sample: whole slabs
-    of the same workload until the budget is spent."""
+    of the same workload until the budget is spent (relativistic or large
+    lattices: the first sites of each slab; max_sites caps them)."""
     from oracle import recursion
     _, nuclei, dims, nt, seed, lam, dt = wl
     import synth
@@ -247,6 +250,8 @@ def cpu_baseline(wl, lists_spec, nt_used, budget_s=15.0):
         for pl in plans:
             if v3 > 4096 or pl.A > 4 or pl.dim == 4:
                 n_sites = min(v3, 256 if pl.A <= 4 else 8)
+            if max_sites:
+                n_sites = min(n_sites, max_sites)
             pl.evaluate(S[:n_sites], batch=16)
             done += n_sites
         t_tot += time.perf_counter() - t0
@@ -367,6 +372,125 @@ def run_reference(args, wl):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def point_flops_per_site(stats, list_dims):
+    """Algorithmic flops per sink site of point-sink lists: recursion (8 per
+    operation) and contraction of every list, plus one diquark and one block
+    per species and operator type (the blocks of a site do not depend on the
+    nucleus, Sec. 2)."""
+    fl = [site_flops(st, d) for st, d in zip(stats, list_dims)]
+    per_site = sum(f["recursion"] + f["contraction"] for f in fl)
+    for d in sorted(set(list_dims)):
+        nxi = 3 * d
+        species = set()
+        bs = 0
+        for st, dd in zip(stats, list_dims):
+            if dd == d:
+                species |= set(st["path"])
+                bs = st["block_size"]
+        per_site += 3 * nxi * nxi * (2 * (4 if d == 4 else 2)) * 8 + len(species) * bs * 6 * 8
+    return per_site
+
+
+def roofline_entry(flops_step, steps, kms, ms, launches, peak, probe, kind, kernel):
+    """ALU roofline of the contraction kernels: algorithmic flops over their
+    CUDA-event time (the whole step when no kernel events were recorded)."""
+    t_ms, basis = (kms, "kernel events") if kms > 0 else (ms, "whole step")
+    if not (t_ms == t_ms) or t_ms <= 0:
+        return None
+    ach = flops_step * steps / (t_ms * 1e-3)
+    return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_kind": kind, "measured_fma_peak": probe / 1e12,
+            "frac_of_measured_fma": ach / probe, "kernel": kernel, "time_basis": basis,
+            "kernel_ms_per_step": t_ms / steps, "launches_timed": launches, "flops_per_step": flops_step}
+
+
+# Configurations of the metric's headline nuclei reported beside the default
+# line: (workload, what the entry covers, oracle sample sites, profile of the
+# dominant kernels' DRAM traffic per site: FP64, mixed).
+PER_CONFIG = {
+    "he4rel_all_components": (
+        "he4rel", "4He relativistic, all 1296 spin components (Table 1: 531,321,120 operations per site), "
+        "one 16^3 slab (t = 0) of the 16^3x32 lattice, complex128, seed 2", 8,
+        ("k_large_step_fp64_he4rel_all_16x16x16x1.md", "k_large_step_mx2_mixed_he4rel_all_16x16x16x1.md")),
+    "be8": (
+        "be8", "8Be relativistic (0,1,2,3,0,1,2,3) (Tables 1, 5: 448,496,928 operations per site), one 16^3 slab "
+        "(configuration 0, t = 0) of the 16^3x32 x 12 lattice, complex64 storage, seed 4", 8,
+        ("k_large_step_fp64_be8_16x16x16x1.md", "k_large_step_mx2_mixed_be8_16x16x16x1.md")),
+}
+
+
+def per_config_entry(mbc, torch, dev, name, peaks, n_sm, probes, warmup=3, steps64=1, steps_mx=3):
+    """FP64 and mixed throughput of one headline configuration on one slab
+    (the full lattices scale linearly in slabs: no work is shared between
+    slabs), with its roofline, clocks, host-buffer e2e (mixed) and the oracle
+    on a bounded sample of the same slab."""
+    key, what, cpu_sites, prof = PER_CONFIG[name]
+    wl = WORKLOADS[key]
+    _, nuclei, dims, _, _, _, _ = wl
+    nt = 1
+    lists = [mbc.build_term_list(n_p, n_n, D, spins=spins) for (n_p, n_n, D, spins) in nuclei]
+    stats = [tl.stats() for tl in lists]
+    field_np = make_field(wl, [0], nt)
+    field = torch.from_numpy(field_np).to(dev)
+    stream = torch.cuda.Stream(dev)
+    v3 = dims[0] * dims[1] * dims[2]
+    units = v3 * nt * len(nuclei)
+    flops_step = point_flops_per_site(stats, [n[2] for n in nuclei]) * v3 * nt
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = {0: n_sm * 2 * 2 * sm_max * 1e6, 1: n_sm * 128 * 2 * sm_max * 1e6}
+    kinds = {0: f"FP64 vector, derived: {n_sm} SMs x 2 DFMA/clk x max SM clock",
+             1: f"FP32 vector, derived: {n_sm} SMs x 128 FFMA/clk x max SM clock"}
+    kernels = {0: "k_large_step<FP64>", 1: "k_large_step_mx2"}
+    src = ("large_kernel.cuh", "mixed_common.cuh", "device_common.cuh")
+    entry = {"workload": what, "units_per_step": units, "sites_per_step": v3 * nt, "n_ops": [st["n_ops_total"] for st in stats],
+             "unit": "sink-site correlators/s", "warmup": warmup, "steps": {"fp64": steps64, "mixed": steps_mx}}
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        for prec, steps in ((0, steps64), (1, steps_mx)):
+            for _ in range(warmup):
+                mbc.contract(field, lists, precision=prec, stream=stream)
+            torch.cuda.synchronize(dev)
+            mbc.timing_enable(True)
+            mbc.timing_read()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                mbc.contract(field, lists, precision=prec, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            kms, launches = mbc.timing_read()
+            mbc.timing_enable(False)
+            roof = roofline_entry(flops_step, steps, kms, ms, launches, peak[prec], probes[prec], kinds[prec],
+                                  kernels[prec])
+            if roof is not None:
+                roof["traffic"] = profiled_traffic(prof[prec], v3 * nt, src)
+                roof["traffic_note"] = ("DRAM bytes of the step kernel per step (all its launches), from the "
+                                        "committed ncu summary scaled by sites; null if the kernel changed since")
+            entry["fp64" if prec == 0 else "mixed"] = {"value": units * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                                                       "roofline": roof}
+    entry["clocks"] = clk.summary()
+    entry["mixed"]["speedup_vs_fp64"] = entry["mixed"]["value"] / entry["fp64"]["value"]
+    # end to end through the public API with host buffers (pinned), mixed
+    pinned = torch.empty(field_np.shape, dtype=field.dtype, pin_memory=True)
+    pinned.copy_(torch.from_numpy(field_np))
+    host = pinned.numpy()
+    mbc.contract(host, lists, precision=1)
+    t0 = time.perf_counter()
+    res = mbc.contract(host, lists, precision=1)
+    _ = complex(res.reshape(-1)[0])
+    dt_s = time.perf_counter() - t0
+    entry["e2e"] = {"value": units / dt_s, "unit": "sink-site correlators/s", "precision": "mixed", "steps": 1,
+                    "h2d_bytes_per_step": int(field_np.nbytes), "d2h_bytes_per_step": int(res.nbytes)}
+    entry["cpu_baseline"] = cpu_baseline(wl, [(n, tl.components()) for n, tl in zip(nuclei, lists)], nt,
+                                         budget_s=8.0, max_sites=cpu_sites)
+    for tl in lists:
+        tl.free()
+    del field
+    torch.cuda.empty_cache()
+    return entry
 
 
 def main():
@@ -520,7 +644,6 @@ def main():
     value_mx = units_per_step * world * args.steps / (msmx * 1e-3)
     value = value64 if primary == 0 else value_mx
     # roofline of the dominant kernel (the contraction kernel; FP64 pipe)
-    fl = [site_flops(st, d) for st, d in zip(stats, list_dims)]
     if sink == "block":
         # per site: blocks of one sink function and their phase-weighted sums
         # over the momenta; per (cfg, t, group): recursion and contraction
@@ -533,20 +656,7 @@ def main():
             per_item += 8 * st["n_ops_total"] + 4 * st["n_l_total"]
         flops_step = (per_site * v3 + per_item * (n_mom // n_sinks)) * nt * args.cfgs
     else:
-        # the blocks of a site do not depend on the nucleus (Sec. 2): nuclei
-        # with the same operators need one diquark and one block of each
-        # species per site, whatever the number of nuclei
-        per_site = sum(f["recursion"] + f["contraction"] for f in fl)
-        for d in sorted(set(list_dims)):
-            nxi = 3 * d
-            species = set()
-            bs = 0
-            for st, dd in zip(stats, list_dims):
-                if dd == d:
-                    species |= set(st["path"])
-                    bs = st["block_size"]
-            per_site += 3 * nxi * nxi * (2 * (4 if d == 4 else 2)) * 8 + len(species) * bs * 6 * 8
-        flops_step = per_site * v3 * nt * args.cfgs
+        flops_step = point_flops_per_site(stats, list_dims) * v3 * nt * args.cfgs
     peaks = measured_peaks()
     probe64 = mbc.fma_probe(0)
     probe32 = mbc.fma_probe(1)
@@ -566,16 +676,7 @@ def main():
             kname = {p: "k_project_blocks + " + k for p, k in kname.items()}
 
     def roofline(kms, ms, launches, peak, probe, kind, prec):
-        # kernel time from the library's CUDA events; with graph replay those
-        # are not recorded and the whole step time is used instead
-        t_ms, basis = (kms, "kernel events") if kms > 0 else (ms, "whole step")
-        if not (t_ms == t_ms) or t_ms <= 0:
-            return None
-        ach = flops_step * args.steps / (t_ms * 1e-3)
-        return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "peak_kind": kind, "measured_fma_peak": probe / 1e12,
-                "frac_of_measured_fma": ach / probe, "kernel": kname[prec], "time_basis": basis,
-                "kernel_ms_per_step": t_ms / args.steps, "launches_timed": launches, "flops_per_step": flops_step}
+        return roofline_entry(flops_step, args.steps, kms, ms, launches, peak, probe, kind, kname[prec])
 
     roof64 = roofline(k64, ms64, n64, nominal64, probe64,
                       f"FP64 vector, derived: {n_sm} SMs x 2 DFMA/clk x max SM clock", 0)
@@ -611,6 +712,9 @@ def main():
         "gpu_launches_per_step": {"fp64": launch_count[0] / args.steps, "mixed": launch_count[1] / args.steps},
         "n_ops": [st["n_ops_total"] for st in stats],
     }
+    if not args.no_per_config and world == 1 and args.workload == "nonrel" and not (args.combined or args.graph):
+        line["per_config"] = {name: per_config_entry(mbc, torch, dev, name, peaks, n_sm, {0: probe64, 1: probe32})
+                              for name in PER_CONFIG}
     if not args.no_cpu_baseline and world == 1:  # the oracle baseline is a single-GPU figure
         if sink == "block":
             line["cpu_baseline"] = cpu_baseline_projected(wl, [(n, tl.components()) for n, tl in zip(nuclei, lists)],

@@ -284,10 +284,10 @@ typedef struct {
     int32_t wave_sites;         /* large-stage kernels: sites in flight        */
     int32_t regime;             /* 0 auto, 1 force small-stage, 2 force large  */
     int32_t zchunk;             /* large-stage step kernel: outputs per warp item */
-    int32_t wave_order;         /* FP64 large-stage step kernel: 0 site groups of a
-                                   chunk side by side, 1 a CTA's warps on consecutive
-                                   chunks of one site group (the mixed step kernels
-                                   have one order)                                */
+    int32_t wave_order;         /* large-stage step kernels on stored lists: 0 site
+                                   groups of a chunk side by side, 1 a CTA's warps on
+                                   consecutive chunks of one site group; 2 (mixed
+                                   only) as 1 with 32 warps per CTA, one CTA per SM */
     int32_t list_free;          /* large-stage step kernel: 0 regenerate the splits of
                                    list-free lists, read the arrays of the others;
                                    1 also regenerate the dense steps of lists with
@@ -415,10 +415,13 @@ mbc_status mbc_timing_read(double *ms, int64_t *launches);
 int64_t mbc_kernel_launches(void);
 
 /*
- * Arithmetic peak probe: runs independent FMA chains on every SM of the
- * current device (precision MBC_FP64: DFMA, MBC_MIXED: FFMA) and writes the
- * achieved flop/s (2 flops per FMA) to *flops. Synchronous; used as the
- * measured denominator of the ALU roofline.
+ * Arithmetic peak probe: fills every SM of the current device (one wave at
+ * the occupancy limit) with independent FMA work and writes the achieved
+ * flop/s (2 flops per FMA) to *flops. MBC_FP64: complex multiply-accumulate
+ * on FP64 registers (the operand pattern of the contraction kernels; chains
+ * that reuse one multiplier register read back lower on this pipe).
+ * MBC_MIXED: packed FP32-pair FMA chains. Synchronous; used as the measured
+ * denominator of the ALU roofline. No counterpart in the paper.
  */
 mbc_status mbc_fma_probe(int32_t precision, double *flops);
 

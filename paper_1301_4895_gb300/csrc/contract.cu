@@ -647,21 +647,30 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
     if constexpr (!std::is_same<Tr, FP64Traits>::value) {
         // mixed precision, stored operations: two sites per lane (W is a
         // multiple of 64; the planar pair layout of the wave buffers is this
-        // kernel's)
-        const int threads = 256;
-        const int64_t total_warps = (int64_t)nsm * 8 * (threads / 32);
+        // kernel's).
+        // wave_order 1: the warps of a CTA on consecutive chunks of one site
+        // group; 2: the same with 32 warps per CTA (one CTA per SM)
+        const int order = tune ? tune->wave_order : 0;
+        const int threads = order == 2 ? 1024 : 256;
+        const int64_t total_warps = (int64_t)nsm * 64;
         const int64_t ngroups = W / 64;
         int64_t zchunk = (s.n_z * ngroups + 8 * total_warps - 1) / (8 * total_warps);
         zchunk = std::max<int64_t>(1, std::min<int64_t>(zchunk, 256));
         if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
         const int64_t items = ((s.n_z + zchunk - 1) / zchunk) * ngroups;
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)nsm * 8));
+        const int wpb = threads / 32;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + wpb - 1) / wpb, (int64_t)nsm * 64 / wpb));
         {
             TimedLaunch tl(stream);
             note_launch();
-            k_large_step_mx2<<<(unsigned)grid, threads, 0, stream>>>(
-                c->d_opx[m], c->d_opy[m], s.n_z, s.k, zchunk, W, reinterpret_cast<const float2 *>(X),
-                reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
+            if (order == 2)
+                k_large_step_mx2<32><<<(unsigned)grid, threads, 0, stream>>>(
+                    c->d_opx[m], c->d_opy[m], s.n_z, s.k, zchunk, W, 1, reinterpret_cast<const float2 *>(X),
+                    reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
+            else
+                k_large_step_mx2<8><<<(unsigned)grid, threads, 0, stream>>>(
+                    c->d_opx[m], c->d_opy[m], s.n_z, s.k, zchunk, W, order, reinterpret_cast<const float2 *>(X),
+                    reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
         }
         MBC_CUDA_TRY(cudaGetLastError());
         return MBC_OK;
@@ -1401,12 +1410,12 @@ extern "C" mbc_status mbc_fma_probe(int32_t precision, double *flops) {
     // one full wave: every SM runs as many probe blocks as fit at once
     int per_sm = 0;
     if (precision == MBC_FP64)
-        MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe<double>, threads, 0));
+        MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe64, threads, 0));
     else
-        MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe<float>, threads, 0));
+        MBC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe32, threads, 0));
     const int blocks = nsm * std::max(1, per_sm);
     // tens of milliseconds per launch (clocks settle, launch cost vanishes)
-    const int iters = precision == MBC_FP64 ? 4096 : 131072;
+    const int iters = precision == MBC_FP64 ? 2048 : 65536;
     void *buf = nullptr;
     MBC_CUDA_TRY(cudaMalloc(&buf, (size_t)threads * blocks * sizeof(double)));
     cudaEvent_t a, b;
@@ -1416,9 +1425,9 @@ extern "C" mbc_status mbc_fma_probe(int32_t precision, double *flops) {
     for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(a);
         if (precision == MBC_FP64)
-            k_fma_probe<double><<<blocks, threads>>>((double *)buf, iters, 1.0);
+            k_fma_probe64<<<blocks, threads>>>((double *)buf, iters);
         else
-            k_fma_probe<float><<<blocks, threads>>>((float *)buf, iters, 1.0f);
+            k_fma_probe32<<<blocks, threads>>>((float *)buf, iters);
         cudaEventRecord(b);
         cudaEventSynchronize(b);
         float ms = 0.f;
@@ -1430,7 +1439,8 @@ extern "C" mbc_status mbc_fma_probe(int32_t precision, double *flops) {
     cudaEventDestroy(b);
     cudaFree(buf);
     if (e != cudaSuccess) return MBC_ERR_CUDA;
-    *flops = 2.0 * kProbeChains * (double)iters * (double)threads * blocks / (best * 1e-3);
+    const double fmas = precision == MBC_FP64 ? probe64_fmas(iters) : probe32_fmas(iters);
+    *flops = 2.0 * fmas * (double)threads * blocks / (best * 1e-3);
     return MBC_OK;
 }
 

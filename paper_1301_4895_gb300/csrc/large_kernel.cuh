@@ -233,21 +233,33 @@ __device__ __forceinline__ void pair_terms(const OpRec *rec, int n, const unsign
     }
 }
 
-__global__ void __launch_bounds__(256, 4) k_large_step_mx2(const uint32_t *__restrict__ opx,
-                                                        const uint16_t *__restrict__ opy, int64_t n_z, int64_t k,
-                                                        int64_t zchunk, int W, const float2 *__restrict__ X,
-                                                        const float2 *__restrict__ Y, float2 *__restrict__ Z) {
-    __shared__ OpRec recs[8][32];
+template <int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? 4 : 1)
+    k_large_step_mx2(const uint32_t *__restrict__ opx, const uint16_t *__restrict__ opy, int64_t n_z, int64_t k,
+                     int64_t zchunk, int W, int order, const float2 *__restrict__ X, const float2 *__restrict__ Y,
+                     float2 *__restrict__ Z) {
+    __shared__ OpRec recs[WARPS][32];
     const int lane = threadIdx.x & 31;
-    OpRec *rec = recs[(threadIdx.x >> 5) & 7];
-    const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    OpRec *rec = recs[threadIdx.x >> 5];
+    const int64_t warp_global = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
     const int ngroups = W >> 6;
     const int64_t nchunks = (n_z + zchunk - 1) / zchunk;
     const uint32_t row_bytes = (uint32_t)W * (uint32_t)sizeof(float2);
     for (int64_t item = warp_global; item < nchunks * ngroups; item += nwarps) {
-        const int64_t chunk = item / ngroups;
-        const int group = (int)(item % ngroups);
+        // order 0: consecutive warps take the site groups of one chunk (they
+        // share operation words); order 1: the warps of a CTA take
+        // consecutive chunks of one site group (they share rows of X and Y)
+        int64_t chunk;
+        int group;
+        if (order == 0 || nchunks % WARPS != 0) {
+            chunk = item / ngroups;
+            group = (int)(item % ngroups);
+        } else {
+            const int64_t blk = item / WARPS;
+            group = (int)(blk % ngroups);
+            chunk = (blk / ngroups) * WARPS + item % WARPS;
+        }
         const int col4 = group * 32 + lane;  // float4 column: sites 2 col4, 2 col4 + 1
         const unsigned char *Xc = reinterpret_cast<const unsigned char *>(reinterpret_cast<const float4 *>(X) + col4);
         const unsigned char *Yc = reinterpret_cast<const unsigned char *>(reinterpret_cast<const float4 *>(Y) + col4);

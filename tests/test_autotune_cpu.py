@@ -1,7 +1,7 @@
 """Candidate launch shapes of the autotuner (host logic, no GPU): every
 candidate is a valid tuning record, the kernels a list set uses decide which
-fields vary, and the item-order choice is offered only where a kernel has it
-(the FP64 wave step)."""
+fields vary, and the item orders are offered per wave step kernel (FP64: 0
+and 1; mixed: 0 and 2, one CTA of 32 warps per SM on one site group)."""
 import paper_1301_4895_gb300 as mbc
 from paper_1301_4895_gb300 import autotune
 
@@ -28,7 +28,7 @@ def test_candidates_cover_each_regime():
     assert all(not ({"sites_per_cta", "threads_per_cta"} & set(c)) for c in _cands(rel, mbc.FP64))
 
 
-def test_item_order_only_for_the_fp64_wave_step():
+def test_item_orders_per_wave_step_kernel():
     rel = [mbc.build_term_list(1, 1, 4)]
-    assert any(c.get("wave_order") == 1 for c in _cands(rel, mbc.FP64))
-    assert not any("wave_order" in c for c in _cands(rel, mbc.MIXED))
+    assert {c.get("wave_order", 0) for c in _cands(rel, mbc.FP64)} == {0, 1}
+    assert {c.get("wave_order", 0) for c in _cands(rel, mbc.MIXED)} == {0, 2}

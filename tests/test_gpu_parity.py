@@ -349,7 +349,7 @@ def test_wave_order_and_chunking_variants(mbc):
     sp = (0, 1, 0, 1)
     tl = mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])
     for tune in ({"wave_order": 1, "zchunk": 8}, {"wave_order": 1, "zchunk": 3, "wave_sites": 32},
-                 {"wave_order": 0, "zchunk": 1}):
+                 {"wave_order": 0, "zchunk": 1}, {"wave_order": 2, "zchunk": 2}):
         check_legs(mbc, 14, 1, 2, dims, 0.4, [tl], [(2, 2, 4)], tune=tune)
 
 
