@@ -285,9 +285,12 @@ typedef struct {
     int32_t regime;             /* 0 auto, 1 force small-stage, 2 force large  */
     int32_t zchunk;             /* large-stage step kernel: outputs per warp item */
     int32_t wave_order;         /* large-stage step kernels on stored lists: 0 site
-                                   groups of a chunk side by side, 1 a CTA's warps on
-                                   consecutive chunks of one site group; 2 (mixed
-                                   only) as 1 with 32 warps per CTA, one CTA per SM */
+                                   groups of a chunk side by side (mixed: block rows
+                                   of runs of outputs staged in shared memory by
+                                   bulk copies on the steps where that pays), 1 a
+                                   CTA's warps on consecutive chunks of one site
+                                   group; mixed only: 2 as 1 with 32 warps per CTA,
+                                   one CTA per SM, 3 as 0 without the staging     */
     int32_t list_free;          /* large-stage step kernel: 0 regenerate the splits of
                                    list-free lists, read the arrays of the others;
                                    1 also regenerate the dense steps of lists with
@@ -391,8 +394,25 @@ mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *const *list
 mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_term_list *list, const mbc_contract_opts *opts,
                                 void *out, void *stream);
 
-/* Wait for the stream and report any deferred device-side status. */
+/*
+ * Wait for the stream and report the kernels' deferred device-side status:
+ * MBC_ERR_TIMEOUT when a bounded wait of a kernel ran out since the last
+ * report (the kernel then stopped without finishing its work, so the
+ * results of the calls in between are not valid; the status is cleared by
+ * this report and the context stays usable), MBC_ERR_CUDA for a failed CUDA
+ * call, MBC_OK otherwise. The kernels' waits are on asynchronous copies
+ * into shared memory and give up after about a second of polling.
+ */
 mbc_status mbc_sync_status(void *stream);
+
+/*
+ * Test of the timeout path (no counterpart in the paper): launches on stream
+ * one CTA that waits, with the library's bounded wait, on a barrier nothing
+ * completes, giving up after polls polls (1 .. 2^20). The next
+ * mbc_sync_status on that stream then returns MBC_ERR_TIMEOUT. No copy is in
+ * flight and nothing faults. MBC_ERR_INVALID_ARG for polls out of range.
+ */
+mbc_status mbc_check_wait_timeout(uint32_t polls, void *stream);
 
 /* Release the library's device scratch on the current device. */
 void mbc_release_scratch(void);

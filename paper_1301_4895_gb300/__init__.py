@@ -17,7 +17,7 @@ import numpy as np
 __all__ = [
     "MbcError", "load", "build_term_list", "TermList", "contract", "sync_status", "release_scratch",
     "FP64", "MIXED", "C128", "C64", "PROTON", "NEUTRON", "timing_enable", "timing_read", "fma_probe",
-    "contract_noalloc",
+    "contract_noalloc", "check_wait_timeout",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -126,6 +126,8 @@ def load(path: str | None = None):
         lib.mbc_contract_noalloc.restype = ctypes.c_int
         lib.mbc_sync_status.argtypes = [V]
         lib.mbc_sync_status.restype = ctypes.c_int
+        lib.mbc_check_wait_timeout.argtypes = [ctypes.c_uint32, V]
+        lib.mbc_check_wait_timeout.restype = ctypes.c_int
         lib.mbc_release_scratch.argtypes = []
         lib.mbc_release_scratch.restype = None
         lib.mbc_timing_enable.argtypes = [ctypes.c_int32]
@@ -428,7 +430,16 @@ def contract_noalloc(field, term_list, out, moms=((0, 0, 0),), t0: int = 0, t1: 
 
 
 def sync_status(stream=None):
+    """``mbc_sync_status``: wait for the stream; raises MbcError with
+    MBC_ERR_TIMEOUT (5) when a kernel's bounded wait ran out since the last
+    report."""
     _check(load().mbc_sync_status(_stream_ptr(stream)), "mbc_sync_status")
+
+
+def check_wait_timeout(polls: int = 64, stream=None):
+    """``mbc_check_wait_timeout``: run a bounded wait that nothing completes
+    (the timeout path's test); the next sync_status reports MBC_ERR_TIMEOUT."""
+    _check(load().mbc_check_wait_timeout(int(polls), _stream_ptr(stream)), "mbc_check_wait_timeout")
 
 
 def release_scratch():

@@ -130,6 +130,18 @@ void place(std::vector<Interval *> &bufs, size_t n_fixed = 0) {
 
 }  // namespace
 
+// Runs of consecutive outputs of a stored step whose operations name at most
+// kYcRows distinct block rows (the mixed step that stages block rows in
+// shared memory, k_large_step_yc): run r covers outputs [z0[r], z0[r+1]),
+// its rows are rows[y0[r] .. y0[r+1]), and slot[z k + j] is the slot of
+// operation j's row in its run, with the sign in bit 15.
+struct YRuns {
+    bool tried = false, ok = false;
+    int64_t n_runs = 0;
+    uint32_t *d_z0 = nullptr, *d_y0 = nullptr;
+    uint16_t *d_rows = nullptr, *d_slot = nullptr;
+};
+
 struct DeviceCache {
     int device = -1;
     bool small_ok = false;
@@ -150,6 +162,7 @@ struct DeviceCache {
     double *d_comp_inv_norm = nullptr;
     int32_t *d_comp_deg = nullptr;
     int64_t max_stage = 0;
+    std::vector<YRuns> yruns;          // per step, made on first mixed use
 };
 
 namespace {
@@ -165,6 +178,12 @@ void free_cache(DeviceCache *c) {
     for (auto p : c->d_opy) cudaFree(p);
     for (auto p : c->d_zrank) cudaFree(p);
     for (auto p : c->d_xmap) cudaFree(p);
+    for (auto &r : c->yruns) {
+        cudaFree(r.d_z0);
+        cudaFree(r.d_y0);
+        cudaFree(r.d_rows);
+        cudaFree(r.d_slot);
+    }
     cudaFree(c->d_fin_off);
     cudaFree(c->d_fin_z);
     cudaFree(c->d_fin_l);
@@ -609,6 +628,84 @@ GenStep gen_step(const mbc_term_list *L, const DeviceCache *c, size_t m) {
     return g;
 }
 
+// Warps per CTA of k_large_step_yc (one CTA per SM: its staged rows take
+// most of the shared memory) and the poll limit of its bounded waits
+// (about a second).
+constexpr int kYcWarps = 32;
+constexpr uint32_t kWaitPolls = 1u << 24;
+
+// The runs of step m for k_large_step_yc, cut on the host at the first mixed
+// call that runs the step and uploaded with the list's device copy. A step
+// takes the kernel only where staging pays: every output's rows fit one run,
+// the staged rows are at most a fifth of the operations, and a run has on
+// average at least four outputs per warp (with fewer, the warps of a run
+// finish unevenly and the step measured slower than k_large_step_mx2).
+// Returns nullptr otherwise.
+const YRuns *yruns_for(const mbc_term_list *Lc, const DeviceCache *cc, size_t m) {
+    mbc_term_list *L = const_cast<mbc_term_list *>(Lc);
+    DeviceCache *c = const_cast<DeviceCache *>(cc);
+    std::lock_guard<std::mutex> g(L->dev_mu);
+    if (c->yruns.size() != L->steps.size()) c->yruns.assign(L->steps.size(), YRuns{});
+    YRuns &R = c->yruns[m];
+    if (R.tried) return R.ok ? &R : nullptr;
+    R.tried = true;
+    const Step &s = L->steps[m];
+    if (s.generated || s.x.empty() || s.n_z < 1 || s.k < 1 || L->block_size > 32767) return nullptr;
+    const int64_t nb = L->block_size;
+    std::vector<int64_t> in_run((size_t)nb, -1), in_z((size_t)nb, -1);
+    std::vector<uint16_t> slot_of((size_t)nb, 0);
+    std::vector<uint32_t> z0{0}, y0{0};
+    std::vector<uint16_t> rows;
+    std::vector<uint16_t> slot((size_t)(s.n_z * s.k));
+    int64_t run = 0, cur = 0;
+    for (int64_t z = 0; z < s.n_z; ++z) {
+        const uint16_t *ys = s.ys.data() + z * s.k;
+        int64_t fresh = 0, distinct = 0;
+        for (int64_t j = 0; j < s.k; ++j) {
+            const int y = ys[j] & 0x7fff;
+            if (in_z[(size_t)y] == z) continue;
+            in_z[(size_t)y] = z;
+            ++distinct;
+            if (in_run[(size_t)y] != run) ++fresh;
+        }
+        if (distinct > kYcRows) return nullptr;
+        if (cur + fresh > kYcRows) {  // close the run
+            ++run;
+            cur = 0;
+            z0.push_back((uint32_t)z);
+            y0.push_back((uint32_t)rows.size());
+        }
+        for (int64_t j = 0; j < s.k; ++j) {
+            const int y = ys[j] & 0x7fff;
+            if (in_run[(size_t)y] != run) {
+                in_run[(size_t)y] = run;
+                slot_of[(size_t)y] = (uint16_t)cur++;
+                rows.push_back((uint16_t)y);
+            }
+            slot[(size_t)(z * s.k + j)] = (uint16_t)(slot_of[(size_t)y] | (ys[j] & 0x8000));
+        }
+    }
+    z0.push_back((uint32_t)s.n_z);
+    y0.push_back((uint32_t)rows.size());
+    const int64_t n_runs = run + 1;
+    const double ops = (double)s.n_z * (double)s.k;
+    if ((double)rows.size() > 0.2 * ops || s.n_z < 4 * kYcWarps * n_runs) return nullptr;
+    if (upload(&R.d_z0, z0.data(), z0.size()) != MBC_OK || upload(&R.d_y0, y0.data(), y0.size()) != MBC_OK ||
+        upload(&R.d_rows, rows.data(), rows.size()) != MBC_OK || upload(&R.d_slot, slot.data(), slot.size()) != MBC_OK) {
+        cudaFree(R.d_z0);
+        cudaFree(R.d_y0);
+        cudaFree(R.d_rows);
+        cudaFree(R.d_slot);
+        R = YRuns{};
+        R.tried = true;
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    R.n_runs = n_runs;
+    R.ok = true;
+    return &R;
+}
+
 // One recursion step of a wave (k_large_step), reading the stored operations
 // or regenerating them (list-free lists; dense steps on request).
 template <class Tr>
@@ -648,9 +745,33 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         // mixed precision, stored operations: two sites per lane (W is a
         // multiple of 64; the planar pair layout of the wave buffers is this
         // kernel's).
-        // wave_order 1: the warps of a CTA on consecutive chunks of one site
-        // group; 2: the same with 32 warps per CTA (one CTA per SM)
+        // Default: the block rows of each run staged in shared memory
+        // (k_large_step_yc) on the steps where that pays; wave_order 1: the
+        // warps of a CTA on consecutive chunks of one site group; 2: the
+        // same with 32 warps per CTA (one CTA per SM); 3: neither.
         const int order = tune ? tune->wave_order : 0;
+        const YRuns *yr = order == 0 ? yruns_for(L, c, m) : nullptr;
+        if (yr) {
+            const size_t smem = (size_t)kYcRows * 512 + (size_t)kYcWarps * 32 * sizeof(OpRec) + 16;
+            int per_sm = 0;
+            mbc_status pst = prepare_kernel((const void *)k_large_step_yc<kYcWarps>, c->device, 32 * kYcWarps, smem,
+                                            &per_sm);
+            if (pst != MBC_OK) return pst;
+            if (per_sm >= 1) {
+                const int64_t items = yr->n_runs * (W / 64);
+                const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)nsm * per_sm));
+                {
+                    TimedLaunch tl(stream);
+                    note_launch();
+                    k_large_step_yc<kYcWarps><<<(unsigned)grid, 32 * kYcWarps, smem, stream>>>(
+                        c->d_opx[m], yr->d_slot, yr->d_z0, yr->d_y0, yr->d_rows, yr->n_runs, s.k, W, kWaitPolls,
+                        reinterpret_cast<const float2 *>(X), reinterpret_cast<const float2 *>(Y),
+                        reinterpret_cast<float2 *>(Z));
+                }
+                MBC_CUDA_TRY(cudaGetLastError());
+                return MBC_OK;
+            }
+        }
         const int threads = order == 2 ? 1024 : 256;
         const int64_t total_warps = (int64_t)nsm * 64;
         const int64_t ngroups = W / 64;
@@ -669,7 +790,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
                     reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
             else
                 k_large_step_mx2<8><<<(unsigned)grid, threads, 0, stream>>>(
-                    c->d_opx[m], c->d_opy[m], s.n_z, s.k, zchunk, W, order, reinterpret_cast<const float2 *>(X),
+                    c->d_opx[m], c->d_opy[m], s.n_z, s.k, zchunk, W, order == 1 ? 1 : 0, reinterpret_cast<const float2 *>(X),
                     reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
         }
         MBC_CUDA_TRY(cudaGetLastError());
@@ -1344,11 +1465,38 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
 }
 
 extern "C" mbc_status mbc_sync_status(void *stream_v) {
-    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream_v));
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_v);
+    cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return MBC_ERR_CUDA;
     }
+    // the kernels' latched status word (a bounded wait that ran out)
+    unsigned int word = 0;
+    if (cudaMemcpyFromSymbolAsync(&word, g_device_status, sizeof(word), 0, cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return MBC_ERR_CUDA;
+    }
+    if (word) {
+        const unsigned int zero = 0;
+        if (cudaMemcpyToSymbolAsync(g_device_status, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return MBC_ERR_CUDA;
+        }
+        return MBC_ERR_TIMEOUT;
+    }
+    return MBC_OK;
+}
+
+extern "C" mbc_status mbc_check_wait_timeout(uint32_t polls, void *stream_v) {
+    if (polls < 1 || polls > (1u << 20)) return MBC_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_v);
+    k_wait_timeout_check<<<1, 32, 0, stream>>>(polls);
+    MBC_CUDA_TRY(cudaGetLastError());
     return MBC_OK;
 }
 

@@ -9,6 +9,7 @@
 // (x, y, sign) operands that the lanes load cooperatively and broadcast.
 #pragma once
 
+#include "async_copy.cuh"
 #include "device_common.cuh"
 #include "gen_ops.cuh"
 #include "mixed_common.cuh"
@@ -280,6 +281,111 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? 4 : 1)
             reinterpret_cast<ulonglong2 *>(Z + z * W)[col4] = acc.store();
         }
     }
+}
+
+// The mixed step with the block rows staged in shared memory. The outputs
+// of a stored step are cut, on the host, into runs of consecutive outputs
+// whose operations name at most kYcRows distinct block rows f[y]; an
+// operation's y is replaced by its row's slot in the run. A CTA takes
+// (run, 64-site group) items: one thread copies the run's rows for the
+// group (512 B each: 64 sites of FP32 complex in planar pairs) into shared
+// memory with bulk asynchronous copies completing on an mbarrier, then the
+// warps take the run's outputs, two sites per lane as in k_large_step_mx2,
+// and per term gather only X[x] (a 512 B row segment) while f[y] is a
+// conflict-free shared-memory read. Same terms in the same order with the
+// same arithmetic as k_large_step_mx2: bitwise equal results. W must be a
+// multiple of 64.
+constexpr int kYcRows = 384;
+
+template <int G>
+__device__ __forceinline__ void yc_terms(const OpRec *rec, int n, const unsigned char *Xc, const unsigned char *Ys,
+                                         uint32_t row_bytes, PairAcc &acc) {
+    int t = 0;
+    for (; t + G <= n; t += G) {
+        ulonglong2 xv[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            xv[g] = __ldg(reinterpret_cast<const ulonglong2 *>(Xc + (size_t)rec[t + g].x * row_bytes));
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const OpRec r = rec[t + g];
+            acc.fma(xv[g], *reinterpret_cast<const ulonglong2 *>(Ys + r.y), r.sg);
+        }
+    }
+    for (; t < n; ++t) {
+        const OpRec r = rec[t];
+        acc.fma(__ldg(reinterpret_cast<const ulonglong2 *>(Xc + (size_t)r.x * row_bytes)),
+                *reinterpret_cast<const ulonglong2 *>(Ys + r.y), r.sg);
+    }
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, 1)
+    k_large_step_yc(const uint32_t *__restrict__ opx, const uint16_t *__restrict__ oslot,
+                    const uint32_t *__restrict__ run_z0, const uint32_t *__restrict__ run_y0,
+                    const uint16_t *__restrict__ run_rows, int64_t n_runs, int64_t k, int W, uint32_t wait_limit,
+                    const float2 *__restrict__ X, const float2 *__restrict__ Y, float2 *__restrict__ Z) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *rows = smem_raw;                                      // [kYcRows][512 B]
+    OpRec *recs = reinterpret_cast<OpRec *>(smem_raw + (size_t)kYcRows * 512);  // [WARPS][32]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(recs + WARPS * 32);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    OpRec *rec = recs + warp * 32;
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    const int ngroups = W >> 6;
+    const uint32_t row_bytes = (uint32_t)W * (uint32_t)sizeof(float2);
+    uint32_t parity = 0;
+    for (int64_t item = blockIdx.x; item < n_runs * ngroups; item += gridDim.x) {
+        const int64_t r = item / ngroups;
+        const int group = (int)(item % ngroups);
+        if (threadIdx.x == 0) {
+            const uint32_t y0 = __ldg(run_y0 + r), ny = __ldg(run_y0 + r + 1) - y0;
+            fence_proxy_async_smem();  // the previous run's rows were read through the generic proxy
+            mbar_arrive_expect_tx(bar, ny * 512u);
+            const unsigned char *Yg = reinterpret_cast<const unsigned char *>(Y) + (size_t)group * 512;
+            for (uint32_t i = 0; i < ny; ++i)
+                bulk_copy_g2s(rows + (size_t)i * 512, Yg + (size_t)__ldg(run_rows + y0 + i) * row_bytes, 512u, bar);
+        }
+        const bool ok = mbar_wait_bounded(bar, parity, wait_limit);
+        if (__syncthreads_or(!ok)) {
+            // the status word is set; let copies in flight land, then leave
+            mbar_wait_bounded(bar, parity, wait_limit);
+            return;
+        }
+        parity ^= 1u;
+        const int64_t z0 = __ldg(run_z0 + r), z1 = __ldg(run_z0 + r + 1);
+        const unsigned char *Xc = reinterpret_cast<const unsigned char *>(X) + (size_t)group * 512 + lane * 16;
+        const unsigned char *Ys = rows + lane * 16;
+        for (int64_t z = z0 + warp; z < z1; z += WARPS) {
+            PairAcc acc;
+            acc.zero();
+            const uint32_t *ox = opx + z * k;
+            const uint16_t *os = oslot + z * k;
+            for (int64_t b0 = 0; b0 < k; b0 += 32) {
+                const int nb = (int)min((int64_t)32, k - b0);
+                __syncwarp();  // the previous records are consumed
+                if (lane < nb) {
+                    const uint32_t sl = __ldg(os + b0 + lane);
+                    rec[lane] = OpRec{__ldg(ox + b0 + lane), (sl & 0x7fffu) * 512u, f2_sign_pair((sl & 0x8000u) != 0)};
+                }
+                __syncwarp();
+                yc_terms<4>(rec, nb, Xc, Ys, row_bytes, acc);
+            }
+            reinterpret_cast<ulonglong2 *>(Z + z * W)[group * 32 + lane] = acc.store();
+        }
+        __syncthreads();  // every warp has read the rows before the next copies overwrite them
+    }
+}
+
+// A bounded wait that nothing completes: the wait runs out after `limit`
+// polls, the status word records it and the kernel returns (the test of the
+// timeout path; no copy is in flight).
+__global__ void k_wait_timeout_check(uint32_t limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    mbar_wait_bounded(&bar, 0, limit);
 }
 
 // The mixed step with the operations regenerated once per CTA (the mixed

@@ -353,6 +353,39 @@ def test_wave_order_and_chunking_variants(mbc):
         check_legs(mbc, 14, 1, 2, dims, 0.4, [tl], [(2, 2, 4)], tune=tune)
 
 
+def test_staged_block_rows_bitwise(mbc):
+    """The mixed wave step that stages the block rows of runs of outputs in
+    shared memory with bulk copies (the default where it pays) performs the
+    same terms in the same order as the step that gathers both operands
+    (wave_order 3): bitwise equal results over several waves, and within the
+    oracle's bound."""
+    dims = (3, 4, 6)  # 72 sites: two waves of 64
+    sp = (0, 1, 0, 1)
+    lists = [mbc.build_term_list(2, 2, 4, spins=[(sp, sp)]), mbc.build_term_list(1, 1, 4)]
+    field = synth.field(16, 1, 2, dims, 0.4, eps=EPS)
+    staged = run(mbc, field, lists, 1, tune={"wave_sites": 64})
+    plain = run(mbc, field, lists, 1, tune={"wave_sites": 64, "wave_order": 3})
+    assert np.array_equal(staged, plain)
+    check_slabs(mbc, field, lists, [(2, 2, 4), (1, 1, 4)], dims, precisions=(1,), tune={"wave_sites": 64})
+
+
+def test_bounded_wait_timeout_is_reported(mbc):
+    """A kernel's bounded wait that runs out (a barrier nothing completes)
+    latches the device status: the next sync_status reports MBC_ERR_TIMEOUT
+    once, and the context stays usable."""
+    import torch
+    s = torch.cuda.Stream()
+    mbc.sync_status(s)
+    mbc.check_wait_timeout(64, stream=s)
+    with pytest.raises(mbc.MbcError) as ei:
+        mbc.sync_status(s)
+    assert ei.value.status == 5
+    mbc.sync_status(s)  # cleared by the report
+    dims = (2, 2, 2)
+    field = synth.field(6, 1, 1, dims, 0.4, eps=EPS)
+    check_slabs(mbc, field, [mbc.build_term_list(1, 1, 2)], [(1, 1, 2)], dims)
+
+
 @pytest.mark.parametrize("n_p,n_n,D,spins", [(1, 0, 4, None), (1, 1, 2, None), (2, 1, 2, None), (2, 2, 2, None),
                                              (2, 2, 4, [((0, 1, 0, 1), (0, 1, 0, 1))])])
 def test_momentum_projected_blocks(mbc, n_p, n_n, D, spins):
