@@ -607,13 +607,27 @@ def main():
 
     nan = float("nan")
     launch_count = {0: 0, 1: 0}
+    outs = {}
     with ClockSampler(local) as clk:
-        ms64, k64, n64 = (timed(0, args.steps, args.warmup)[:3] if args.precision in ("both", "fp64")
-                          else (nan, 0.0, 0))
-        msmx, kmx, nmx = (timed(1, args.steps, args.warmup)[:3] if args.precision in ("both", "mixed")
-                          else (nan, 0.0, 0))
+        if args.precision in ("both", "fp64"):
+            ms64, k64, n64, outs[0] = timed(0, args.steps, args.warmup)
+        else:
+            ms64, k64, n64 = nan, 0.0, 0
+        if args.precision in ("both", "mixed"):
+            msmx, kmx, nmx, outs[1] = timed(1, args.steps, args.warmup)
+        else:
+            msmx, kmx, nmx = nan, 0.0, 0
     clocks = clk.summary()
     primary = 0 if args.precision in ("both", "fp64") else 1
+    # the one exchange of the sharded path, after the timed region: every
+    # rank's per-slab correlators gathered in slab order (shard.gather_slabs)
+    exchange = None
+    if world > 1:
+        from paper_1301_4895_gb300.shard import gather_slabs
+        res_local = outs[primary].cpu().numpy()  # (cfgs, n_lists, nt, n_mom', n_comp)
+        part = {(rank * args.cfgs + c, t): res_local[c, :, t] for c in range(args.cfgs) for t in range(nt)}
+        full = gather_slabs(part, world * args.cfgs, nt, res_local.shape[1:2] + res_local.shape[3:])
+        exchange = {"kind": "gather of per-slab correlators after the timed region", "bytes": int(full.nbytes)}
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
@@ -699,7 +713,7 @@ def main():
                    "list_free": bool(args.list_free), "list_bytes": [st["op_bytes"] for st in stats],
                    "tune": {"fp64": tunes[0], "mixed": tunes[1]},
                    "l2": "inputs larger than L2 (field %.0f MB)" % (field_np.nbytes / 2 ** 20),
-                   "parallelism": f"configurations sharded over {world} GPU(s)"},
+                   "parallelism": f"configurations sharded over {world} GPU(s)", "exchange": exchange},
         "roofline": roof,
         "fp64": {"value": value64, "ms_per_step": ms64 / args.steps, "roofline": roof64},
         "mixed": {"value": value_mx, "ms_per_step": msmx / args.steps, "speedup_vs_fp64": value_mx / value64,

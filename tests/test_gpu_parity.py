@@ -327,6 +327,38 @@ def test_batched_geometry_sampled(mbc):
         _check_sparse(mbc, 3, dims, 0.4, sites, tl, spec, dtype=np.complex64)
 
 
+def test_autotune_on_batched_geometry(mbc, tmp_path, monkeypatch):
+    """autotune() on the batched configuration's geometry (24^3, complex64,
+    pn, 3He, 4He nonrelativistic and 4He relativistic (0,1,0,1), mixed
+    precision): it times every candidate launch shape, keeps one of them,
+    caches it, and the contraction with the chosen shape matches the oracle
+    on the live sites."""
+    import torch
+    from oracle import site_sum
+    from paper_1301_4895_gb300.autotune import autotune, candidates
+    monkeypatch.setenv("MBC_TUNE_CACHE", str(tmp_path / "tune.json"))
+    dims = (24, 24, 24)
+    sites = [0, 7777, 13823]
+    field = _sparse_slab_field(3, dims, 0.4, sites, dtype=np.complex64, eps=EPS)
+    sp = (0, 1, 0, 1)
+    specs = [(1, 1, 2), (2, 1, 2), (2, 2, 2), (2, 2, 4)]
+    lists = [mbc.build_term_list(1, 1, 2), mbc.build_term_list(2, 1, 2), mbc.build_term_list(2, 2, 2),
+             mbc.build_term_list(2, 2, 4, spins=[(sp, sp)])]
+    dev = torch.from_numpy(field).to("cuda:0")
+    tune = autotune(dev, lists, precision=mbc.MIXED, reps=1)
+    assert tune in list(candidates(lists, mbc.MIXED))
+    assert autotune(dev, lists, precision=mbc.MIXED) == tune  # from the cache
+    out = run(mbc, field, lists, mbc.MIXED, tune=tune)
+    coords = synth.site_coords(dims)[sites]
+    for li, (tl, spec) in enumerate(zip(lists, specs)):
+        comps = tl.components()
+        C, sc = oracle_plan(*spec, comps).evaluate(field.reshape(-1, 12, 12)[sites].astype(np.complex128))
+        ref = site_sum.site_sum(C, coords, tuple(dims[::-1]), [(0, 0, 0)])
+        e = parity.check(out[0, li, 0, :, : len(comps)], ref, site_sum.scale_sum(sc)[None, :], mbc.MIXED,
+                         what=f"autotuned {spec}")
+        record(f"({spec[0]},{spec[1]}) D={spec[2]} autotuned 24^3", mbc.MIXED, e)
+
+
 def test_out_of_memory_is_a_clean_error(mbc):
     """A scratch request beyond the device's memory returns MBC_ERR_OOM and
     leaves the context usable."""
