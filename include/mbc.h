@@ -88,9 +88,11 @@ enum { MBC_PROTON = 0, MBC_NEUTRON = 1 };
  *                source baryon indices become spin x source, chi = N_s alpha + s,
  *                quark indices spinor-colour x source, xi = N_s kappa + s, and
  *                G carries the source deltas (eq. G_tilde); 3 dirac_dim N_s
- *                must not exceed 24. Contraction kernels take
- *                3 dirac_dim N_s <= 12 (one source relativistic, up to two
- *                nonrelativistic); larger lists are built for their counts.
+ *                must not exceed 24. Stages whose index space exceeds 2^27
+ *                (two relativistic sources) are pruned with sorted index
+ *                lists instead of dense marks. Contraction kernels take
+ *                3 dirac_dim N_s <= 24 with point sinks and <= 12 with
+ *                momentum-projected blocks (see mbc_props.n_src).
  *   n_sinks      number of sink functions N_k for the sink baryon indices
  *                psi = N_k alpha + k (Sec. 6); 0 or 1 = one sink. N_k > 1
  *                lists contract with momentum-projected blocks, one momentum
@@ -262,10 +264,12 @@ enum { MBC_SINK_POINT = 0, MBC_SINK_BLOCK_MOMENTUM = 1 };  /* sink function   */
  *                source, and every list must have been built with
  *                n_sources = n_src (else MBC_ERR_INVALID_ARG). The source
  *                quark index of the lists is xi = n_src * kappa + s for
- *                column kappa of source s. Contraction kernels take lists
- *                with one sink function and 3 * dirac_dim * n_src <= 12
- *                (MBC_ERR_UNSUPPORTED otherwise); the allocation-free entry
- *                point takes n_src = 1 only.
+ *                column kappa of source s. Contraction kernels take
+ *                3 * dirac_dim * n_src <= 24 source columns with point
+ *                sinks (two relativistic sources: 12 x 24 tiles) and <= 12
+ *                with momentum-projected blocks (MBC_ERR_UNSUPPORTED
+ *                otherwise); the allocation-free entry point takes n_src = 1
+ *                only.
  */
 typedef struct {
     const void *s_u;

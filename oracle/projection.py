@@ -26,16 +26,18 @@ from .site_sum import phases
 
 def projected_correlators(plan, slab, dims_zyx, moms, chunk: int = 256, n_sinks: int = 1, dirac_dim: int = 0):
     """C(t, n) of one slab with momentum-projected blocks.
-    slab: (Lz, Ly, Lx, 12, 12); returns (C (n_groups, n_req), scale (n_groups,
+    slab: (Lz, Ly, Lx, 12, 12) (or 12 x 24 tiles for a wide plan); returns (C (n_groups, n_req), scale (n_groups,
     n_req)) with n_groups = n_mom / n_sinks (one group = n_sinks momenta, one
     per sink function; dirac_dim, needed when n_sinks > 1, is the number of
     spin values alpha of the single-sink blocks)."""
     import synth
-    S = np.asarray(slab, dtype=np.complex128).reshape(-1, 12, 12)
+    S = np.asarray(slab, dtype=np.complex128)
+    S = S.reshape((-1, 12, S.shape[-1]))
     coords = synth.site_coords(dims_zyx)
     dims_xyz = tuple(dims_zyx[::-1])
     ph = np.stack([phases(coords, dims_xyz, m) for m in moms])  # (n_mom, V)
-    shp = (len(moms), 4, 12, 12, 12)
+    q = plan.nq
+    shp = (len(moms), 4, q, q, q)
     Pp = np.zeros(shp, dtype=np.complex128)
     Pn = np.zeros(shp, dtype=np.complex128)
     Mp = np.zeros(shp)

@@ -30,20 +30,39 @@
  * that is the scale "sum |terms|" used for the error bounds.
  *
  * Keys are 32-bit: bits 0-3 proton spin set, 4-7 neutron spin set, 8-19 the
- * set of u indices, 20-31 the set of d indices (one quark source).
+ * set of u indices, 20-31 the set of d indices (one quark source). Built
+ * with O3_WIDE the keys are 64-bit for two relativistic quark sources
+ * (Sec. 6: 24 quark index values, 8 source baryon index values): bits 0-7
+ * and 8-15 the spin sets, 16-39 the u set, 40-63 the d set; the blocks then
+ * take 12 x 24 propagator tiles (sink rows x source columns) and the
+ * pruning collects keys in sorted arrays instead of a bitmap over all keys.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
 
+#ifdef O3_WIDE
+typedef uint64_t key_t32;
+#define NQ 24  /* quark index values */
+#define NSP 8  /* source baryon index values */
+#define KEY(dp, dn, u, d) \
+    ((uint64_t)(dp) | ((uint64_t)(dn) << 8) | ((uint64_t)(u) << 16) | ((uint64_t)(d) << 40))
+#define KDP(k) ((uint32_t)((k) & 0xFFu))
+#define KDN(k) ((uint32_t)(((k) >> 8) & 0xFFu))
+#define KU(k) ((uint32_t)(((k) >> 16) & 0xFFFFFFu))
+#define KD(k) ((uint32_t)(((k) >> 40) & 0xFFFFFFu))
+#else
 typedef uint32_t key_t32;
-
+#define NQ 12
+#define NSP 4
 #define KEY(dp, dn, u, d) ((uint32_t)(dp) | ((uint32_t)(dn) << 4) | ((uint32_t)(u) << 8) | ((uint32_t)(d) << 20))
 #define KDP(k) ((k) & 0xFu)
 #define KDN(k) (((k) >> 4) & 0xFu)
 #define KU(k) (((k) >> 8) & 0xFFFu)
 #define KD(k) (((k) >> 20) & 0xFFFu)
+#endif
+#define NBLK ((int64_t)4 * NQ * NQ * NQ) /* block entries: sink spin x three source indices */
 
 typedef struct { key_t32 key; int64_t val; } kv_t;
 
@@ -60,7 +79,7 @@ typedef struct {
     int64_t n_need[16];
     key_t32 *need[16];
     int64_t ops[16];          /* ops of step m -> m+1 at index m-1 */
-    int8_t G[4 * 12 * 12 * 12];   /* source tensor: L (eq. def_L) */
+    int8_t G[NSP * NQ * NQ * NQ]; /* source tensor: L (eq. def_L) */
     int8_t Gs[4 * 12 * 12 * 12];  /* sink tensor: the blocks (eq. def_f) */
     double norm;
 } o3_plan;
@@ -70,7 +89,7 @@ static int popc(uint32_t x) { return __builtin_popcount(x); }
 /* sgn(x|y) for one group: (-1)^{#(i in x, j in y, i > j)} */
 static int sgn_group(uint32_t x, uint32_t y) {
     int n = 0;
-    for (int j = 0; j < 12; ++j)
+    for (int j = 0; j < NQ; ++j)
         if (y & (1u << j)) n += popc(x >> (j + 1));
     return (n & 1) ? -1 : 1;
 }
@@ -130,11 +149,11 @@ static int64_t find_key(const key_t32 *k, int64_t n, key_t32 x) {
 static int64_t g_minus(const o3_plan *p, int b, kv_t *out) {
     int64_t n = 0;
     const int8_t *G = p->G;
-#define GV(a, i, j, k) ((int64_t)G[(((a) * 12 + (i)) * 12 + (j)) * 12 + (k)])
-    for (int a = 0; a < 4; ++a)
-        for (int i = 0; i < 12; ++i)
-            for (int j = 0; j < 12; ++j)
-                for (int k = 0; k < 12; ++k) {
+#define GV(a, i, j, k) ((int64_t)G[(((a) * NQ + (i)) * NQ + (j)) * NQ + (k)])
+    for (int a = 0; a < NSP; ++a)
+        for (int i = 0; i < NQ; ++i)
+            for (int j = 0; j < NQ; ++j)
+                for (int k = 0; k < NQ; ++k) {
                     int64_t v;
                     key_t32 key;
                     if (b == 0) { /* proton (u,u,d): u pair slots 1,2 */
@@ -157,12 +176,12 @@ typedef void (*split_cb)(void *ctx, key_t32 x, key_t32 y, int sgn);
 
 static int bits_of(uint32_t m, int *pos) {
     int n = 0;
-    for (int i = 0; i < 12; ++i) if (m & (1u << i)) pos[n++] = i;
+    for (int i = 0; i < NQ; ++i) if (m & (1u << i)) pos[n++] = i;
     return n;
 }
 
 static int64_t for_splits(key_t32 z, int b, split_cb cb, void *ctx) {
-    int dpos[12], upos[12], qpos[12];
+    int dpos[NQ], upos[NQ], qpos[NQ];
     uint32_t dset = b == 0 ? KDP(z) : KDN(z);
     int nd = bits_of(dset, dpos), nu = bits_of(KU(z), upos), nq = bits_of(KD(z), qpos);
     int64_t cnt = 0;
@@ -202,11 +221,13 @@ static void kv_push_cb(void *ctx, key_t32 x, key_t32 y, int s) {
     v->buf[v->n++] = x;
 }
 
+#ifndef O3_WIDE
 static void mark_cb(void *ctx, key_t32 x, key_t32 y, int s) {
     (void)y; (void)s;
     uint64_t *bm = (uint64_t *)ctx;
     __atomic_fetch_or(&bm[x >> 6], (uint64_t)1 << (x & 63), __ATOMIC_RELAXED);
 }
+#endif
 
 static double factorial(int n) { double f = 1; for (int i = 2; i <= n; ++i) f *= i; return f; }
 
@@ -231,7 +252,9 @@ int o3_plan_build(int n_p, int n_n, int dim, const int8_t *path, const int8_t *G
     p->A = A; p->n_p = n_p; p->n_n = n_n; p->dim = dim; p->n_req = n_req;
     memcpy(p->path, path, (size_t)A);
     memcpy(p->G, G, sizeof(p->G));
-    memcpy(p->Gs, G, sizeof(p->Gs));
+#ifndef O3_WIDE
+    memcpy(p->Gs, G, sizeof(p->Gs)); /* one source: the same tensor at the sink */
+#endif
     p->norm = factorial(n_p) * factorial(n_n);
     p->norm *= p->norm;
 
@@ -239,7 +262,7 @@ int o3_plan_build(int n_p, int n_n, int dim, const int8_t *path, const int8_t *G
     kv_t *gm[2];
     int64_t ngm[2];
     for (int b = 0; b < 2; ++b) {
-        gm[b] = (kv_t *)malloc(sizeof(kv_t) * 4 * 12 * 12 * 12);
+        gm[b] = (kv_t *)malloc(sizeof(kv_t) * NSP * NQ * NQ * NQ);
         ngm[b] = g_minus(p, b, gm[b]);
     }
     int64_t nL = ngm[path[0]];
@@ -298,6 +321,19 @@ int o3_plan_build(int n_p, int n_n, int dim, const int8_t *path, const int8_t *G
     p->need[A - 1] = fin.buf;
     p->n_need[A - 1] = fin.n;
 
+#ifdef O3_WIDE
+    /* 4: backward pruning: the x of every split of a needed key of stage m+1,
+     * sorted and made unique, are the needed keys of stage m; every split of
+     * a needed key is one operation */
+    for (int m = A - 1; m >= 1; --m) {
+        keyvec xs = {0, 0, 0};
+        int64_t ops = 0;
+        for (int64_t i = 0; i < p->n_need[m]; ++i) ops += for_splits(p->need[m][i], path[m], kv_push_cb, &xs);
+        p->ops[m - 1] = ops;
+        p->n_need[m - 1] = sorted_unique(xs.buf, xs.n);
+        p->need[m - 1] = xs.buf ? xs.buf : (key_t32 *)malloc(sizeof(key_t32));
+    }
+#else
     /* 4: backward pruning: a bitmap over all 2^32 keys marks the needed
      * components of stage m; every split of a needed key is one operation */
     uint64_t *bm = (uint64_t *)calloc((size_t)1 << 26, sizeof(uint64_t));
@@ -325,6 +361,7 @@ int o3_plan_build(int n_p, int n_n, int dim, const int8_t *path, const int8_t *G
         p->n_need[m - 1] = n;
     }
     free(bm);
+#endif
     *out = p;
     return 0;
 }
@@ -343,7 +380,7 @@ int64_t o3_n_ops(const o3_plan *p, int64_t *per_step, int64_t *stage_sizes) {
 
 /* Needed keys of stage m (1-based), ascending; returns their number and
  * copies them to out when out is not NULL. */
-int64_t o3_stage_keys(const o3_plan *p, int m, uint32_t *out) {
+int64_t o3_stage_keys(const o3_plan *p, int m, key_t32 *out) {
     if (m < 1 || m > p->A) return -1;
     if (out) memcpy(out, p->need[m - 1], sizeof(key_t32) * (size_t)p->n_need[m - 1]);
     return p->n_need[m - 1];
@@ -362,24 +399,24 @@ typedef struct {
     const o3_plan *p;
     int nb;                 /* sites in the batch */
     const cplx *X; const double *Xm;   /* stage m: [need][nb] */
-    const cplx *Y; const double *Ym;   /* block of the added baryon: [12^3*4][nb] */
+    const cplx *Y; const double *Ym;   /* block of the added baryon: [site][NBLK] */
     int64_t nX;
     const key_t32 *kX;
     cplx *acc; double *accm;           /* [nb] */
 } eval_ctx;
 
 static int64_t block_index(key_t32 y, int b) {
-    int pos[12];
+    int pos[NQ];
     uint32_t dset = b == 0 ? KDP(y) : KDN(y);
     int a = __builtin_ctz(dset);
     if (b == 0) {
         bits_of(KU(y), pos);
         int i = pos[0], j = pos[1], k = __builtin_ctz(KD(y));
-        return ((int64_t)(a * 12 + i) * 12 + j) * 12 + k;
+        return ((int64_t)(a * NQ + i) * NQ + j) * NQ + k;
     } else {
         bits_of(KD(y), pos);
         int i = pos[0], k = pos[1], j = __builtin_ctz(KU(y));
-        return ((int64_t)(a * 12 + i) * 12 + j) * 12 + k;
+        return ((int64_t)(a * NQ + i) * NQ + j) * NQ + k;
     }
 }
 
@@ -390,7 +427,7 @@ static void eval_cb(void *vctx, key_t32 x, key_t32 y, int sgn) {
     int64_t iy = block_index(y, (KDP(y) != 0) ? 0 : 1);
     const cplx *xv = c->X + ix * c->nb;
     const double *xm = c->Xm + ix * c->nb;
-    const int64_t NBk = 4 * 12 * 12 * 12;
+    const int64_t NBk = NBLK;
     for (int s = 0; s < c->nb; ++s) {
         cplx t = cmul(xv[s], c->Y[s * NBk + iy]);
         c->acc[s].re += sgn * t.re;
@@ -401,29 +438,30 @@ static void eval_cb(void *vctx, key_t32 x, key_t32 y, int sgn) {
 
 /* 5a: raw blocks f(delta; xi1, xi2, xi3) = sum G(delta; xi') S S S of nb
  * sites and their antisymmetric components for P and N; fm[b], fmm[b] are
- * [site][4*12*12*12] (values and magnitudes), allocated here. */
+ * [site][NBLK] (values and magnitudes), allocated here. S: [site][12][NQ]
+ * (sink row xi', source column xi). */
 static void blocks_batch(const o3_plan *p, int nb, const cplx *S, cplx *fm[2], double *fmm[2]) {
-    const int64_t NB = 4 * 12 * 12 * 12;
+    const int64_t NB = NBLK;
     cplx *fraw = (cplx *)calloc((size_t)(NB * nb), sizeof(cplx));
     double *fmag = (double *)calloc((size_t)(NB * nb), sizeof(double));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int s = 0; s < nb; ++s) {
-        const cplx *Ss = S + (int64_t)s * 144;
+        const cplx *Ss = S + (int64_t)s * 12 * NQ;
         for (int a = 0; a < 4; ++a)
             for (int p1 = 0; p1 < 12; ++p1)
                 for (int p2 = 0; p2 < 12; ++p2)
                     for (int p3 = 0; p3 < 12; ++p3) {
                         int g = p->Gs[((a * 12 + p1) * 12 + p2) * 12 + p3];
                         if (!g) continue;
-                        for (int i = 0; i < 12; ++i)
-                            for (int j = 0; j < 12; ++j)
-                                for (int k = 0; k < 12; ++k) {
-                                    int64_t idx = ((int64_t)(a * 12 + i) * 12 + j) * 12 + k;
-                                    cplx t = cmul(cmul(Ss[p1 * 12 + i], Ss[p2 * 12 + j]), Ss[p3 * 12 + k]);
+                        for (int i = 0; i < NQ; ++i)
+                            for (int j = 0; j < NQ; ++j)
+                                for (int k = 0; k < NQ; ++k) {
+                                    int64_t idx = ((int64_t)(a * NQ + i) * NQ + j) * NQ + k;
+                                    cplx t = cmul(cmul(Ss[p1 * NQ + i], Ss[p2 * NQ + j]), Ss[p3 * NQ + k]);
                                     fraw[s * NB + idx].re += g * t.re;
                                     fraw[s * NB + idx].im += g * t.im;
-                                    fmag[s * NB + idx] += abs(g) * cabs2(Ss[p1 * 12 + i]) *
-                                                          cabs2(Ss[p2 * 12 + j]) * cabs2(Ss[p3 * 12 + k]);
+                                    fmag[s * NB + idx] += abs(g) * cabs2(Ss[p1 * NQ + i]) *
+                                                          cabs2(Ss[p2 * NQ + j]) * cabs2(Ss[p3 * NQ + k]);
                                 }
                     }
     }
@@ -434,12 +472,12 @@ static void blocks_batch(const o3_plan *p, int nb, const cplx *S, cplx *fm[2], d
 #pragma omp parallel for schedule(static)
     for (int s = 0; s < nb; ++s)
         for (int a = 0; a < 4; ++a)
-            for (int i = 0; i < 12; ++i)
-                for (int j = 0; j < 12; ++j)
-                    for (int k = 0; k < 12; ++k) {
-                        int64_t idx = ((int64_t)(a * 12 + i) * 12 + j) * 12 + k;
-                        int64_t sw_p = ((int64_t)(a * 12 + j) * 12 + i) * 12 + k; /* f(a; j, i, k) */
-                        int64_t sw_n = ((int64_t)(a * 12 + k) * 12 + j) * 12 + i; /* f(a; k, j, i) */
+            for (int i = 0; i < NQ; ++i)
+                for (int j = 0; j < NQ; ++j)
+                    for (int k = 0; k < NQ; ++k) {
+                        int64_t idx = ((int64_t)(a * NQ + i) * NQ + j) * NQ + k;
+                        int64_t sw_p = ((int64_t)(a * NQ + j) * NQ + i) * NQ + k; /* f(a; j, i, k) */
+                        int64_t sw_n = ((int64_t)(a * NQ + k) * NQ + j) * NQ + i; /* f(a; k, j, i) */
                         const int64_t o = s * NB;
                         if (i < j) {
                             fm[0][o + idx].re = fraw[o + idx].re - fraw[o + sw_p].re;
@@ -456,12 +494,12 @@ static void blocks_batch(const o3_plan *p, int nb, const cplx *S, cplx *fm[2], d
     free(fmag);
 }
 
-/* 5b-5d for nb items whose blocks are given ([item][4*12*12*12]); results to
+/* 5b-5d for nb items whose blocks are given ([item][NBLK]); results to
  * out/scale rows o0 .. o0 + nb - 1. */
 static void recursion_batch(const o3_plan *p, int nb, cplx *const fm[2], double *const fmm[2], int64_t o0,
                             double *out, double *scale) {
     const int A = p->A;
-    const int64_t NB = 4 * 12 * 12 * 12;
+    const int64_t NB = NBLK;
     /* 5b: F^(1) = f_{B1} on the needed keys of stage 1 */
     int b0 = p->path[0];
     cplx *X = (cplx *)calloc((size_t)(p->n_need[0] * nb), sizeof(cplx));
@@ -508,7 +546,7 @@ static void recursion_batch(const o3_plan *p, int nb, cplx *const fm[2], double 
 }
 
 /*
- * Evaluate the plan on n_sites sites. S: [site][12][12] complex (re, im
+ * Evaluate the plan on n_sites sites. S: [site][12][NQ] complex (re, im
  * interleaved), u = d. out: [site][n_req] complex; scale: [site][n_req]
  * (the magnitude recursion). batch: sites evaluated together.
  */
@@ -517,7 +555,7 @@ int o3_eval(const o3_plan *p, int64_t n_sites, const double *S_in, double *out, 
     for (int64_t s0 = 0; s0 < n_sites; s0 += batch) {
         int nb = (int)((n_sites - s0) < batch ? (n_sites - s0) : batch);
         cplx *fm[2]; double *fmm[2];
-        blocks_batch(p, nb, (const cplx *)S_in + s0 * 144, fm, fmm);
+        blocks_batch(p, nb, (const cplx *)S_in + s0 * 12 * NQ, fm, fmm);
         recursion_batch(p, nb, fm, fmm, s0, out, scale);
         for (int b = 0; b < 2; ++b) { free(fm[b]); free(fmm[b]); }
     }
@@ -525,12 +563,12 @@ int o3_eval(const o3_plan *p, int64_t n_sites, const double *S_in, double *out, 
 }
 
 /* Antisymmetric block components of n_sites sites (Sec. 2, Sec. 4):
- * out_fm[b]: [site][4][12][12][12] complex (re, im interleaved), out_mag[b]
+ * out_fm[b]: [site][4][NQ][NQ][NQ] complex (re, im interleaved), out_mag[b]
  * the magnitudes, for b = 0 (proton) and 1 (neutron); entries that are not
  * independent components are zero. */
 int o3_blocks(const o3_plan *p, int64_t n_sites, const double *S_in, double *fm_p, double *fm_n, double *mag_p,
               double *mag_n) {
-    const int64_t NB = 4 * 12 * 12 * 12;
+    const int64_t NB = NBLK;
     cplx *fm[2]; double *fmm[2];
     blocks_batch(p, (int)n_sites, (const cplx *)S_in, fm, fmm);
     memcpy(fm_p, fm[0], sizeof(cplx) * (size_t)(NB * n_sites));

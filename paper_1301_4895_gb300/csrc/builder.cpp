@@ -28,6 +28,10 @@
 
 #include "mbc_internal.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 namespace {
 
 using u32 = uint32_t;
@@ -177,6 +181,25 @@ inline void for_splits(const Key &z, int b, F &&f) {
                     }
         }
     }
+}
+
+// Index spaces larger than this are tracked as sorted index lists instead of
+// dense marks (two relativistic quark sources: C(24, 6)^2 quark sets alone).
+constexpr i64 kDenseLimit = (i64)1 << 27;
+
+inline int omp_threads() {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+inline int omp_thread() {
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
 }
 
 // ---- Gamma matrices and G (eq. def_g) -------------------------------------
@@ -498,9 +521,40 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
         auto c = counts_after(L->path, m + 1);
         Space sp;
         sp.init(dim_src, nxi, c.kp, c.kn, c.ku, c.kd);  // L lives on source-side baryon indices
+        const auto &g = gm[b];
+        if (sp.size() > kDenseLimit) {
+            // index space too large for dense marks (two relativistic sources):
+            // products collected per thread, sorted by index, equal keys added
+            std::vector<std::vector<std::pair<i64, i64>>> parts_t((size_t)omp_threads());
+#pragma omp parallel for schedule(dynamic, 64)
+            for (i64 i = 0; i < (i64)cur.size(); ++i) {
+                auto &out = parts_t[(size_t)omp_thread()];
+                for (auto &y : g)
+                    if (disjoint(cur[i].k, y.k))
+                        out.push_back({sp.index(unite(cur[i].k, y.k)), cur[i].v * y.v * key_sign(cur[i].k, y.k)});
+            }
+            std::vector<std::pair<i64, i64>> all;
+            for (auto &v : parts_t) {
+                all.insert(all.end(), v.begin(), v.end());
+                std::vector<std::pair<i64, i64>>().swap(v);
+            }
+            std::sort(all.begin(), all.end(), [](const std::pair<i64, i64> &a, const std::pair<i64, i64> &b2) {
+                return a.first < b2.first;
+            });
+            std::vector<SparseEntry> nxt;
+            for (size_t i = 0; i < all.size();) {
+                size_t j = i;
+                i64 v = 0;
+                while (j < all.size() && all[j].first == all[i].first) v += all[j++].second;
+                if (v) nxt.push_back({sp.key(all[i].first), v});
+                i = j;
+            }
+            cur.swap(nxt);
+            if (stage_wanted[(size_t)m + 1]) Lm[(size_t)m + 1] = cur;
+            continue;
+        }
         std::vector<std::atomic<i64>> dense((size_t)sp.size());
         for (auto &d : dense) d.store(0, std::memory_order_relaxed);
-        const auto &g = gm[b];
 #pragma omp parallel for schedule(dynamic, 256)
         for (i64 i = 0; i < (i64)cur.size(); ++i)
             for (auto &y : g)
@@ -525,9 +579,17 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
         auto c = counts_after(L->path, m);
         spaces[(size_t)m].init(dim, nxi, c.kp, c.kn, c.ku, c.kd);
     }
+    // needed components per stage: dense marks, or for index spaces beyond
+    // kDenseLimit a list of full indices (sorted and made unique when read)
+    std::vector<bool> sparse((size_t)A + 1, false);
+    for (int m = 1; m <= A; ++m) sparse[(size_t)m] = spaces[(size_t)m].size() > kDenseLimit;
+    if (list_free)
+        for (int m = 1; m <= A; ++m)
+            if (sparse[(size_t)m]) return MBC_ERR_UNSUPPORTED;  // list-free steps rank dense spaces
     std::vector<std::vector<uint8_t>> need((size_t)A + 1);  // dense marks, allocated when first used
+    std::vector<std::vector<i64>> need_sp((size_t)A + 1);
     for (int m = 1; m <= A; ++m)
-        if (stage_wanted[(size_t)m]) need[(size_t)m].assign((size_t)spaces[(size_t)m].size(), 0);
+        if (stage_wanted[(size_t)m] && !sparse[(size_t)m]) need[(size_t)m].assign((size_t)spaces[(size_t)m].size(), 0);
     struct FinEntry {
         i64 zfull;
         double l;
@@ -564,7 +626,12 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
                 i = k;
             }
             v.resize(w);
-            for (auto &e : v) need[(size_t)R.A][(size_t)e.zfull] = 1;
+            for (auto &e : v) {
+                if (sparse[(size_t)R.A])
+                    need_sp[(size_t)R.A].push_back(e.zfull);
+                else
+                    need[(size_t)R.A][(size_t)e.zfull] = 1;
+            }
         }
     }
     Lm.clear();
@@ -574,15 +641,34 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
     std::vector<std::vector<i64>> members((size_t)A + 1);  // needed full indices, ascending
     std::vector<std::vector<int32_t>> compact((size_t)A + 1);
     for (int m = A; m >= 1; --m) {
-        auto &nd = need[(size_t)m];
         auto &mem = members[(size_t)m];
-        for (i64 i = 0; i < (i64)nd.size(); ++i)
-            if (nd[(size_t)i]) mem.push_back(i);
+        if (sparse[(size_t)m]) {
+            mem.swap(need_sp[(size_t)m]);
+            std::sort(mem.begin(), mem.end());
+            mem.erase(std::unique(mem.begin(), mem.end()), mem.end());
+        } else {
+            auto &nd = need[(size_t)m];
+            for (i64 i = 0; i < (i64)nd.size(); ++i)
+                if (nd[(size_t)i]) mem.push_back(i);
+            std::vector<uint8_t>().swap(nd);
+        }
         if (m == 1) break;
         const Space &sz = spaces[(size_t)m], &sx = spaces[(size_t)m - 1];
+        int b = L->path[m - 1];
+        if (sparse[(size_t)m - 1]) {
+            std::vector<std::vector<i64>> parts_t((size_t)omp_threads());
+#pragma omp parallel for schedule(dynamic, 256)
+            for (i64 i = 0; i < (i64)mem.size(); ++i) {
+                auto &out = parts_t[(size_t)omp_thread()];
+                Key z = sz.key(mem[(size_t)i]);
+                for_splits(z, b, [&](const Key &y) { out.push_back(sx.index(minus(z, y))); });
+            }
+            auto &nx = need_sp[(size_t)m - 1];
+            for (auto &v : parts_t) nx.insert(nx.end(), v.begin(), v.end());
+            continue;
+        }
         auto &nx = need[(size_t)m - 1];
         if (nx.empty()) nx.assign((size_t)sx.size(), 0);
-        int b = L->path[m - 1];
 #pragma omp parallel for schedule(dynamic, 256)
         for (i64 i = 0; i < (i64)mem.size(); ++i) {
             Key z = sz.key(mem[(size_t)i]);
@@ -590,12 +676,20 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
                 __atomic_store_n(&nx[(size_t)sx.index(minus(z, y))], (uint8_t)1, __ATOMIC_RELAXED);
             });
         }
-        std::vector<uint8_t>().swap(nd);
     }
     for (int m = 1; m <= A; ++m) st.stage_size[m - 1] = (i64)members[(size_t)m].size();
 
-    // compact index of every needed component; stage 1 uses block indices
+    // compact index of every needed component; stage 1 uses block indices.
+    // Sparse stages keep no map: the compact index is the position in the
+    // sorted member list.
+    auto compact_index = [&](int m, i64 full) -> i64 {
+        if (!sparse[(size_t)m]) return (i64)compact[(size_t)m][(size_t)full];
+        const auto &mem = members[(size_t)m];
+        auto it = std::lower_bound(mem.begin(), mem.end(), full);
+        return (it != mem.end() && *it == full) ? (i64)(it - mem.begin()) : -1;
+    };
     for (int m = 2; m <= A; ++m) {
+        if (sparse[(size_t)m]) continue;
         auto &cm = compact[(size_t)m];
         cm.assign((size_t)spaces[(size_t)m].size(), -1);
         auto &mem = members[(size_t)m];
@@ -634,7 +728,6 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
         st.op_bytes += k * s.n_z * (i64)(sizeof(uint32_t) + sizeof(uint16_t));
         s.x.resize((size_t)(k * s.n_z));
         s.ys.resize((size_t)(k * s.n_z));
-        const auto &cmx = compact[(size_t)m];
         int bprev = L->path[0];
         std::atomic<bool> bad{false};
 #pragma omp parallel for schedule(dynamic, 256)
@@ -643,7 +736,7 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
             i64 j = 0;
             for_splits(z, b, [&](const Key &y) {
                 Key x = minus(z, y);
-                i64 xi = m == 1 ? block_index(x, bprev, nxi) : (i64)cmx[(size_t)sx.index(x)];
+                i64 xi = m == 1 ? block_index(x, bprev, nxi) : compact_index(m, sx.index(x));
                 if (xi < 0 || j >= k) {
                     bad = true;
                     return;
@@ -663,10 +756,9 @@ mbc_status build(const mbc_op_spec *specs, int n_specs, mbc_term_list *L) {
     for (size_t j = 0; j < parts.size(); ++j) {
         const mbc_term_list::Part &pt = L->parts[j];
         const int Aj = pt.A;
-        const auto &cmA = compact[(size_t)Aj];
         for (int c = pt.c0; c < pt.c1; ++c) {
             for (auto &e : fin[(size_t)c]) {
-                i64 zi = Aj == 1 ? block_index(spaces[1].key(e.zfull), L->path[0], nxi) : (i64)cmA[(size_t)e.zfull];
+                i64 zi = Aj == 1 ? block_index(spaces[1].key(e.zfull), L->path[0], nxi) : compact_index(Aj, e.zfull);
                 L->fin_z.push_back((uint32_t)zi);
                 L->fin_l.push_back(e.l);
             }

@@ -438,9 +438,9 @@ std::mutex g_const_mu;
 mbc_status ensure_constants(int device) {
     std::lock_guard<std::mutex> g(g_const_mu);
     if (device < 31 && (g_const_dev_mask >> device) & 1) return MBC_OK;
-    uint8_t pi[66], pj[66];
+    uint8_t pi[276], pj[276];
     int r = 0;
-    for (int j = 1; j < 12; ++j)
+    for (int j = 1; j < 24; ++j)
         for (int i = 0; i < j; ++i) {  // colex order: rank = i + j(j-1)/2
             pi[r] = (uint8_t)i;
             pj[r] = (uint8_t)j;
@@ -862,11 +862,15 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
     int32_t *sexp = reinterpret_cast<int32_t *>(p);
     const int nsm = sm_count(device);
     const int nxi = L->nxi, nrow = 3 * L->dim;
-    const size_t blk_smem = (size_t)16 * (tile_stride(nrow, nxi) + diquark_stride(nxi)) * sizeof(V);
+    // sites per CTA of the block kernel: 16, or 4 for 24 source columns
+    const int ns_blk = nxi > 12 ? 4 : 16;
+    const void *blk_kern = ns_blk == 4 ? (const void *)k_large_blocks<Tr, 4> : (const void *)k_large_blocks<Tr, 16>;
+    const size_t blk_smem = (size_t)ns_blk * (tile_stride(nrow, nxi) + diquark_stride(nxi)) * sizeof(V);
     {
         int per_sm = 0;
-        mbc_status pst = prepare_kernel((const void *)k_large_blocks<Tr>, device, 512, blk_smem, &per_sm);
+        mbc_status pst = prepare_kernel(blk_kern, device, 512, blk_smem, &per_sm);
         if (pst != MBC_OK) return pst;
+        if (per_sm < 1) return MBC_ERR_UNSUPPORTED;
     }
     for (int64_t item0 = 0; item0 < n_items; item0 += W) {
         WaveDesc wv;
@@ -876,9 +880,14 @@ mbc_status run_large(const mbc_term_list *L, const DeviceCache *c, const FieldDe
         wv.v3p = v3p;
         wv.n_items = n_items;
         note_launch();
-        k_large_blocks<Tr><<<W / 16, 512, blk_smem, stream>>>(F, wv, nrow, nxi, n_g2(L), (int)L->block_size,
-                                                              (int)binom64(nxi, 2), L->need_block[0],
-                                                              L->need_block[1], fP, fN, sexp);
+        if (ns_blk == 4)
+            k_large_blocks<Tr, 4><<<W / 4, 512, blk_smem, stream>>>(F, wv, nrow, nxi, n_g2(L), (int)L->block_size,
+                                                                    (int)binom64(nxi, 2), L->need_block[0],
+                                                                    L->need_block[1], fP, fN, sexp);
+        else
+            k_large_blocks<Tr, 16><<<W / 16, 512, blk_smem, stream>>>(F, wv, nrow, nxi, n_g2(L), (int)L->block_size,
+                                                                      (int)binom64(nxi, 2), L->need_block[0],
+                                                                      L->need_block[1], fP, fN, sexp);
         MBC_CUDA_TRY(cudaGetLastError());
         const V *X = L->path[0] == MBC_PROTON ? fP : fN;
         mbc_status cst = contract_parts<Tr>(L, c, 1, X, W, sexp, 3, Cb, nsm, stream);
@@ -1200,7 +1209,10 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
     for (int i = 0; i < n_lists; ++i) {
         if (!lists[i]) return MBC_ERR_INVALID_ARG;
         if (lists[i]->n_sources != n_src) return MBC_ERR_INVALID_ARG;  // list and field disagree
-        if (lists[i]->nxi > 12) return MBC_ERR_UNSUPPORTED;  // source tiles up to 12 columns (c_pair tables)
+        // source tiles: up to 24 columns with point sinks (two relativistic
+        // sources), 12 with momentum-projected blocks
+        if (lists[i]->nxi > 24 || (lists[i]->nxi > 12 && opts->sink_mode != MBC_SINK_POINT))
+            return MBC_ERR_UNSUPPORTED;
         if (lists[i]->n_sinks != n_k) return MBC_ERR_INVALID_ARG;
     }
     if (n_k > 1 && opts->sink_mode == MBC_SINK_POINT) return MBC_ERR_UNSUPPORTED;  // one sink point per site

@@ -69,9 +69,10 @@ __device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
 __constant__ int c_g2[4][3] = {{0, 1, -1}, {1, 0, 1}, {2, 3, -1}, {3, 2, 1}};
 // epsilon: for colour c of slot 1, the two (c2, c3, sign) completions
 __constant__ int c_eps[3][2][3] = {{{1, 2, 1}, {2, 1, -1}}, {{2, 0, 1}, {0, 2, -1}}, {{0, 1, 1}, {1, 0, -1}}};
-// colex pair decoding for up to 12 values: pair rank -> (i < j)
-__constant__ uint8_t c_pair_i[66];
-__constant__ uint8_t c_pair_j[66];
+// colex pair decoding for up to 24 quark index values (two relativistic
+// sources): pair rank -> (i < j)
+__constant__ uint8_t c_pair_i[276];
+__constant__ uint8_t c_pair_j[276];
 
 // Diquark Q[c][xi2][xi3] = sum_{Gamma_2, eps} v eps S[3 s2 + c2][xi2] S[3 s3 + c3][xi3]
 // (the slot-2/slot-3 part of a block, Sec. 2). S is an nxi x nxi tile.

@@ -41,15 +41,18 @@ __device__ __forceinline__ bool item_site(const FieldDesc &F, const WaveDesc &wv
 __host__ __device__ constexpr int tile_stride(int nrow, int nxi) { return nrow * nxi + 1; }
 __host__ __device__ constexpr int diquark_stride(int nxi) { return 3 * nxi * nxi + 1; }
 
-// Blocks for 16 sites per CTA (512 threads): thread = (site lane, entry slice).
-// The tile of a site has nrow sink rows (3 x Dirac dimension) and nxi source
-// columns (quark index over all sources).
-template <class Tr>
+// Blocks for NS sites per CTA (512 threads): thread = (site lane, entry
+// slice). The tile of a site has nrow sink rows (3 x Dirac dimension) and nxi
+// source columns (quark index over all sources, up to 24: two relativistic
+// sources, Sec. 6); NS = 4 for 24 columns keeps the tiles and diquarks in
+// shared memory.
+constexpr int kTileLoads = 9;  // tile entries per lane: 12 x 24 / 32
+
+template <class Tr, int NS>
 __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, int nrow, int nxi, int n_g2,
                                                       int block_size, int npair, int need_p, int need_n,
                                                       typename Tr::V *fP, typename Tr::V *fN, int32_t *sexp_out) {
     using V = typename Tr::V;
-    constexpr int NS = 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int sst = tile_stride(nrow, nxi), qst = diquark_stride(nxi);
     V *S = reinterpret_cast<V *>(smem_raw);  // [NS][sst]: nrow*nxi entries each
@@ -63,9 +66,10 @@ __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, 
         int cfg, t, site;
         bool live = item_site(F, wv, wv.item0 + w0 + s, cfg, t, site);
         int64_t base = live ? cfg * F.stride_cfg + t * F.stride_t + (int64_t)site * site_elems(F) : 0;
-        double2 sv[5];
+        double2 sv[kTileLoads];
         double amax = 0.0;
-        for (int q = 0; q < 5; ++q) {
+#pragma unroll
+        for (int q = 0; q < kTileLoads; ++q) {
             int e = lane + 32 * q;
             sv[q] = make_double2(0, 0);
             if (live && e < nent) {
@@ -78,7 +82,8 @@ __global__ void __launch_bounds__(512) k_large_blocks(FieldDesc F, WaveDesc wv, 
             for (int off = 16; off > 0; off >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, off));
             se = amax > 0.0 ? -ilogb(amax) : 0;
         }
-        for (int q = 0; q < 5; ++q) {
+#pragma unroll
+        for (int q = 0; q < kTileLoads; ++q) {
             int e = lane + 32 * q;
             if (e < nent) S[s * sst + e] = Tr::from_d(make_double2(scalbn(sv[q].x, se), scalbn(sv[q].y, se)));
         }

@@ -16,8 +16,10 @@ def oracle_plan(n_p, n_n, D, comps):
 
 def oracle_slab(plan, slab, dims_zyx, moms):
     """Site-summed oracle correlators and error scale of one slab.
-    slab: (Lz, Ly, Lx, 12, 12) complex; returns (ref (n_mom, n_comp), scale (n_comp,))."""
-    C, sc = plan.evaluate(np.asarray(slab, dtype=np.complex128).reshape(-1, 12, 12))
+    slab: (Lz, Ly, Lx, 12, 12) complex (12 x 24 tiles for two relativistic
+    sources); returns (ref (n_mom, n_comp), scale (n_comp,))."""
+    slab = np.asarray(slab, dtype=np.complex128)
+    C, sc = plan.evaluate(slab.reshape(-1, 12, slab.shape[-1]))
     coords = synth.site_coords(dims_zyx)
     ref = site_sum.site_sum(C, coords, tuple(dims_zyx[::-1]), moms)
     return ref, site_sum.scale_sum(sc)

@@ -374,3 +374,22 @@ def test_term_list_files_damaged_anywhere(tmp_path):
             b.stats()
         except mbc.MbcError:
             pass
+
+
+@pytest.mark.parametrize("n_p,n_n,spins", [
+    (1, 1, None), (0, 2, [((0, 1), (0, 1))]), (2, 1, [((0, 1, 0), (0, 2, 4))]),
+    pytest.param(2, 2, [((0, 1, 0, 1), (0, 2, 4, 6))], marks=pytest.mark.slow),
+])
+def test_two_relativistic_sources_counts_match_oracle(n_p, n_n, spins):
+    """Two relativistic quark sources (Sec. 6, 24 source quark indices): the
+    builder's sparse index sets give the same pruned stages and operation
+    counts as the oracle's 64-bit-key pruning."""
+    from oracle import gamma, recursion
+    tl = mbc.build_term_list(n_p, n_n, 4, spins=spins, n_sources=2)
+    st = tl.stats()
+    plan = recursion.Plan(n_p, n_n, 4, requests=tl.components(), G=gamma.g_tensor_sources(4, 2),
+                          G_sink=gamma.g_tensor(4))
+    tot, per, stages = plan.ops()
+    assert st["n_ops_total"] == tot
+    assert st["stage_size"][: n_p + n_n] == stages
+    assert st["block_size"] == 4 * 276 * 24

@@ -591,6 +591,31 @@ def test_two_quark_sources_larger_slab(mbc):
             record("(2,2) D=2 two sources 8^3", p, e)
 
 
+def test_two_relativistic_sources(mbc):
+    """Two relativistic quark sources (Sec. 6): 12 x 24 propagator tiles
+    (column xi = 2 kappa + s from source s), G~ at the source, point sinks,
+    against the oracle's 64-bit-key build. pn with all 1024 components; 4He
+    with one component on source 0 alone and one whose neutrons take both
+    sources (79 M operations per site)."""
+    from oracle import gamma, recursion
+    dims = (1, 2, 2)
+    cases = [(1, 1, None), (2, 2, [((0, 1, 0, 1), (0, 2, 4, 6)), ((0, 1, 0, 1), (0, 2, 4, 7))])]
+    for n_p, n_n, spins in cases:
+        tl = mbc.build_term_list(n_p, n_n, 4, spins=spins, n_sources=2)
+        comps = tl.components()
+        plan = recursion.Plan(n_p, n_n, 4, requests=comps, G=gamma.g_tensor_sources(4, 2), G_sink=gamma.g_tensor(4))
+        for field, precs in legs(30, 1, 1, dims, 0.4, n_src=2):
+            ref, scale = oracle_slab(plan, recursion.source_columns(field[0, 0], 4), dims, [(0, 0, 0), (1, 0, 0)])
+            for p in precs:
+                got = run(mbc, field, [tl], p, moms=((0, 0, 0), (1, 0, 0)))[0, 0, 0, :, : len(comps)]
+                e = parity.check(got, ref, scale[None, :], p, what=f"({n_p},{n_n}) D=4 two sources")
+                record(f"({n_p},{n_n}) D=4 two sources", p, e)
+    # momentum-projected blocks keep 12-column tiles: refused, not wrong
+    with pytest.raises(mbc.MbcError) as ei:
+        run(mbc, field, [tl], 0, moms=((0, 0, 0),), sink=mbc.SINK_BLOCK_MOMENTUM)
+    assert ei.value.status == 6
+
+
 def test_loaded_term_lists_contract_identically(mbc, tmp_path):
     """A list written to a file and loaded back contracts bitwise like the
     list that was built (both regimes, a list-free list included)."""

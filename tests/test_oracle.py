@@ -459,3 +459,53 @@ def test_two_sink_functions_pins(rng):
     nx = [sum(pair[psi % 2][0] for psi in snk) for snk, _ in reqs]
     for r in range(2):
         assert abs(Cm[0, r] - C[0, r] * np.exp(-2j * np.pi * nx[r] / 4)) <= 1e-13 * sc[0, r]
+
+
+# ---- two relativistic quark sources (Sec. 6): the 64-bit-key build of O3 ----------
+
+def test_wide_build_equals_narrow_on_one_source(rng):
+    """The O3 build with 64-bit keys (24 quark and 8 source baryon index
+    values) computes single-source correlators exactly as the 32-bit build:
+    same operation counts, bitwise the same values and scales."""
+    S = rand_prop(rng, 2)
+    for n_p, n_n, D, req in ((1, 1, 4, None), (2, 1, 2, None), (2, 2, 4, [((0, 1, 0, 1), (0, 1, 0, 1))])):
+        a = recursion.Plan(n_p, n_n, D, requests=req)
+        b = recursion.Plan(n_p, n_n, D, requests=req, wide=True)
+        assert b.wide and a.ops() == b.ops()
+        Ca, sa = a.evaluate(S)
+        Cb, sb = b.evaluate(S)
+        assert np.array_equal(Ca, Cb) and np.array_equal(sa, sb)
+
+
+@pytest.mark.parametrize("bs,reqs", [
+    ("PN", [((0, 1), (0, 3)), ((2, 3), (5, 6)), ((1, 1), (7, 2)), ((3, 0), (4, 4))]),
+    ("NN", [((0, 1), (1, 6)), ((2, 3), (0, 5))]),
+])
+def test_two_relativistic_sources_equal_wick(rng, bs, reqs):
+    """O3 with G~ over 24 source quark indices (two relativistic sources,
+    chi = 2 alpha + s) equals the explicit Wick sum with the rectangular
+    12 x 24 propagator."""
+    S2 = np.stack([rand_prop(rng), rand_prop(rng)])
+    n_p, n_n = bs.count("P"), bs.count("N")
+    plan = recursion.Plan(n_p, n_n, 4, requests=reqs, G=gamma.g_tensor_sources(4, 2), G_sink=gamma.g_tensor(4))
+    assert plan.wide
+    C, sc = plan.evaluate(recursion.source_columns(S2, 4)[None])
+    for r, (d, a) in enumerate(plan.requests):
+        c1 = wick.correlator_sources(bs, d, a, 4, S2)
+        assert abs(C[0, r] - c1) <= 1e-13 * sc[0, r], (d, a)
+        assert abs(C[0, r]) > 1e-6 * sc[0, r]  # a genuine component
+
+
+@pytest.mark.slow
+def test_two_relativistic_sources_single_source_limit(rng):
+    """4He with two relativistic sources: source indices chi = 2 alpha + s all
+    on source s give the single-source correlator of that source's
+    propagator (alpha = 0, 1 | 2, 3)."""
+    S2 = np.stack([rand_prop(rng), rand_prop(rng)])
+    reqs = [((0, 1, 0, 1), (0, 2, 4, 6)), ((0, 1, 0, 1), (1, 3, 5, 7))]
+    plan = recursion.Plan(2, 2, 4, requests=reqs, G=gamma.g_tensor_sources(4, 2), G_sink=gamma.g_tensor(4))
+    C, sc = plan.evaluate(recursion.source_columns(S2, 4)[None])
+    one = recursion.Plan(2, 2, 4, requests=[((0, 1, 0, 1), (0, 1, 2, 3))])
+    for r, s in ((0, 0), (1, 1)):
+        ref, _ = one.evaluate(S2[s][None])
+        assert abs(C[0, r] - ref[0, 0]) <= 1e-13 * sc[0, r]
