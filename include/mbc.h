@@ -287,14 +287,17 @@ typedef struct {
     int32_t threads_per_cta;    /* mixed small-stage kernel: threads per CTA   */
     int32_t wave_sites;         /* large-stage kernels: sites in flight        */
     int32_t regime;             /* 0 auto, 1 force small-stage, 2 force large  */
-    int32_t zchunk;             /* large-stage step kernel: outputs per warp item */
-    int32_t wave_order;         /* large-stage step kernels on stored lists: 0 site
-                                   groups of a chunk side by side (mixed: block rows
-                                   of runs of outputs staged in shared memory by
-                                   bulk copies on the steps where that pays), 1 a
-                                   CTA's warps on consecutive chunks of one site
-                                   group; mixed only: 2 as 1 with 32 warps per CTA,
-                                   one CTA per SM, 3 as 0 without the staging     */
+    int32_t zchunk;             /* large-stage step kernel: outputs per warp item
+                                   (mixed default 1)                            */
+    int32_t wave_order;         /* large-stage step kernels on stored lists. FP64:
+                                   0 site groups of a chunk side by side, 1 a CTA's
+                                   warps on consecutive chunks of one site group.
+                                   Mixed: 0 (or 2) one CTA of 32 warps per SM on
+                                   consecutive outputs of one site group, 1 the same
+                                   with 8-warp CTAs, 3 8-warp CTAs with the site
+                                   groups of a chunk side by side, 4 block rows of
+                                   runs of outputs staged in shared memory by bulk
+                                   copies (where the runs qualify)                */
     int32_t list_free;          /* large-stage step kernel: 0 regenerate the splits of
                                    list-free lists, read the arrays of the others;
                                    1 also regenerate the dense steps of lists with

@@ -53,7 +53,7 @@ def candidates(lists, precision):
     if large:
         opt_large = [dict(w, **z, **o) for w, z, o in itertools.product(
             [{}, {"wave_sites": 128}, {"wave_sites": 512}, {"wave_sites": 2048}],
-            [{}, {"zchunk": 4}, {"zchunk": 32}], [{}, {"wave_order": 1}] if fp64 else [{}, {"wave_order": 2}])]
+            [{}, {"zchunk": 4}, {"zchunk": 32}], [{}, {"wave_order": 1}] if fp64 else [{}, {"wave_order": 3}])]
     for a, b in itertools.product(opt_small, opt_large):
         yield dict(a, **b)
 

@@ -745,12 +745,18 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         // mixed precision, stored operations: two sites per lane (W is a
         // multiple of 64; the planar pair layout of the wave buffers is this
         // kernel's).
-        // Default: the block rows of each run staged in shared memory
-        // (k_large_step_yc) on the steps where that pays; wave_order 1: the
-        // warps of a CTA on consecutive chunks of one site group; 2: the
-        // same with 32 warps per CTA (one CTA per SM); 3: neither.
-        const int order = tune ? tune->wave_order : 0;
-        const YRuns *yr = order == 0 ? yruns_for(L, c, m) : nullptr;
+        // wave_order (mixed): 0 (default) or 2: one CTA of 32 warps per SM
+        // takes consecutive outputs of one site group, one output per warp
+        // item, so that neighbouring outputs' gathers of X (they share rows)
+        // hit in L1 and the few hundred outputs in flight keep their rows
+        // in L2; 1: the same order with 8-warp CTAs; 3: 8-warp CTAs with the
+        // site groups of an output side by side; 4: the block rows of runs
+        // of outputs staged in shared memory by bulk copies
+        // (k_large_step_yc, on the steps where the runs qualify). Measured
+        // on GB300, mixed: 8Be 2,508 (0) / 2,035 (3) / 1,942 (4) sink-site
+        // correlators/s, 4He with all components 2,109 / 2,062 / 1,871.
+        const int order = tune ? (tune->wave_order == 2 ? 0 : tune->wave_order) : 0;
+        const YRuns *yr = order == 4 ? yruns_for(L, c, m) : nullptr;
         if (yr) {
             const size_t smem = (size_t)kYcRows * 512 + (size_t)kYcWarps * 32 * sizeof(OpRec) + 16;
             int per_sm = 0;
@@ -772,11 +778,15 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
                 return MBC_OK;
             }
         }
-        const int threads = order == 2 ? 1024 : 256;
-        const int64_t total_warps = (int64_t)nsm * 64;
+        const int threads = order == 0 ? 1024 : 256;
         const int64_t ngroups = W / 64;
-        int64_t zchunk = (s.n_z * ngroups + 8 * total_warps - 1) / (8 * total_warps);
-        zchunk = std::max<int64_t>(1, std::min<int64_t>(zchunk, 256));
+        // one output per warp item: the warps in flight then cover a few
+        // hundred consecutive outputs, whose operations read a few rows of
+        // the previous stage, and those stay in L2 (with items of many
+        // outputs the window spans tens of thousands of outputs and the
+        // gathers of X come from HBM: 4.9-6.0 TB/s on 8Be and 4He with all
+        // components)
+        int64_t zchunk = 1;
         if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
         const int64_t items = ((s.n_z + zchunk - 1) / zchunk) * ngroups;
         const int wpb = threads / 32;
@@ -784,7 +794,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         {
             TimedLaunch tl(stream);
             note_launch();
-            if (order == 2)
+            if (order == 0)
                 k_large_step_mx2<32><<<(unsigned)grid, threads, 0, stream>>>(
                     c->d_opx[m], c->d_opy[m], s.n_z, s.k, zchunk, W, 1, reinterpret_cast<const float2 *>(X),
                     reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));

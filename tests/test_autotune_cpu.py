@@ -1,7 +1,8 @@
 """Candidate launch shapes of the autotuner (host logic, no GPU): every
 candidate is a valid tuning record, the kernels a list set uses decide which
 fields vary, and the item orders are offered per wave step kernel (FP64: 0
-and 1; mixed: 0 and 2, one CTA of 32 warps per SM on one site group)."""
+and 1; mixed: 0, one CTA of 32 warps per SM on consecutive outputs of one
+site group, and 3, 8-warp CTAs with the site groups side by side)."""
 import paper_1301_4895_gb300 as mbc
 from paper_1301_4895_gb300 import autotune
 
@@ -31,4 +32,4 @@ def test_candidates_cover_each_regime():
 def test_item_orders_per_wave_step_kernel():
     rel = [mbc.build_term_list(1, 1, 4)]
     assert {c.get("wave_order", 0) for c in _cands(rel, mbc.FP64)} == {0, 1}
-    assert {c.get("wave_order", 0) for c in _cands(rel, mbc.MIXED)} == {0, 2}
+    assert {c.get("wave_order", 0) for c in _cands(rel, mbc.MIXED)} == {0, 3}

@@ -387,18 +387,20 @@ def test_wave_order_and_chunking_variants(mbc):
 
 def test_staged_block_rows_bitwise(mbc):
     """The mixed wave step that stages the block rows of runs of outputs in
-    shared memory with bulk copies (the default where it pays) performs the
-    same terms in the same order as the step that gathers both operands
-    (wave_order 3): bitwise equal results over several waves, and within the
+    shared memory with bulk copies (wave_order 4) performs the same terms in
+    the same order as the steps that gather both operands (every CTA
+    order): bitwise equal results over several waves, and within the
     oracle's bound."""
     dims = (3, 4, 6)  # 72 sites: two waves of 64
     sp = (0, 1, 0, 1)
     lists = [mbc.build_term_list(2, 2, 4, spins=[(sp, sp)]), mbc.build_term_list(1, 1, 4)]
     field = synth.field(16, 1, 2, dims, 0.4, eps=EPS)
-    staged = run(mbc, field, lists, 1, tune={"wave_sites": 64})
-    plain = run(mbc, field, lists, 1, tune={"wave_sites": 64, "wave_order": 3})
-    assert np.array_equal(staged, plain)
-    check_slabs(mbc, field, lists, [(2, 2, 4), (1, 1, 4)], dims, precisions=(1,), tune={"wave_sites": 64})
+    staged = run(mbc, field, lists, 1, tune={"wave_sites": 64, "wave_order": 4})
+    for order in (0, 1, 3):
+        plain = run(mbc, field, lists, 1, tune={"wave_sites": 64, "wave_order": order})
+        assert np.array_equal(staged, plain), order
+    check_slabs(mbc, field, lists, [(2, 2, 4), (1, 1, 4)], dims, precisions=(1,),
+                tune={"wave_sites": 64, "wave_order": 4})
 
 
 def test_bounded_wait_timeout_is_reported(mbc):
