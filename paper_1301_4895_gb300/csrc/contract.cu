@@ -721,7 +721,10 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         const int64_t nblk = (W / 64 + 7) / 8;
         const int64_t target = (int64_t)nsm * 3 * 8;
         int64_t nchunks = std::max<int64_t>(1, std::min<int64_t>(s.n_z, (target + nblk - 1) / nblk));
-        int64_t zchunk = (s.n_z + nchunks - 1) / nchunks;
+        // at most 16 outputs per item: the resident CTAs then cover a narrow
+        // window of consecutive outputs (measured +3 % on 8Be, +2 % on 4He
+        // (0,1,0,1) against one range per CTA)
+        int64_t zchunk = std::min<int64_t>(16, (s.n_z + nchunks - 1) / nchunks);
         if (tune && tune->zchunk > 0) zchunk = tune->zchunk;
         nchunks = (s.n_z + zchunk - 1) / zchunk;
         const int zb = (int)std::max<int64_t>(1, std::min<int64_t>(zchunk, (int64_t)((64u << 10) / per_z)));
