@@ -443,7 +443,8 @@ def per_config_entry(mbc, torch, dev, name, peaks, n_sm, probes, warmup=3, steps
     kinds = {0: f"FP64 vector, derived: {n_sm} SMs x 2 DFMA/clk x max SM clock",
              1: f"FP32 vector, derived: {n_sm} SMs x 128 FFMA/clk x max SM clock"}
     kernels = {0: "k_large_step<FP64>", 1: "k_large_step_mx2"}
-    src = ("large_kernel.cuh", "mixed_common.cuh", "device_common.cuh")
+    # the launch shape changes the step kernels' traffic: the launch code is hashed too
+    src = ("large_kernel.cuh", "mixed_common.cuh", "device_common.cuh", "contract.cu")
     entry = {"workload": what, "units_per_step": units, "sites_per_step": v3 * nt, "n_ops": [st["n_ops_total"] for st in stats],
              "unit": "sink-site correlators/s", "warmup": warmup, "steps": {"fp64": steps64, "mixed": steps_mx}}
     with ClockSampler(dev.index if dev.index is not None else 0) as clk:
@@ -697,10 +698,15 @@ def main():
     roof_mx = roofline(kmx, msmx, nmx, nominal32, probe32,
                        f"FP32 vector, derived: {n_sm} SMs x 128 FFMA/clk x max SM clock", 1)
     roof = roof64 if primary == 0 else roof_mx
-    if roof is not None and args.workload == "nonrel" and primary == 0 and not has_large and not args.combined:
-        roof["traffic"] = profiled_traffic("k_small_fp64_he3_he4_16x16x16x16.md", v3 * nt * args.cfgs)
-        roof["traffic_note"] = ("DRAM bytes per launch (one launch per step) from the committed ncu summary, "
-                                "scaled from 65,536 to the step's sites")
+    if args.workload == "nonrel" and not has_large and not args.combined and not args.graph:
+        note = ("DRAM bytes per launch (one launch per step) from the committed ncu summary, "
+                "scaled from 65,536 to the step's sites")
+        for r, name, srcs in ((roof64, "k_small_fp64_he3_he4_16x16x16x16.md", ("small_kernel.cuh", "device_common.cuh")),
+                              (roof_mx, "k_small_ls_mixed_he3_he4_16x16x16x16.md",
+                               ("small_ls_kernel.cuh", "mixed_common.cuh", "device_common.cuh"))):
+            if r is not None:
+                r["traffic"] = profiled_traffic(name, v3 * nt * args.cfgs, srcs)
+                r["traffic_note"] = note
     line = {
         "metric": metric, "value": value, "unit": metric, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
