@@ -413,11 +413,11 @@ PER_CONFIG = {
     "he4rel_all_components": (
         "he4rel", "4He relativistic, all 1296 spin components (Table 1: 531,321,120 operations per site), "
         "one 16^3 slab (t = 0) of the 16^3x32 lattice, complex128, seed 2", 8,
-        ("k_large_step_fp64_he4rel_all_16x16x16x1.md", "k_large_step_mx2_mixed_he4rel_all_16x16x16x1.md")),
+        ("k_large_step_fp64_he4rel_all_16x16x16x1.md", "k_large_step_split_mixed_he4rel_all_16x16x16x1.md")),
     "be8": (
         "be8", "8Be relativistic (0,1,2,3,0,1,2,3) (Tables 1, 5: 448,496,928 operations per site), one 16^3 slab "
         "(configuration 0, t = 0) of the 16^3x32 x 12 lattice, complex64 storage, seed 4", 8,
-        ("k_large_step_fp64_be8_16x16x16x1.md", "k_large_step_mx2_mixed_be8_16x16x16x1.md")),
+        ("k_large_step_fp64_be8_16x16x16x1.md", "k_large_step_split_mixed_be8_16x16x16x1.md")),
 }
 
 
@@ -442,7 +442,7 @@ def per_config_entry(mbc, torch, dev, name, peaks, n_sm, probes, warmup=3, steps
     peak = {0: n_sm * 2 * 2 * sm_max * 1e6, 1: n_sm * 128 * 2 * sm_max * 1e6}
     kinds = {0: f"FP64 vector, derived: {n_sm} SMs x 2 DFMA/clk x max SM clock",
              1: f"FP32 vector, derived: {n_sm} SMs x 128 FFMA/clk x max SM clock"}
-    kernels = {0: "k_large_step<FP64>", 1: "k_large_step_mx2"}
+    kernels = {0: "k_large_step<FP64>", 1: "k_large_step_split"}
     # the launch shape changes the step kernels' traffic: the launch code is hashed too
     src = ("large_kernel.cuh", "mixed_common.cuh", "device_common.cuh", "contract.cu")
     entry = {"workload": what, "units_per_step": units, "sites_per_step": v3 * nt, "n_ops": [st["n_ops_total"] for st in stats],
@@ -683,10 +683,10 @@ def main():
     has_large = any(n[2] == 4 for n in nuclei)
     kname = {0: " + ".join(k for k, on in (("k_small<FP64>", has_small), ("k_large_step<FP64>", has_large)) if on),
              1: " + ".join(k for k, on in (("k_small_ls<Mixed>", has_small),
-                                            ("k_large_step_gen" if args.list_free else "k_large_step_mx2", has_large))
+                                            ("k_large_step_gen" if args.list_free else "k_large_step_split", has_large))
                            if on)}
     if sink == "block" or n_src > 1 or args.list_free:  # wave kernels only
-        kname = {0: "k_large_step<FP64>", 1: "k_large_step_gen" if args.list_free else "k_large_step_mx2"}
+        kname = {0: "k_large_step<FP64>", 1: "k_large_step_gen" if args.list_free else "k_large_step_split"}
         if sink == "block":
             kname = {p: "k_project_blocks + " + k for p, k in kname.items()}
 
@@ -740,7 +740,16 @@ def main():
             line["cpu_baseline"] = cpu_baseline_projected(wl, [(n, tl.components()) for n, tl in zip(nuclei, lists)],
                                                           nt, moms, n_src, n_sinks)
         else:
-            line["cpu_baseline"] = cpu_baseline(wl, [(n, tl.components()) for n, tl in zip(nuclei, lists)], nt)
+            if args.combined:  # one list, one part per nucleus: each nucleus' own components
+                comps = lists[0].components()
+                spec = []
+                for part in lists[0].parts():
+                    a_ = part["n_p"] + part["n_n"]
+                    nu = next(n for n in nuclei if n[0] == part["n_p"] and n[1] == part["n_n"])
+                    spec.append((nu, [(snk[:a_], src[:a_]) for snk, src in comps[part["c0"]:part["c1"]]]))
+            else:
+                spec = [(n, tl.components()) for n, tl in zip(nuclei, lists)]
+            line["cpu_baseline"] = cpu_baseline(wl, spec, nt)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -293,11 +293,13 @@ typedef struct {
                                    0 site groups of a chunk side by side, 1 a CTA's
                                    warps on consecutive chunks of one site group.
                                    Mixed: 0 (or 2) one CTA of 32 warps per SM on
-                                   consecutive outputs of one site group, 1 the same
-                                   with 8-warp CTAs, 3 8-warp CTAs with the site
-                                   groups of a chunk side by side, 4 block rows of
-                                   runs of outputs staged in shared memory by bulk
-                                   copies (where the runs qualify)                */
+                                   consecutive (output, site group) pairs, one warp
+                                   per output; 5 the same with an output's terms split
+                                   over several warps; 1 8-warp CTAs on consecutive
+                                   outputs of one site group; 3 8-warp CTAs with the
+                                   site groups side by side; 4 block rows of runs of
+                                   outputs staged in shared memory by bulk copies
+                                   (where the runs qualify)                       */
     int32_t list_free;          /* large-stage step kernel: 0 regenerate the splits of
                                    list-free lists, read the arrays of the others;
                                    1 also regenerate the dense steps of lists with

@@ -749,16 +749,36 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         // multiple of 64; the planar pair layout of the wave buffers is this
         // kernel's).
         // wave_order (mixed): 0 (default) or 2: one CTA of 32 warps per SM
-        // takes consecutive outputs of one site group, one output per warp
-        // item, so that neighbouring outputs' gathers of X (they share rows)
-        // hit in L1 and the few hundred outputs in flight keep their rows
-        // in L2; 1: the same order with 8-warp CTAs; 3: 8-warp CTAs with the
-        // site groups of an output side by side; 4: the block rows of runs
-        // of outputs staged in shared memory by bulk copies
-        // (k_large_step_yc, on the steps where the runs qualify). Measured
-        // on GB300, mixed: 8Be 2,508 (0) / 2,035 (3) / 1,942 (4) sink-site
-        // correlators/s, 4He with all components 2,109 / 2,062 / 1,871.
-        const int order = tune ? (tune->wave_order == 2 ? 0 : tune->wave_order) : 0;
+        // takes consecutive (output, 64-site group) pairs, group fastest, one
+        // warp per output (k_large_step_split, S = 1): the outputs in flight
+        // are a few hundred consecutive ones, whose rows of X stay in L2;
+        // 5: the same with each output's terms split over S = 2 .. 32 warps
+        // (S grows with the splits per output) and the partial sums combined
+        // in a fixed order; 1: k_large_step_mx2 with 8-warp CTAs on
+        // consecutive outputs of one site group; 3: 8-warp CTAs with the site
+        // groups side by side; 4: the block rows of runs of outputs staged in
+        // shared memory by bulk copies (k_large_step_yc, where the runs
+        // qualify). Measured on GB300, mixed, sink-site correlators/s: 8Be
+        // 2,452 (0) / 2,086 (5) / 1,982 (1) / 1,942 (4); 4He with all
+        // components 2,213 / 2,112 / 2,033 / 1,871; 4He (0,1,0,1) 129.4 K /
+        // 127.4 K / 104.8 K / 117 K.
+        const int order = tune ? tune->wave_order : 0;
+        if (order == 0 || order == 2 || order == 5) {
+            int S = 1;
+            if (order == 5)
+                while (S < 32 && (int64_t)(2 * S) * 32 <= s.k) S *= 2;
+            const int64_t items = (s.n_z * (W / 64) + 32 / S - 1) / (32 / S);
+            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)nsm));
+            {
+                TimedLaunch tl(stream);
+                note_launch();
+                k_large_step_split<<<(unsigned)grid, 1024, 0, stream>>>(
+                    c->d_opx[m], c->d_opy[m], s.n_z, s.k, S, W, reinterpret_cast<const float2 *>(X),
+                    reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
+            }
+            MBC_CUDA_TRY(cudaGetLastError());
+            return MBC_OK;
+        }
         const YRuns *yr = order == 4 ? yruns_for(L, c, m) : nullptr;
         if (yr) {
             const size_t smem = (size_t)kYcRows * 512 + (size_t)kYcWarps * 32 * sizeof(OpRec) + 16;
@@ -781,7 +801,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
                 return MBC_OK;
             }
         }
-        const int threads = order == 0 ? 1024 : 256;
+        const int threads = 256;
         const int64_t ngroups = W / 64;
         // one output per warp item: the warps in flight then cover a few
         // hundred consecutive outputs, whose operations read a few rows of
@@ -797,12 +817,7 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         {
             TimedLaunch tl(stream);
             note_launch();
-            if (order == 0)
-                k_large_step_mx2<32><<<(unsigned)grid, threads, 0, stream>>>(
-                    c->d_opx[m], c->d_opy[m], s.n_z, s.k, zchunk, W, 1, reinterpret_cast<const float2 *>(X),
-                    reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
-            else
-                k_large_step_mx2<8><<<(unsigned)grid, threads, 0, stream>>>(
+            k_large_step_mx2<8><<<(unsigned)grid, threads, 0, stream>>>(
                     c->d_opx[m], c->d_opy[m], s.n_z, s.k, zchunk, W, order == 1 ? 1 : 0, reinterpret_cast<const float2 *>(X),
                     reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
         }

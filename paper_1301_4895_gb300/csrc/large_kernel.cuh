@@ -288,6 +288,75 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? 4 : 1)
     }
 }
 
+// The mixed step with one CTA of 32 warps per SM and the terms of an output
+// split over S warps (S = 1, 2, 4, ..., 32): the CTA takes 32 / S consecutive
+// (output, 64-site group) pairs at a time, warp w works on pair w / S and
+// its term range (w mod S) of k / S terms with a PairAcc (two sites per
+// lane, as k_large_step_mx2). Each further warp of an output rounds its
+// compensated partial sum to FP32 (the stored stage value is FP32 too) and
+// passes it through its operation-record buffer; the output's first warp adds
+// them to its own compensated sum in a fixed order (two-sum, the errors
+// joining the compensation). No shared memory beyond the records: L1 keeps
+// its room for the rows of X. Few outputs are in flight at once, so the rows
+// they name stay in L2 even when their number per output is large; S = 1
+// is k_large_step_mx2's order with one output per item. W must be a
+// multiple of 64.
+__global__ void __launch_bounds__(1024, 1)
+    k_large_step_split(const uint32_t *__restrict__ opx, const uint16_t *__restrict__ opy, int64_t n_z, int64_t k,
+                       int S, int W, const float2 *__restrict__ X, const float2 *__restrict__ Y,
+                       float2 *__restrict__ Z) {
+    __shared__ OpRec recs[32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    OpRec *rec = recs[warp];
+    const int opc = 32 / S, oo = warp / S, seg = warp % S;
+    const int ngroups = W >> 6;
+    // outputs (z, site group) numbered with the group fastest; a CTA item is
+    // 32 / S consecutive ones (the measured-fastest order: a few outputs
+    // across all site groups per CTA)
+    const int64_t n_out = n_z * ngroups;
+    const int64_t n_items = (n_out + opc - 1) / opc;
+    const int64_t j0 = k * seg / S, j1 = k * (seg + 1) / S;
+    const uint32_t row_bytes = (uint32_t)W * (uint32_t)sizeof(float2);
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int64_t o = item * opc + oo;
+        const bool live = o < n_out;
+        const int64_t z = live ? o / ngroups : 0;
+        const int group = (int)(o % ngroups);
+        const int col4 = group * 32 + lane;  // float4 column: sites 2 col4, 2 col4 + 1
+        PairAcc acc;
+        acc.zero();
+        if (live) {
+            const unsigned char *Xc =
+                reinterpret_cast<const unsigned char *>(reinterpret_cast<const float4 *>(X) + col4);
+            const unsigned char *Yc =
+                reinterpret_cast<const unsigned char *>(reinterpret_cast<const float4 *>(Y) + col4);
+            const uint32_t *ox = opx + z * k;
+            const uint16_t *oy = opy + z * k;
+            for (int64_t b0 = j0; b0 < j1; b0 += 32) {
+                const int nb = (int)min((int64_t)32, j1 - b0);
+                __syncwarp();  // the previous records are consumed
+                if (lane < nb) rec[lane] = op_rec(__ldg(ox + b0 + lane), __ldg(oy + b0 + lane));
+                __syncwarp();
+                pair_terms<4>(rec, nb, Xc, Yc, row_bytes, acc);
+            }
+        }
+        if (S == 1) {
+            if (live) reinterpret_cast<ulonglong2 *>(Z + z * W)[col4] = acc.store();
+            continue;
+        }
+        __syncthreads();  // every warp is done with its records
+        ulonglong2 *mine = reinterpret_cast<ulonglong2 *>(recs[warp]);
+        if (seg != 0) mine[lane] = acc.store();
+        __syncthreads();
+        if (seg == 0 && live) {
+            for (int p = 1; p < S; ++p)
+                acc.add(reinterpret_cast<const ulonglong2 *>(recs[warp + p])[lane], make_ulonglong2(0ull, 0ull));
+            reinterpret_cast<ulonglong2 *>(Z + z * W)[col4] = acc.store();
+        }
+        __syncthreads();  // the partials are read before the next item's records overwrite them
+    }
+}
+
 // The mixed step with the block rows staged in shared memory. The outputs
 // of a stored step are cut, on the host, into runs of consecutive outputs
 // whose operations name at most kYcRows distinct block rows f[y]; an

@@ -163,6 +163,18 @@ struct PairAcc {
     __device__ __forceinline__ ulonglong2 store() const {
         return make_ulonglong2(f2_add(sr, nr), f2_add(si, ni));
     }
+    // add another accumulator (t = its sums, u = its negated compensations):
+    // two-sum of the sums, the rounding error joins the compensations
+    __device__ __forceinline__ void add(ulonglong2 t, ulonglong2 u) {
+        const uint64_t r = f2_add(sr, t.x), br = f2_sub(r, sr);
+        const uint64_t er = f2_add(f2_sub(sr, f2_sub(r, br)), f2_sub(t.x, br));
+        const uint64_t i = f2_add(si, t.y), bi = f2_sub(i, si);
+        const uint64_t ei = f2_add(f2_sub(si, f2_sub(i, bi)), f2_sub(t.y, bi));
+        sr = r;
+        si = i;
+        nr = f2_add(er, f2_add(nr, u.x));
+        ni = f2_add(ei, f2_add(ni, u.y));
+    }
 };
 
 }  // namespace mbc

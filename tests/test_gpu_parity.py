@@ -388,19 +388,20 @@ def test_wave_order_and_chunking_variants(mbc):
 def test_staged_block_rows_bitwise(mbc):
     """The mixed wave step that stages the block rows of runs of outputs in
     shared memory with bulk copies (wave_order 4) performs the same terms in
-    the same order as the steps that gather both operands (every CTA
-    order): bitwise equal results over several waves, and within the
-    oracle's bound."""
+    the same order as the steps that gather both operands with one warp per
+    output: bitwise equal results over several waves; it and the order that
+    splits an output's terms over warps are within the oracle's bound."""
     dims = (3, 4, 6)  # 72 sites: two waves of 64
     sp = (0, 1, 0, 1)
     lists = [mbc.build_term_list(2, 2, 4, spins=[(sp, sp)]), mbc.build_term_list(1, 1, 4)]
     field = synth.field(16, 1, 2, dims, 0.4, eps=EPS)
     staged = run(mbc, field, lists, 1, tune={"wave_sites": 64, "wave_order": 4})
-    for order in (0, 1, 3):
+    for order in (0, 1, 3):  # the orders with one warp per output
         plain = run(mbc, field, lists, 1, tune={"wave_sites": 64, "wave_order": order})
         assert np.array_equal(staged, plain), order
-    check_slabs(mbc, field, lists, [(2, 2, 4), (1, 1, 4)], dims, precisions=(1,),
-                tune={"wave_sites": 64, "wave_order": 4})
+    for order in (4, 5):  # 5: outputs' terms split over warps (another fixed order)
+        check_slabs(mbc, field, lists, [(2, 2, 4), (1, 1, 4)], dims, precisions=(1,),
+                    tune={"wave_sites": 64, "wave_order": order})
 
 
 def test_bounded_wait_timeout_is_reported(mbc):
@@ -652,11 +653,14 @@ def test_list_free_steps_match_stored_lists(mbc, n_p, n_n, D, spins):
     assert st["n_ops_total"] == sf["n_ops_total"] and sf["op_bytes"] < st["op_bytes"]
     moms = ((0, 0, 0), (1, 0, 1))
     for p in (0, 1):
-        a = run(mbc, field, [stored], p, moms=moms, tune={"regime": 2})
+        # stored lists in the default order (mixed: one warp per output, the
+        # order the regenerated operations run in)
+        order = {}
+        a = run(mbc, field, [stored], p, moms=moms, tune={"regime": 2, **order})
         b = run(mbc, field, [free], p, moms=moms)
         assert np.array_equal(a, b), p
         if st["dense_steps"]:
-            c = run(mbc, field, [stored], p, moms=moms, tune={"regime": 2, "list_free": 1})
+            c = run(mbc, field, [stored], p, moms=moms, tune={"regime": 2, "list_free": 1, **order})
             assert np.array_equal(a, c), p
     check_slabs(mbc, field, [free], [(n_p, n_n, D)], dims, moms=moms)
     check_slabs(mbc, synth.field(28, 1, 2, dims, 0.4), [free], [(n_p, n_n, D)], dims, precisions=(0,), moms=moms)
