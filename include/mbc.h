@@ -292,10 +292,13 @@ typedef struct {
     int32_t wave_order;         /* large-stage step kernels on stored lists. FP64:
                                    0 site groups of a chunk side by side, 1 a CTA's
                                    warps on consecutive chunks of one site group.
-                                   Mixed: 0 (or 2) one CTA of 32 warps per SM on
-                                   consecutive (output, site group) pairs, one warp
-                                   per output; 5 the same with an output's terms split
-                                   over several warps; 1 8-warp CTAs on consecutive
+                                   Mixed: 0 one CTA per SM on consecutive (output,
+                                   site group) pairs, one warp per output: 20 warps
+                                   with 8 gathers in flight each on steps of at least
+                                   64 terms per output, 32 warps with 4 on the others;
+                                   2 32 warps on every step; 6 20 warps on every step;
+                                   5 32 warps with an output's terms split over
+                                   several warps; 1 8-warp CTAs on consecutive
                                    outputs of one site group; 3 8-warp CTAs with the
                                    site groups side by side; 4 block rows of runs of
                                    outputs staged in shared memory by bulk copies

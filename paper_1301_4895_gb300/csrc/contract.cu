@@ -633,6 +633,9 @@ GenStep gen_step(const mbc_term_list *L, const DeviceCache *c, size_t m) {
 // (about a second).
 constexpr int kYcWarps = 32;
 constexpr uint32_t kWaitPolls = 1u << 24;
+// Terms per output from which the mixed wave step keeps 8 gathers in flight
+// per warp (20-warp CTAs) rather than 4 (32-warp CTAs).
+constexpr int64_t kSplitWideTerms = 64;
 
 // The runs of step m for k_large_step_yc, cut on the host at the first mixed
 // call that runs the step and uploaded with the list's device copy. A step
@@ -748,33 +751,47 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         // mixed precision, stored operations: two sites per lane (W is a
         // multiple of 64; the planar pair layout of the wave buffers is this
         // kernel's).
-        // wave_order (mixed): 0 (default) or 2: one CTA of 32 warps per SM
-        // takes consecutive (output, 64-site group) pairs, group fastest, one
-        // warp per output (k_large_step_split, S = 1): the outputs in flight
-        // are a few hundred consecutive ones, whose rows of X stay in L2;
-        // 5: the same with each output's terms split over S = 2 .. 32 warps
-        // (S grows with the splits per output) and the partial sums combined
-        // in a fixed order; 1: k_large_step_mx2 with 8-warp CTAs on
-        // consecutive outputs of one site group; 3: 8-warp CTAs with the site
-        // groups side by side; 4: the block rows of runs of outputs staged in
-        // shared memory by bulk copies (k_large_step_yc, where the runs
-        // qualify). Measured on GB300, mixed, sink-site correlators/s: 8Be
-        // 2,452 (0) / 2,086 (5) / 1,982 (1) / 1,942 (4); 4He with all
-        // components 2,213 / 2,112 / 2,033 / 1,871; 4He (0,1,0,1) 129.4 K /
-        // 127.4 K / 104.8 K / 117 K.
+        // wave_order (mixed): 0 (default): one CTA per SM takes consecutive
+        // (output, 64-site group) pairs, group fastest, one warp per output
+        // (k_large_step_split, S = 1): the outputs in flight are a few
+        // hundred consecutive ones, whose rows of X stay in L2. Steps whose
+        // outputs have at least kSplitWideTerms terms run 20-warp CTAs with 8
+        // gathers in flight per warp (96 registers), the others 32-warp CTAs
+        // with 4 (64 registers), where a group of 8 would leave a serial
+        // tail of up to 7 terms; 2: 32 warps on every step, 6: 20 warps on
+        // every step; 5: 32 warps with each output's terms split over S = 2
+        // .. 16 warps (S grows with the splits per output) and the partial
+        // sums combined in a fixed order; 1: k_large_step_mx2 with 8-warp
+        // CTAs on consecutive outputs of one site group; 3: 8-warp CTAs with
+        // the site groups side by side; 4: the block rows of runs of outputs
+        // staged in shared memory by bulk copies (k_large_step_yc, where the
+        // runs qualify). Measured on GB300, mixed, sink-site correlators/s:
+        // 8Be 2,797 (0) / 2,517 (2) / 2,793 (6) / 2,086 (5) / 1,982 (1) /
+        // 1,942 (4); 4He with all components 2,434 / 2,305 / 2,386 / 2,112 /
+        // 2,033 / 1,871; 4He (0,1,0,1) 132.9 K / 132.7 K / 125.1 K / 127.4 K
+        // / 104.8 K / 117 K. (24 warps x 6 gathers, 28 x 5 and 16 x 12 were
+        // within 1 % of 20 x 8 on 8Be and up to 5 % slower on 4He.)
         const int order = tune ? tune->wave_order : 0;
-        if (order == 0 || order == 2 || order == 5) {
+        if (order == 0 || order == 2 || order == 5 || order == 6) {
+            const bool wide = order == 6 || (order == 0 && s.k >= kSplitWideTerms);
+            const int warps = wide ? 20 : 32;
             int S = 1;
             if (order == 5)
-                while (S < 32 && (int64_t)(2 * S) * 32 <= s.k) S *= 2;
-            const int64_t items = (s.n_z * (W / 64) + 32 / S - 1) / (32 / S);
+                while (2 * S <= warps / 2 && (int64_t)(2 * S) * 32 <= s.k) S *= 2;
+            const int opc = warps / S;
+            const int64_t items = (s.n_z * (W / 64) + opc - 1) / opc;
             const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)nsm));
             {
                 TimedLaunch tl(stream);
                 note_launch();
-                k_large_step_split<<<(unsigned)grid, 1024, 0, stream>>>(
-                    c->d_opx[m], c->d_opy[m], s.n_z, s.k, S, W, reinterpret_cast<const float2 *>(X),
-                    reinterpret_cast<const float2 *>(Y), reinterpret_cast<float2 *>(Z));
+                const uint32_t *ox = c->d_opx[m];
+                const uint16_t *oy = c->d_opy[m];
+                const float2 *Xf = reinterpret_cast<const float2 *>(X), *Yf = reinterpret_cast<const float2 *>(Y);
+                float2 *Zf = reinterpret_cast<float2 *>(Z);
+                if (wide)
+                    k_large_step_split<20, 8><<<(unsigned)grid, 640, 0, stream>>>(ox, oy, s.n_z, s.k, S, W, Xf, Yf, Zf);
+                else
+                    k_large_step_split<32, 4><<<(unsigned)grid, 1024, 0, stream>>>(ox, oy, s.n_z, s.k, S, W, Xf, Yf, Zf);
             }
             MBC_CUDA_TRY(cudaGetLastError());
             return MBC_OK;

@@ -288,8 +288,9 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? 4 : 1)
     }
 }
 
-// The mixed step with one CTA of 32 warps per SM and the terms of an output
-// split over S warps (S = 1, 2, 4, ..., 32): the CTA takes 32 / S consecutive
+// The mixed step with one CTA of WARPS warps per SM, G gathers in flight per
+// warp, and the terms of an output split over S warps (S = 1, 2, 4, ...,
+// WARPS / 2): the CTA takes WARPS / S consecutive
 // (output, 64-site group) pairs at a time, warp w works on pair w / S and
 // its term range (w mod S) of k / S terms with a PairAcc (two sites per
 // lane, as k_large_step_mx2). Each further warp of an output rounds its
@@ -301,17 +302,18 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? 4 : 1)
 // they name stay in L2 even when their number per output is large; S = 1
 // is k_large_step_mx2's order with one output per item. W must be a
 // multiple of 64.
-__global__ void __launch_bounds__(1024, 1)
+template <int WARPS, int G>
+__global__ void __launch_bounds__(32 * WARPS, 1)
     k_large_step_split(const uint32_t *__restrict__ opx, const uint16_t *__restrict__ opy, int64_t n_z, int64_t k,
                        int S, int W, const float2 *__restrict__ X, const float2 *__restrict__ Y,
                        float2 *__restrict__ Z) {
-    __shared__ OpRec recs[32][32];
+    __shared__ OpRec recs[WARPS][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     OpRec *rec = recs[warp];
-    const int opc = 32 / S, oo = warp / S, seg = warp % S;
+    const int opc = WARPS / S, oo = warp / S, seg = warp % S;
     const int ngroups = W >> 6;
     // outputs (z, site group) numbered with the group fastest; a CTA item is
-    // 32 / S consecutive ones (the measured-fastest order: a few outputs
+    // WARPS / S consecutive ones (the measured-fastest order: a few outputs
     // across all site groups per CTA)
     const int64_t n_out = n_z * ngroups;
     const int64_t n_items = (n_out + opc - 1) / opc;
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(1024, 1)
                 __syncwarp();  // the previous records are consumed
                 if (lane < nb) rec[lane] = op_rec(__ldg(ox + b0 + lane), __ldg(oy + b0 + lane));
                 __syncwarp();
-                pair_terms<4>(rec, nb, Xc, Yc, row_bytes, acc);
+                pair_terms<G>(rec, nb, Xc, Yc, row_bytes, acc);
             }
         }
         if (S == 1) {
