@@ -285,7 +285,11 @@ typedef struct {
 typedef struct {
     int32_t sites_per_cta;      /* FP64 small-stage kernel: sites per CTA      */
     int32_t threads_per_cta;    /* mixed small-stage kernel: threads per CTA   */
-    int32_t wave_sites;         /* large-stage kernels: sites in flight        */
+    int32_t wave_sites;         /* large-stage kernels: sites in flight (0: the
+                                   narrowest multiple of 64 that gives a wave at
+                                   least 2e10 site-operations, within an 8 GB
+                                   scratch budget; mixed list-free lists at least
+                                   512, in multiples of 512)                      */
     int32_t regime;             /* 0 auto, 1 force small-stage, 2 force large  */
     int32_t zchunk;             /* large-stage step kernel: outputs per warp item
                                    (mixed default 1)                            */
@@ -295,7 +299,9 @@ typedef struct {
                                    Mixed: 0 one CTA per SM on consecutive (output,
                                    site group) pairs, one warp per output: 20 warps
                                    with 8 gathers in flight each on steps of at least
-                                   64 terms per output, 32 warps with 4 on the others;
+                                   64 terms per output, 32 warps with 4 on the others,
+                                   an output's terms split over up to 16 warps on steps
+                                   of fewer items than SMs and at least 1024 terms;
                                    2 32 warps on every step; 6 20 warps on every step;
                                    5 32 warps with an output's terms split over
                                    several warps; 1 8-warp CTAs on consecutive

@@ -577,6 +577,9 @@ mbc_status launch_small_batch(const SmallBatch &B, const FieldDesc &F, const Mom
     return MBC_OK;
 }
 
+// Site-operations (operations x sites) a wave needs at least.
+constexpr int64_t kWaveSiteOps = 20000000000LL;
+
 struct LargeSizes {
     int W;
     size_t blk_bytes, stage_bytes, c_bytes, sexp_bytes;
@@ -590,6 +593,24 @@ LargeSizes large_sizes(const mbc_term_list *L, const DeviceCache *c, const mbc_t
                        16LL * L->n_comp + 4;
     const int64_t budget = 8LL << 30;
     int64_t W = budget / per_site;
+    // no wider than kWaveSiteOps site-operations need: narrow waves keep the
+    // stage rows that concurrent outputs gather close together in L2
+    // (measured on GB300: 8Be mixed 2,777 -> 3,251 correlators/s with 64
+    // instead of 576 sites, FP64 318 -> 324), and waves of that much work
+    // amortise their launches and small steps (4He (0,1,0,1), 8.5 M
+    // operations: 52 K correlators/s with 64 sites, 132 K with 2,176). The
+    // CTA-shared regeneration of list-free steps covers 512 sites per CTA
+    // (8Be list-free mixed: 1,338 with 640 sites, 2,100 with 512).
+    int64_t ops = 0;
+    bool regen = false;
+    for (const auto &st : L->steps) {
+        ops += st.n_z * st.k;
+        regen = regen || st.generated || (tune && tune->list_free == 1 && st.dense);
+    }
+    const bool regen_ctas = regen && sizeof(V) == sizeof(float2);
+    W = std::min<int64_t>(W, std::max<int64_t>(regen_ctas ? 512 : 64,
+                                               (kWaveSiteOps + ops - 1) / std::max<int64_t>(ops, 1)));
+    if (regen_ctas && W >= 512) W = W / 512 * 512;  // whole CTAs of 8 site groups
     if (tune && tune->wave_sites > 0) W = tune->wave_sites;
     // multiples of 64 sites: the mixed step kernel covers 64 sites per warp
     W = std::max<int64_t>(64, std::min<int64_t>(W, 4096));
@@ -636,6 +657,9 @@ constexpr uint32_t kWaitPolls = 1u << 24;
 // Terms per output from which the mixed wave step keeps 8 gathers in flight
 // per warp (20-warp CTAs) rather than 4 (32-warp CTAs).
 constexpr int64_t kSplitWideTerms = 64;
+// Terms per output from which a step of fewer items than SMs splits its
+// outputs' terms over several warps.
+constexpr int64_t kSplitFewTerms = 1024;
 
 // The runs of step m for k_large_step_yc, cut on the host at the first mixed
 // call that runs the step and uploaded with the list's device copy. A step
@@ -761,22 +785,32 @@ mbc_status launch_step(const mbc_term_list *L, const DeviceCache *c, size_t m, c
         // tail of up to 7 terms; 2: 32 warps on every step, 6: 20 warps on
         // every step; 5: 32 warps with each output's terms split over S = 2
         // .. 16 warps (S grows with the splits per output) and the partial
-        // sums combined in a fixed order; 1: k_large_step_mx2 with 8-warp
+        // sums combined in a fixed order (order 0 does this too on steps of
+        // fewer items than SMs and at least kSplitFewTerms terms); 1: k_large_step_mx2 with 8-warp
         // CTAs on consecutive outputs of one site group; 3: 8-warp CTAs with
         // the site groups side by side; 4: the block rows of runs of outputs
         // staged in shared memory by bulk copies (k_large_step_yc, where the
-        // runs qualify). Measured on GB300, mixed, sink-site correlators/s:
+        // runs qualify). Measured on GB300, mixed, sink-site correlators/s
+        // (8Be with waves of 576 sites, before the narrower default waves):
         // 8Be 2,797 (0) / 2,517 (2) / 2,793 (6) / 2,086 (5) / 1,982 (1) /
         // 1,942 (4); 4He with all components 2,434 / 2,305 / 2,386 / 2,112 /
         // 2,033 / 1,871; 4He (0,1,0,1) 132.9 K / 132.7 K / 125.1 K / 127.4 K
         // / 104.8 K / 117 K. (24 warps x 6 gathers, 28 x 5 and 16 x 12 were
-        // within 1 % of 20 x 8 on 8Be and up to 5 % slower on 4He.)
+        // within 1 % of 20 x 8 on 8Be and up to 5 % slower on 4He; 6
+        // gathers on the steps of 24 and 30 terms, which leave no tail,
+        // measured -0.7 % to +2 %.)
         const int order = tune ? tune->wave_order : 0;
         if (order == 0 || order == 2 || order == 5 || order == 6) {
-            const bool wide = order == 6 || (order == 0 && s.k >= kSplitWideTerms);
+            const int ngroups = W / 64;
+            // a step of fewer (output, site group) items than SMs with many
+            // terms per output (8Be's last step: one output of 3,168 terms)
+            // splits each output's terms over up to 16 warps of a 32-warp CTA
+            // (8Be mixed 3,266 -> 3,308 correlators/s)
+            const bool few = order == 0 && s.n_z * ngroups < (int64_t)nsm && s.k >= kSplitFewTerms;
+            const bool wide = !few && (order == 6 || (order == 0 && s.k >= kSplitWideTerms));
             const int warps = wide ? 20 : 32;
             int S = 1;
-            if (order == 5)
+            if (order == 5 || few)
                 while (2 * S <= warps / 2 && (int64_t)(2 * S) * 32 <= s.k) S *= 2;
             const int opc = warps / S;
             const int64_t items = (s.n_z * (W / 64) + opc - 1) / opc;
