@@ -470,8 +470,9 @@ __global__ void k_wait_timeout_check(uint32_t limit) {
 // outputs at a time its 256 threads regenerate the outputs' operations once
 // into shared memory, then every warp runs them on its sites exactly as the
 // stored words would run (same order, same arithmetic), so the integer work
-// is shared by the CTA's 512 sites (records as in k_large_step_mx2).
-// W must be a multiple of 64.
+// is shared by the CTA's 512 sites (records as in k_large_step_mx2), and
+// each warp keeps G gathers in flight. W must be a multiple of 64.
+template <int G>
 __global__ void __launch_bounds__(256, 3) k_large_step_gen(GenStep gs, int64_t n_z, int64_t k, int64_t zchunk, int zb,
                                                            int W, const float2 *__restrict__ X,
                                                            const float2 *__restrict__ Y, float2 *__restrict__ Z) {
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(256, 3) k_large_step_gen(GenStep gs, int64_t n
             for (int q = 0; q < nzr; ++q) {
                 PairAcc acc;
                 acc.zero();
-                pair_terms<4>(srec + q * k, (int)k, Xc, Yc, row_bytes, acc);  // k * 16 B fit shared memory
+                pair_terms<G>(srec + q * k, (int)k, Xc, Yc, row_bytes, acc);  // k * 16 B fit shared memory
                 reinterpret_cast<ulonglong2 *>(Z + (zr + q) * W)[col4] = acc.store();
             }
         }
