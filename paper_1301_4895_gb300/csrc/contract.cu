@@ -557,7 +557,9 @@ SmallLaunch size_small_batch(const std::vector<const DeviceCache *> &cs, const F
 mbc_status launch_small_batch(const SmallBatch &B, const FieldDesc &F, const MomDesc &M, const SmallLaunch &l,
                               bool mixed, int device, cudaStream_t stream, const double2 *phase, double2 *partial,
                               bool timed) {
-    auto kern = mixed ? k_small_ls<MixedTraits> : k_small<FP64Traits>;
+    bool nxi6 = true;
+    for (int i = 0; i < B.n_lists; ++i) nxi6 = nxi6 && B.plan[i].nxi == 6;
+    auto kern = !mixed ? k_small<FP64Traits> : nxi6 ? k_small_ls<MixedTraits, 6> : k_small_ls<MixedTraits, 0>;
     int per_sm = 0;
     mbc_status pst = prepare_kernel((const void *)kern, device, l.threads, l.smem, &per_sm);
     if (pst != MBC_OK) return pst;

@@ -50,7 +50,10 @@ __device__ __forceinline__ int f32_exponent(float f) {
     return eb == 0 ? -100000 : eb - 127;
 }
 
-template <class Tr>
+// NXI > 0: every list of the batch has NXI quark index values (6 for the
+// nonrelativistic operators), so the row-index arithmetic of the load,
+// diquark and block phases divides by constants; NXI = 0 reads it from the plan.
+template <class Tr, int NXI>
 __global__ void __launch_bounds__(1024, 1)
     k_small_ls(const __grid_constant__ SmallBatch B, FieldDesc F, MomDesc M, const double2 *__restrict__ phase,
                double2 *partial_base) {
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(1024, 1)
         const int l_end = B.shared ? B.n_lists : li0 + 1;
         const SmallPlan &P = B.plan[li0];
         const int32_t *need = B.shared ? B.need_union : P.need_blk;
-        const int nxi = P.nxi, nent = nxi * nxi;
+        const int nxi = NXI > 0 ? NXI : P.nxi, nent = nxi * nxi;
         const int64_t slab = tile / tiles_per_slab;
         const int tin = (int)(tile % tiles_per_slab);
         const int cfg = (int)(slab / F.n_t), t = F.t0 + (int)(slab % F.n_t);
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(1024, 1)
             ROW(P.q_off + e) = acc;
         }
         __syncthreads();
-        const int per_spin = P.npair * nxi;
+        const int per_spin = (NXI > 0 ? NXI * (NXI - 1) / 2 : P.npair) * nxi;
         for (int b = 0; b < 2; ++b) {
             if (!need[b]) continue;
             for (int e = warp; e < P.block_size; e += NW) {
