@@ -362,17 +362,24 @@ DeviceCache *get_cache(const mbc_term_list *Lc, int device, mbc_status &st) {
         // lanes-are-sites layout: z-major, operands as byte offsets of their
         // 256 B shared-memory rows (x << 8 | sign in bit 0 | y << 24), which
         // needs every stage and block index below 256 (all nonrelativistic
-        // lists); otherwise the mixed path takes the wave kernels
+        // lists); otherwise the mixed path takes the wave kernels. Each
+        // output's terms are ordered positive first (stable), so the kernel
+        // adds the first ones and subtracts the rest and its operation
+        // records need no sign
         std::vector<uint32_t> zpk;
         c->ls_ok = true;
         for (size_t m = 0; m < L->steps.size(); ++m) {
             const Step &s = L->steps[m];
             c->sp.step[m].zop_off = (int64_t)zpk.size();
-            for (size_t i = 0; i < s.x.size(); ++i) {
-                const uint32_t x = s.x[i], y = s.ys[i] & 0x7fffu, sg = (uint32_t)(s.ys[i] >> 15);
-                if (x >= 256 || y >= 256) c->ls_ok = false;
-                zpk.push_back((x & 0xffu) << 8 | sg | (y & 0xffu) << 24);
-            }
+            for (int64_t z = 0; z < s.n_z; ++z)
+                for (uint32_t want = 0; want < 2; ++want)
+                    for (int64_t j = 0; j < s.k; ++j) {
+                        const size_t i = (size_t)(z * s.k + j);
+                        const uint32_t x = s.x[i], y = s.ys[i] & 0x7fffu, sg = (uint32_t)(s.ys[i] >> 15);
+                        if (sg != want) continue;
+                        if (x >= 256 || y >= 256) c->ls_ok = false;
+                        zpk.push_back((x & 0xffu) << 8 | sg | (y & 0xffu) << 24);
+                    }
         }
         if ((st = upload(&c->d_small_zops, zpk.data(), zpk.size())) != MBC_OK) {
             free_cache(c);

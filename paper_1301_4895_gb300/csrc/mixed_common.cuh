@@ -104,6 +104,16 @@ struct MixedTraits {
         __device__ __forceinline__ void fma_sg(float2 x, float2 y, uint64_t sg) {
             f2_kahan_signed(s, n, prod(x.x, x.y, y), sg);
         }
+        // acc += x y and acc -= x y: the Kahan step's first sum is p + n
+        // and n - p, rounded as fma_sg's fma(p, +-1, n)
+        __device__ __forceinline__ void add_prod(float2 x, float2 y) { f2_kahan(s, n, prod(x.x, x.y, y)); }
+        __device__ __forceinline__ void sub_prod(float2 x, float2 y) {
+            const uint64_t p = prod(x.x, x.y, y);
+            const uint64_t yv = f2_sub(n, p);
+            const uint64_t t = f2_add(s, yv);
+            n = f2_sub(yv, f2_sub(t, s));
+            s = t;
+        }
         // combine with another accumulator (s2 + n2): two-sum of the sums
         __device__ __forceinline__ void add(float s2r, float n2r, float s2i, float n2i) {
             float2 sv = f2_unpack(s), nv = f2_unpack(n);

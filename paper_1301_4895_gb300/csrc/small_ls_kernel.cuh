@@ -63,8 +63,10 @@ __global__ void __launch_bounds__(1024, 1)
     __shared__ int sexp_s[32];
     const int NW = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // after the site region and the 64 partial rows: 32 operation records per warp
-    OpRec *rec = reinterpret_cast<OpRec *>(R + (int64_t)(B.site_stride + 64) * 32) + warp * 32;
+    // after the site region and the 64 partial rows: 32 operation records
+    // (x and y row byte offsets, 8 B) per warp, read two at a time
+    uint2 *rec = reinterpret_cast<uint2 *>(R + (int64_t)(B.site_stride + 64) * 32) + warp * 32;
+    const uint4 *rec2 = reinterpret_cast<const uint4 *>(rec);
     const int V3 = F.lx * F.ly * F.lz;
     const unsigned full = 0xffffffffu;
     const int tiles_per_slab = B.tiles_per_slab;
@@ -198,19 +200,39 @@ __global__ void __launch_bounds__(1024, 1)
                     for (int b0 = 0; b0 < len; b0 += 32) {
                         const int nb = min(32, len - b0);
                         // operands are byte offsets of 256 B rows, the sign is
-                        // bit 0: decoded once per batch into the warp's records
+                        // bit 0: decoded once per batch into the warp's records;
+                        // an output's positive terms come first, so the batch's
+                        // first npos terms are added and the rest subtracted
                         __syncwarp();
-                        if (lane < nb) {
-                            const uint32_t op = __ldg(op_ptr + b0 + lane);
-                            rec[lane] = OpRec{op & 0xff00u, op >> 16, f2_sign_pair(op & 1u)};
-                        }
+                        const uint32_t op = lane < nb ? __ldg(op_ptr + b0 + lane) : 0u;
+                        if (lane < nb) rec[lane] = make_uint2(op & 0xff00u, op >> 16);
+                        const int npos = nb - __popc(__ballot_sync(full, (op & 1u) != 0u));
                         __syncwarp();
-    #pragma unroll 4
-                        for (int q = 0; q < nb; ++q) {
-                            const OpRec r = rec[q];
-                            acc.fma_sg(*reinterpret_cast<const V *>(Xb + r.x), *reinterpret_cast<const V *>(Yb + r.y),
-                                       r.sg);
+#define LS_TERM(xo, yo, op_) acc.op_(*reinterpret_cast<const V *>(Xb + (xo)), *reinterpret_cast<const V *>(Yb + (yo)))
+                        int q = 0;
+#pragma unroll 2
+                        for (; q + 1 < npos; q += 2) {
+                            const uint4 r = rec2[q >> 1];
+                            LS_TERM(r.x, r.y, add_prod);
+                            LS_TERM(r.z, r.w, add_prod);
                         }
+                        if (q < npos) {  // the last positive term, then possibly the first negative one
+                            const uint4 r = rec2[q >> 1];
+                            LS_TERM(r.x, r.y, add_prod);
+                            if (q + 1 < nb) LS_TERM(r.z, r.w, sub_prod);
+                            q += 2;
+                        }
+#pragma unroll 2
+                        for (; q + 1 < nb; q += 2) {
+                            const uint4 r = rec2[q >> 1];
+                            LS_TERM(r.x, r.y, sub_prod);
+                            LS_TERM(r.z, r.w, sub_prod);
+                        }
+                        if (q < nb) {
+                            const uint2 r = rec[q];
+                            LS_TERM(r.x, r.y, sub_prod);
+                        }
+#undef LS_TERM
                     }
                     if (part < 0) {
                         Zl[((int)zb + zz) << 5] = acc.store();
