@@ -13,11 +13,13 @@ namespace mbc {
 // per-site values are rows of 32 lanes in shared memory ([entry][lane], 8 B
 // per lane), so every access of a warp is one conflict-free row. The warps
 // split the output components of each step; a warp's lanes decode 32
-// operations at a time into the warp's records (row offsets and the sign as
-// a +-1 pair, OpRec), which every lane then reads by broadcast; steps with
-// fewer outputs than warps split each output's terms over several warps and
-// combine the compensated partials in a fixed order. Shared memory: the
-// site region and 64 partial rows of 32 lanes, then 32 records per warp.
+// operations at a time into the warp's records (the two row offsets, 8 B;
+// an output's positive terms come first, so a ballot gives the batch's
+// split into added and subtracted terms), which every lane then reads two
+// at a time by broadcast; steps with fewer outputs than warps split each
+// output's terms over several warps and combine the compensated partials in
+// a fixed order. Shared memory: the site region and 64 partial rows of 32
+// lanes, then the records (16 B per thread reserved, 8 B used).
 
 // RN(d * 2^e) as FP32 from the bits of an FP64 value, integer operations only
 // (GB300's FP64 pipe is 1/64 of FP32). Results below the FP32 normal range
