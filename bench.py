@@ -393,17 +393,33 @@ def point_flops_per_site(stats, list_dims):
     return per_site
 
 
-def roofline_entry(flops_step, steps, kms, ms, launches, peak, probe, kind, kernel):
+def l1_operand_bound(n_sm, sm_max_mhz):
+    """The mixed recursion's operand bound, flop/s: a site-operation (8 flops)
+    reads two 8 B FP32 complex operands through the L1 / shared-memory data
+    pipe, which delivers one 128 B wavefront per SM clock."""
+    return n_sm * 128.0 * sm_max_mhz * 1e6 / 16.0 * 8.0
+
+
+def roofline_entry(flops_step, steps, kms, ms, launches, peak, probe, kind, kernel, l1_peak=None):
     """ALU roofline of the contraction kernels: algorithmic flops over their
-    CUDA-event time (the whole step when no kernel events were recorded)."""
+    CUDA-event time (the whole step when no kernel events were recorded).
+    l1_peak (mixed precision): the operand bound of l1_operand_bound beside it."""
     t_ms, basis = (kms, "kernel events") if kms > 0 else (ms, "whole step")
     if not (t_ms == t_ms) or t_ms <= 0:
         return None
     ach = flops_step * steps / (t_ms * 1e-3)
-    return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "peak_kind": kind, "measured_fma_peak": probe / 1e12,
-            "frac_of_measured_fma": ach / probe, "kernel": kernel, "time_basis": basis,
-            "kernel_ms_per_step": t_ms / steps, "launches_timed": launches, "flops_per_step": flops_step}
+    r = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+         "traffic": None, "peak_kind": kind, "measured_fma_peak": probe / 1e12,
+         "frac_of_measured_fma": ach / probe, "kernel": kernel, "time_basis": basis,
+         "kernel_ms_per_step": t_ms / steps, "launches_timed": launches, "flops_per_step": flops_step}
+    if l1_peak:
+        r["l1_operand_bound"] = {
+            "peak": l1_peak / 1e12, "unit": "TFLOP/s", "frac": ach / l1_peak,
+            "kind": "derived: SMs x 128 B/clk (one L1/shared-memory wavefront) x max SM clock / 16 B of FP32 "
+                    "complex operands per site-operation x 8 flop; the data pipe, not the FP32 pipe, bounds the "
+                    "mixed recursion (ncu: 63 % of a wavefront per SM clock in k_small_ls on the default workload, "
+                    "81 % L1/shared throughput in k_large_step_split on 8Be's largest step)"}
+    return r
 
 
 # Configurations of the metric's headline nuclei reported beside the default
@@ -465,7 +481,7 @@ def per_config_entry(mbc, torch, dev, name, peaks, n_sm, probes, warmup=3, steps
             kms, launches = mbc.timing_read()
             mbc.timing_enable(False)
             roof = roofline_entry(flops_step, steps, kms, ms, launches, peak[prec], probes[prec], kinds[prec],
-                                  kernels[prec])
+                                  kernels[prec], l1_operand_bound(n_sm, sm_max) if prec == 1 else None)
             if roof is not None:
                 roof["traffic"] = profiled_traffic(prof[prec], v3 * nt, src)
                 roof["traffic_note"] = ("DRAM bytes of the step kernel per step (all its launches), from the "
@@ -691,7 +707,8 @@ def main():
             kname = {p: "k_project_blocks + " + k for p, k in kname.items()}
 
     def roofline(kms, ms, launches, peak, probe, kind, prec):
-        return roofline_entry(flops_step, args.steps, kms, ms, launches, peak, probe, kind, kname[prec])
+        return roofline_entry(flops_step, args.steps, kms, ms, launches, peak, probe, kind, kname[prec],
+                              l1_operand_bound(n_sm, sm_max) if prec == 1 else None)
 
     roof64 = roofline(k64, ms64, n64, nominal64, probe64,
                       f"FP64 vector, derived: {n_sm} SMs x 2 DFMA/clk x max SM clock", 0)

@@ -37,3 +37,17 @@ def test_reference_arm_prints_one_line(args, metric):
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == metric and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_mixed_roofline_carries_the_operand_bound():
+    """The mixed recursion reads 16 B of FP32 complex operands per
+    site-operation (8 flops) through a data pipe of 128 B per SM clock: on 152
+    SMs at 2070 MHz that is 20.14 TFLOP/s, a quarter of the FP32 peak."""
+    import bench
+    l1 = bench.l1_operand_bound(152, 2070.0)
+    assert abs(l1 - 152 * 2070e6 * 64) < 1.0
+    fp32 = 152 * 128 * 2 * 2070e6
+    assert abs(l1 / fp32 - 0.25) < 1e-12
+    r = bench.roofline_entry(1e12, 1, 100.0, 110.0, 1, fp32, 0.99 * fp32, "fp32", "k", l1)
+    assert abs(r["achieved"] - 10.0) < 1e-9 and abs(r["l1_operand_bound"]["frac"] - 1e13 / l1) < 1e-12
+    assert "l1_operand_bound" not in bench.roofline_entry(1e12, 1, 100.0, 110.0, 1, fp32, fp32, "fp64", "k")
