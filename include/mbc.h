@@ -419,7 +419,10 @@ mbc_status mbc_contract_noalloc(const mbc_props *props, const mbc_term_list *lis
  * results of the calls in between are not valid; the status is cleared by
  * this report and the context stays usable), MBC_ERR_CUDA for a failed CUDA
  * call, MBC_OK otherwise. The kernels' waits are on asynchronous copies
- * into shared memory and give up after about a second of polling.
+ * into shared memory and give up after about a second of polling. A
+ * mbc_contract call with props->memory = MBC_MEM_HOST synchronises before it
+ * returns and reports (and clears) the same status itself; calls on device
+ * memory are asynchronous and leave it to this function.
  */
 mbc_status mbc_sync_status(void *stream);
 

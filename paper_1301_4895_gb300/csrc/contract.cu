@@ -33,6 +33,10 @@ inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_rel
 
 namespace mbc {
 
+// After a synchronisation of stream: the kernels' latched status word, read
+// and cleared (defined with mbc_sync_status).
+mbc_status take_device_status(cudaStream_t stream);
+
 #define MBC_CUDA_TRY(expr)                         \
     do {                                           \
         cudaError_t _e = (expr);                   \
@@ -1277,6 +1281,7 @@ mbc_status contract_host_pipelined(const mbc_props *props, const mbc_term_list *
     if (st == MBC_OK) cuda_ok(cudaMemcpyAsync(hout, dout, full_out, cudaMemcpyDeviceToHost, stream));
     cudaFreeAsync(stage, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess && st == MBC_OK) st = MBC_ERR_CUDA;
+    if (st == MBC_OK) st = take_device_status(stream);  // synchronous call: report a latched timeout
     return st;
 }
 
@@ -1566,6 +1571,7 @@ extern "C" mbc_status mbc_contract(const mbc_props *props, const mbc_term_list *
         MBC_CUDA_TRY(cudaMemcpyAsync(out, dev_out, out_bytes, cudaMemcpyDeviceToHost, stream));
         MBC_CUDA_TRY(cudaFreeAsync(staging, stream));
         MBC_CUDA_TRY(cudaStreamSynchronize(stream));
+        return take_device_status(stream);  // synchronous call: report a latched timeout
     }
     return MBC_OK;
 }
@@ -1577,7 +1583,13 @@ extern "C" mbc_status mbc_sync_status(void *stream_v) {
         (void)cudaGetLastError();
         return MBC_ERR_CUDA;
     }
-    // the kernels' latched status word (a bounded wait that ran out)
+    return mbc::take_device_status(stream);
+}
+
+namespace mbc {
+// After a synchronisation of stream: the kernels' latched status word (a
+// bounded wait that ran out), read and cleared; MBC_ERR_TIMEOUT if set.
+mbc_status take_device_status(cudaStream_t stream) {
     unsigned int word = 0;
     if (cudaMemcpyFromSymbolAsync(&word, g_device_status, sizeof(word), 0, cudaMemcpyDeviceToHost, stream) !=
             cudaSuccess ||
@@ -1597,6 +1609,7 @@ extern "C" mbc_status mbc_sync_status(void *stream_v) {
     }
     return MBC_OK;
 }
+}  // namespace mbc
 
 extern "C" mbc_status mbc_check_wait_timeout(uint32_t polls, void *stream_v) {
     if (polls < 1 || polls > (1u << 20)) return MBC_ERR_INVALID_ARG;

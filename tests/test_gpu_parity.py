@@ -418,7 +418,14 @@ def test_bounded_wait_timeout_is_reported(mbc):
     mbc.sync_status(s)  # cleared by the report
     dims = (2, 2, 2)
     field = synth.field(6, 1, 1, dims, 0.4, eps=EPS)
-    check_slabs(mbc, field, [mbc.build_term_list(1, 1, 2)], [(1, 1, 2)], dims)
+    tl = mbc.build_term_list(1, 1, 2)
+    # a host-memory call synchronises and reports a latched timeout itself
+    mbc.check_wait_timeout(64, stream=s)
+    with pytest.raises(mbc.MbcError) as ei:
+        mbc.contract(field, [tl], precision=0, stream=s)
+    assert ei.value.status == 5
+    mbc.sync_status(s)  # cleared by that report
+    check_slabs(mbc, field, [tl], [(1, 1, 2)], dims)
 
 
 @pytest.mark.parametrize("n_p,n_n,D,spins", [(1, 0, 4, None), (1, 1, 2, None), (2, 1, 2, None), (2, 2, 2, None),
